@@ -1,0 +1,375 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every test here checks the oracle against something other than itself: values
+the paper prints, published generator sequences, closed-form solutions of the
+discrete scheme, conservation laws, exact lattice moment identities, a dense
+matrix assembly of the immersed-boundary operator, and an FFT solve of the
+magnetic sweep's fixed point.  None of them needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_09370_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ------------------------------------------------------------ generator, N_mag
+
+def test_splitmix64_published_sequences():
+    for row in _golden_lines("splitmix64.txt"):
+        seed = int(row[0], 0)
+        state = seed
+        for want in row[1:]:
+            # the oracle takes the pre-increment state: output k uses seed + k*golden
+            assert oracle.splitmix64(state) == int(want, 0)
+            state = (state + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+
+
+def test_nmag_matches_paper_constants():
+    # Sec. V.G/V.H: N = ceil(6 eta) on a c_s^2 = c^2/3 lattice (D2Q5 here)
+    for eta, n in _golden_lines("nmag_paper.txt"):
+        eta, n = float(eta), int(n)
+        R = 10.0
+        p = W.hartmann_channel_2d(U0=0.05, diameter=2 * R, Rm=0.05 * R / eta, n_mag_cap=0)
+        d = oracle.derive(p)
+        assert d["eta"] == pytest.approx(eta, rel=1e-14)
+        assert d["n_mag"] == n
+
+
+def test_nmag_cap_and_workload_mapping():
+    d1 = oracle.derive(W.hartmann_channel_2d())
+    assert d1["n_mag"] == 465 and d1["tau"] == pytest.approx(0.7325)
+    d2 = oracle.derive(W.pipe_64x64x128())
+    # effective count of Sec. V.H: the sweep is capped at 270 iterations
+    assert d2["n_mag"] == 270 and d2["c_mag"] == pytest.approx(11200.0)
+    # dimensionless groups of Sec. II recovered from the lattice values
+    for p, d in ((W.hartmann_channel_2d(), d1), (W.pipe_64x64x128(), d2)):
+        assert d["U0"] * d["R"] / d["nu"] == pytest.approx(p["Re"], rel=1e-12)
+        assert d["U0"] * d["R"] / d["eta"] == pytest.approx(p["Rm"], rel=1e-12)
+        assert d["B0"] * d["R"] / math.sqrt(d["eta"] * d["nu"]) == pytest.approx(p["Ha"], rel=1e-12)
+
+
+# ------------------------------------------------------------------ IB kernel
+
+def test_kernel_reproduces_quadratics():
+    # The pieces of the Lagrange kernel (Sec. V.B) make three-point Lagrange
+    # interpolation: it reproduces 1, X and X^2 exactly for every X.
+    rng = np.random.default_rng(1)
+    for X in np.concatenate([rng.uniform(-3, 3, 200), [0.0, 0.5, -0.5, 1.5, 2.25]]):
+        nodes = np.arange(math.floor(X) - 3, math.floor(X) + 4)
+        w = np.array([oracle.kernel1d(n - X) for n in nodes])
+        assert np.count_nonzero(w) <= 3
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+        assert (w * nodes).sum() == pytest.approx(X, abs=1e-13)
+        assert (w * nodes ** 2).sum() == pytest.approx(X * X, abs=1e-12)
+    assert oracle.kernel1d(0.0) == 1.0
+    assert oracle.kernel1d(1.0) == 0.0 and oracle.kernel1d(-1.0) == 0.0
+    assert oracle.kernel1d(1.6) == 0.0 and oracle.kernel1d(-1.6) == 0.0
+
+
+def _dense_D(o, p):
+    """Interpolation matrix D (markers x nodes) assembled from the kernel."""
+    m = o.markers()
+    nx, ny = p["nx"], p["ny"]
+    nz = p.get("nz", 1) if p.get("dim", 3) == 3 else 1
+    D = np.zeros((len(m["X"]), nx * ny * nz))
+    for j, (X, Y, Z) in enumerate(zip(m["X"], m["Y"], m["Z"])):
+        zr = range(int(math.floor(Z)) - 2, int(math.floor(Z)) + 3) if p.get("dim", 3) == 3 else [0]
+        for kz in zr:
+            wz = oracle.kernel1d(kz - Z) if p.get("dim", 3) == 3 else 1.0
+            for ky in range(int(math.floor(Y)) - 2, int(math.floor(Y)) + 3):
+                for kx in range(int(math.floor(X)) - 2, int(math.floor(X)) + 3):
+                    w = oracle.kernel1d(kx - X) * oracle.kernel1d(ky - Y) * wz
+                    if w != 0.0:
+                        D[j, ((kz % nz) * ny + ky % ny) * nx + kx % nx] += w
+    return D
+
+
+@pytest.mark.parametrize("case", ["pipe", "channel_offgrid"])
+def test_ib_diagonal_matches_dense_assembly(case):
+    if case == "pipe":
+        p = W.small_pipe(nx=16, ny=16, nz=2, diameter=10.0)
+    else:
+        p = W.hartmann_channel_2d(nx=16, ny=12, diameter=8.6, marker_spacing=0.8)
+    o = oracle.Oracle(p)
+    D = _dense_D(o, p)
+    A = D @ D.T  # Sec. V.B: A = D D^T
+    d_dense = A.sum(axis=1)  # Sec. V.C: d_i = sum_j A_ij
+    m = o.markers()
+    np.testing.assert_allclose(m["d"], d_dense, rtol=1e-13, atol=1e-14)
+    lam = o.derived()["lambda"]
+    np.testing.assert_allclose(m["s"], lam / (d_dense * (1 + d_dense * (lam - 1))), rtol=1e-13)
+
+
+def test_ib_on_node_wall_has_unit_scaling_for_any_lambda():
+    # Flat walls on nodes: A = I, d = 1, and lambda/(d(1+d(lambda-1))) = 1.
+    for nu_ref in (0.0, 0.02, 1.0 / 6.0, 0.5):
+        o = oracle.Oracle(W.hartmann_channel_2d(nu_ref=nu_ref))
+        m = o.markers()
+        assert len(m["d"]) == 128
+        np.testing.assert_array_equal(m["d"], 1.0)
+        np.testing.assert_allclose(m["s"], 1.0, rtol=1e-14)
+        np.testing.assert_allclose(m["sm"], 1.0, rtol=1e-14)
+
+
+def test_explicit_ib_equals_implicit_solve_when_A_is_diagonal():
+    # Walls off the nodes in y but on them in x: supports do not overlap, A is
+    # diagonal, and the explicit corrector equals u* - D^T A^{-1} D u*.
+    p = W.hartmann_channel_2d(nx=16, ny=12, diameter=8.6)
+    o = oracle.Oracle(p)
+    D = _dense_D(o, p)
+    A = D @ D.T
+    assert np.allclose(A, np.diag(np.diag(A)))
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=(3, D.shape[1]))
+    implicit = f - (D.T @ np.linalg.solve(A, D @ f.T)).T
+    explicit = o.ib_apply(f.reshape(3, 1, 12, 16), magnetic=False).reshape(3, -1)
+    np.testing.assert_allclose(explicit, implicit, rtol=1e-12, atol=1e-13)
+    # and the corrected field interpolates to the wall value (zero) exactly
+    np.testing.assert_allclose(D @ explicit.T, 0.0, atol=1e-12)
+
+
+def test_explicit_ib_close_to_implicit_on_curved_wall():
+    # Sec. V.C: the lumped corrector approximates the implicit solve; the
+    # interpolated wall velocity after one correction is a small fraction of
+    # the uncorrected one for a smooth field.
+    p = W.small_pipe(nx=24, ny=24, nz=1, diameter=16.0)
+    o = oracle.Oracle(p)
+    D = _dense_D(o, p)
+    y, x = np.mgrid[0:24, 0:24]
+    f = np.zeros((3, 1, 24, 24))
+    f[2, 0] = 1.0 + 0.01 * x
+    before = np.abs(D @ f.reshape(3, -1)[2]).max()
+    after = np.abs(D @ o.ib_apply(f, magnetic=False).reshape(3, -1)[2]).max()
+    assert after < 0.5 * before
+
+
+# ------------------------------------------------------------ forcing moments
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gzs_moments(dim):
+    # Sec. V.A: sum F_i = 0, sum c_i F_i = (1-1/2tau) F,
+    # sum c_i c_i F_i = (1-1/2tau)(u F + F u), exactly on the lattice.
+    rng = np.random.default_rng(7 + dim)
+    for _ in range(20):
+        tau = rng.uniform(0.51, 1.0)
+        u = rng.uniform(-0.1, 0.1, 3)
+        F = rng.uniform(-1e-3, 1e-3, 3)
+        if dim == 2:
+            u[2] = F[2] = 0.0
+        Fi, c = oracle.gzs_terms(dim, tau, u, F)
+        k = 1 - 1 / (2 * tau)
+        assert abs(Fi.sum()) < 1e-18
+        np.testing.assert_allclose(c.T @ Fi, k * F, rtol=1e-12, atol=1e-19)
+        second = np.einsum("ia,ib,i->ab", c, c, Fi)
+        np.testing.assert_allclose(second, k * (np.outer(u, F) + np.outer(F, u)), rtol=1e-11, atol=1e-19)
+
+
+# --------------------------------------------------- closed forms of the scheme
+
+def test_channel_shear_mode_decays_at_discrete_rate():
+    # Ha = 0 channel, walls on nodes y = 0, 31 (Sec. III.C update): for a
+    # unidirectional u_x(y) the update reduces to u <- u + nu lap_h u + F, so
+    # the parabola F y (31 - y)/(2 nu) is steady and the mode sin(pi y/31)
+    # decays by exactly 1 - 4 nu sin^2(pi/62) per step.
+    p = W.hartmann_channel_2d(Ha=0.0, n_mag=1)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    nu, F = d["nu"], d["F0"]
+    y = np.arange(32, dtype=float)
+    parab = F * y * (31 - y) / (2 * nu)
+    assert parab.max() == pytest.approx(d["U0"], rel=2e-3)  # F0 maps Re to U0
+    eps = 1e-3
+    u = np.zeros((3, 1, 32, 64))
+    u[0, 0] = (parab + eps * np.sin(np.pi * y / 31))[:, None]
+    o.set_state(rho=np.ones((1, 32, 64)), u=u, b=np.zeros_like(u), t=0)
+    n = 400
+    o.step(n)
+    rho, uu, b = o.state()
+    g = (1 - 4 * nu * math.sin(math.pi / 62) ** 2) ** n
+    want = parab + eps * g * np.sin(np.pi * y / 31)
+    np.testing.assert_allclose(uu[0, 0], np.broadcast_to(want[:, None], (32, 64)), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+    np.testing.assert_allclose(uu[1], 0.0, atol=1e-15)
+
+
+def test_uniform_flow_gains_exactly_the_body_force():
+    # Uniform fields in a periodic box: every neighbour equilibrium equals the
+    # local one, the discrete-effect correction vanishes and rho u gains F per
+    # step (Sec. V.A update); rho stays one.
+    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    u0 = np.array([0.01, -0.02, 0.005])
+    u = np.broadcast_to(u0[:, None, None, None], (3, 4, 5, 6)).copy()
+    o.set_state(rho=np.ones((4, 5, 6)), u=u, b=np.zeros_like(u), t=0)
+    o.step(40)
+    rho, uu, _ = o.state()
+    want = u0 + np.array([0.0, 0.0, 40 * d["F0"]])
+    for a in range(3):
+        np.testing.assert_allclose(uu[a], want[a], rtol=1e-13, atol=1e-17)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+
+
+def test_3d_shear_wave_exact_at_rest():
+    p = W.small_pipe(nx=8, ny=6, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    x = np.arange(8, dtype=float)
+    eps = 1e-3
+    u = np.zeros((3, 4, 6, 8))
+    u[2] = eps * np.sin(2 * np.pi * x / 8)
+    o.set_state(rho=np.ones((4, 6, 8)), u=u, b=np.zeros_like(u), t=0)
+    n = 50
+    o.step(n)
+    _, uu, _ = o.state()
+    g = (1 - 4 * d["nu"] * math.sin(math.pi / 8) ** 2) ** n
+    want = n * d["F0"] + eps * g * np.sin(2 * np.pi * x / 8)
+    np.testing.assert_allclose(uu[2], np.broadcast_to(want, (4, 6, 8)), rtol=0, atol=1e-15)
+
+
+def test_mass_conserved_to_roundoff():
+    # Sec. III.C density update: the coefficients 3/2 - 1 + 1/2 sum to one over
+    # a periodic box and the IB corrects velocity only.
+    o = oracle.Oracle(W.small_pipe(nx=16, ny=16, nz=6, diameter=10.0, n_mag=20, perturb=0.05))
+    o.step(15)
+    ob = o.observables()
+    assert abs(ob["mass_drift"]) < 1e-13
+    assert ob["nan_flag"] == 0
+
+
+# ------------------------------------------------------------ magnetic sweep
+
+def test_sweep_single_mode_amplification():
+    # With u = 0 one tau_m = 1 sweep multiplies a Fourier mode cos(k x) by
+    # sum_i w_i cos(k e_ix): 3/4 + cos(k)/4 on D3Q7, 2/3 + cos(k)/3 on D2Q5.
+    for dim, gain in ((3, lambda k: 0.75 + 0.25 * math.cos(k)), (2, lambda k: 2 / 3 + math.cos(k) / 3)):
+        if dim == 3:
+            p = W.small_pipe(nx=12, ny=4, nz=4, geometry="none", perturb=0.0)
+            shape = (4, 4, 12)
+        else:
+            p = W.hartmann_channel_2d(nx=12, ny=4, geometry="none")
+            shape = (1, 4, 12)
+        o = oracle.Oracle(p)
+        x = np.arange(12, dtype=float)
+        k = 2 * np.pi * 3 / 12
+        b = np.zeros((3,) + shape)
+        b[1] = 1e-3 * np.cos(k * x)
+        o.set_state(rho=np.ones(shape), u=np.zeros((3,) + shape), b=b, t=0)
+        o.mag_sweeps(1)
+        _, _, bb = o.state()
+        np.testing.assert_allclose(bb[1], gain(k) * b[1], rtol=0, atol=1e-17)
+
+
+def test_sweep_fixed_point_is_discrete_qs_poisson_solution():
+    # Sec. V.G: iterated to convergence the sweep solves
+    # eta lap b = div(u B^ext - B^ext u) (strict QS flux).  Compare with an FFT
+    # solve of the same discrete operators (7-point Laplacian, central
+    # divergence) on a periodic box without walls.
+    n = 12
+    p = W.small_pipe(nx=n, ny=n, nz=n, geometry="none", diameter=10.0, Re=10.0, Ha=5.0, Rm=0.05,
+                     U0=0.05, strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    eta = d["eta"]
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    t = 2 * np.pi / n
+    u = np.stack([0.02 * np.sin(t * y) * np.cos(t * z), 0.03 * np.cos(t * x + 2 * t * z),
+                  0.01 * np.sin(t * x + t * y)])
+    o.set_state(rho=np.ones((n, n, n)), u=u, b=np.zeros_like(u), t=0)
+    o.mag_sweeps(3000)
+    _, _, b = o.state()
+    Be = d["B0"] * np.array([0.6, 0.8, 0.0])
+    k = [np.fft.fftfreq(n) * 2 * np.pi] * 3
+    kz, ky, kx = np.meshgrid(*k, indexing="ij")
+    K = (kx, ky, kz)  # axis index 0 = x
+    lap = sum(2 * np.cos(kk) - 2 for kk in K)
+    lap[0, 0, 0] = 1.0
+    uh = [np.fft.fftn(u[a]) for a in range(3)]
+    for a in range(3):
+        rhs = np.zeros((n, n, n), dtype=complex)
+        for be in range(3):
+            phi = uh[be] * Be[a] - uh[a] * Be[be]
+            rhs += 1j * np.sin(K[be]) * phi
+        bh = rhs / (eta * lap)
+        bh[0, 0, 0] = 0.0
+        want = np.fft.ifftn(bh).real
+        np.testing.assert_allclose(b[a], want, rtol=0, atol=1e-10 * np.abs(want).max() + 1e-18)
+    # at the fixed point the QS residual of the observables vanishes
+    assert o.observables()["qs_residual"] < 1e-9 * np.abs(u).max() * np.abs(Be).max()
+
+
+# --------------------------------------------------- converged physical flows
+
+@pytest.fixture(scope="module")
+def hartmann_state():
+    # Converged 2-D Hartmann channel (the 64x32 workload).  N_mag = 40 instead
+    # of 465 changes only the transient: at steady state each sweep sits at its
+    # fixed point whatever the sub-iteration count.
+    p = W.hartmann_channel_2d(n_mag=40)
+    o = oracle.Oracle(p)
+    o.step(2500)
+    return o, p
+
+
+@pytest.mark.slow
+def test_hartmann_profiles_match_closed_form(hartmann_state):
+    o, p = hartmann_state
+    d = o.derived()
+    _, u, b = o.state()
+    a, Ha, F, B0 = d["R"], p["Ha"], d["F0"], d["B0"]
+    y = np.arange(32, dtype=float) - 15.5
+    k = Ha / a
+    u_exact = F * a * a / (d["nu"] * Ha) * (math.cosh(Ha) - np.cosh(k * y)) / math.sinh(Ha)
+    b_exact = F * a / B0 * (np.sinh(k * y) / math.sinh(Ha) - y / a)
+    ux = u[0, 0, :, 0]
+    bx = b[0, 0, :, 0]
+    assert np.ptp(u[0, 0], axis=1).max() < 1e-15  # streamwise invariant
+    eu = np.linalg.norm(ux - u_exact) / np.linalg.norm(u_exact)
+    eb = np.linalg.norm(bx - b_exact) / np.linalg.norm(b_exact)
+    assert eu < 1.5e-2, eu  # measured 6.0e-3 at 64x32
+    assert eb < 3e-2, eb  # measured 1.24e-2
+
+
+@pytest.mark.slow
+def test_hartmann_steady_energy_balance(hartmann_state):
+    # Eq. "Energy balance equations" at steady state: pumping = viscous + Joule.
+    o, _ = hartmann_state
+    o.observables()
+    o.step(100)
+    ob = o.observables()
+    P, V, J = ob["pump"], ob["visc"], ob["joule"]
+    assert P > 0 and V > 0 and J > 0
+    assert abs(P - V - J) / P < 2e-2
+    assert ob["steady_residual"] < 5e-6
+
+
+@pytest.mark.slow
+def test_pipe_poiseuille_at_zero_hartmann():
+    # Ha -> 0: u_z(r) = F (R^2 - r^2)/(4 nu) up to the IB wall error, which
+    # falls as the pipe is refined (first order in 1/R).
+    errs = []
+    for D, box in ((16, 24), (24, 32)):
+        p = W.small_pipe(nx=box, ny=box, nz=2, diameter=float(D), Re=10.0, Ha=0.0, n_mag=1, perturb=0.0)
+        o = oracle.Oracle(p)
+        d = o.derived()
+        R, nu, F = d["R"], d["nu"], d["F0"]
+        o.step(int(6 * R * R / nu))
+        _, u, _ = o.state()
+        yy, xx = np.mgrid[0:box, 0:box]
+        r = np.hypot(xx - (box - 1) / 2, yy - (box - 1) / 2)
+        ex = F * (R * R - r * r) / (4 * nu)
+        msk = r <= R - 1
+        errs.append(np.linalg.norm((u[2, 0] - ex)[msk]) / np.linalg.norm(ex[msk]))
+    assert errs[1] < errs[0] < 8e-2, errs
+    assert errs[1] < 5e-2, errs
