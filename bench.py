@@ -1,0 +1,308 @@
+"""Benchmark: flow steps of the 64x64x128 pipe (D3Q19 + D3Q7, FP32, N_mag = 270).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step is the whole per-time-step hot path: 270 magnetic sweeps each followed
+by the IB corrector on b, the Lorentz/body force, the single-step flow update
+with the discrete-effect correction, and the IB corrector on u, over all
+524,288 nodes.  The metric is MLUPS (node flow-updates per second).  Inputs are
+resident in HBM when timing starts; L2 is flushed (a 256 MB device write)
+before every timed step, since the working set (~45 MB) fits in L2.
+
+With N > 1 GPUs (torchrun) every rank advances its own independent pipe
+(replicas; there is no exchange step) and value = all ranks' node updates / the
+slowest rank's time.
+
+--impl reference times the CPU oracle on the host cores instead (a z-slab of 8
+planes of the same pipe per step, same cross-section and markers; the per-node
+work is the same as in the full pipe).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_09370_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS"
+WORKLOAD = "pipe_64x64x128 D3Q19+D3Q7 D=56 Re=100 Ha=20 Rm=1e-3 N_mag=270 (10k-step workload, per step)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2211_09370_gb300", "csrc", "qslbm_kernels.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha") != kernel_source_sha():
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    p = W.pipe_64x64x128(nz=8, precision="fp64")
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    o = oracle.Oracle(p)
+    for _ in range(args.warmup):
+        o.step(1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t
+    nodes = W.nodes(p)
+    value = nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "z-slab 64x64x8 of the same pipe", "nodes": nodes},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} flow steps of a 64x64x8 z-slab (N_mag=270) of the pipe"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on the host cores: one flow step of the full
+    64x64x128 pipe (about 10-30 s of CPU work)."""
+    import oracle
+
+    p = W.pipe_64x64x128(precision="fp64")
+    o = oracle.Oracle(p)
+    t = time.perf_counter()
+    o.step(1)
+    dt = time.perf_counter() - t
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": W.nodes(p) / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"1 flow step (N_mag=270) of the full 64x64x128 pipe in {dt:.1f}s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2211_09370_gb300 import _lib
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = W.pipe_64x64x128(seed=2211 + rank)
+    solver = _lib.Solver(p, stream=stream.cuda_stream)
+    n = solver.n
+    n_mag = solver.units["n_mag"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        solver.step(1)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        solver.step(1)
+        ev[i][1].record(stream)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    # dominant kernel: the fused sweep + IB-on-b kernel, timed over back-to-back launches
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.mag_sweeps(n_mag)
+    e1.record(stream)
+    barrier()
+    sweep_ms = e0.elapsed_time(e1) / n_mag
+    clk = clocks.stop()
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = ws * n * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the public call with host buffers (pinned), per step
+    o = solver.observables()
+    rho, u, b = solver.state()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).pin_memory()  # noqa: E731
+    h_rho, h_u, h_b = pin(rho), pin(u), pin(b)
+    o_rho, o_u, o_b = (torch.empty(k * n, dtype=torch.float64).pin_memory() for k in (1, 3, 3))
+    dp = lambda t: C.cast(t.data_ptr(), C.POINTER(C.c_double))  # noqa: E731
+    obs = _lib.qslbm_obs()
+    e2e_steps = max(3, min(args.steps, 20))
+    t_state = o["step"]
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        rc = solver.L.qslbm_step_host(solver.h, dp(h_rho), dp(h_u), dp(h_b), t_state, 1, dp(o_rho), dp(o_u),
+                                      dp(o_b), C.byref(obs))
+        _lib.check(rc, "qslbm_step_host")
+        h_rho, o_rho = o_rho, h_rho
+        h_u, o_u = o_u, h_u
+        h_b, o_b = o_b, h_b
+        t_state += 1
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t_e2e, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = ws * n * e2e_steps / float(t_e2e.item()) / 1e6
+    state_bytes = 7 * n * 8
+    obs_bytes = C.sizeof(_lib.qslbm_obs)
+
+    peak, peak_kind = peaks()
+    n_shell = int(solver.units["shell_nodes"])
+    alg_bytes = 36 * n + 24 * n_shell
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": n, "n_mag": n_mag, "precision": "fp32",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single",
+                   "l2": "flushed before every timed step (256 MB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "kernel": "k_sweep_ib<float,3> (sweep + IB on b, one z plane per CTA)",
+                     "bytes_per_launch": alg_bytes, "ms_per_launch": sweep_ms,
+                     "peak_kind": f"{peak_kind} (hbm_gbs)",
+                     "note": "working set is L2-resident within a step; achieved counts algorithmic bytes"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes + obs_bytes, "steps": e2e_steps},
+        "gpu_launches": args.steps * (n_mag + 2),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_sample()
+    solver.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

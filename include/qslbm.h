@@ -1,0 +1,182 @@
+/*
+ * qslbm: C ABI of a GB300 (sm_103a) implementation of the single-step
+ * simplified lattice Boltzmann method for quasi-static MHD pipe flow
+ * (H.S. Tavares, B. Magacho, L. Moriconi, J. Loureiro, arXiv 2211.09370).
+ *
+ * One flow step t -> t+1 runs, in the paper's order:
+ *   1. N_mag sweeps of the tau_m = 1 magnetic scheme (Sec. V.G, Eq. "Single step
+ *      algoritm for magnetic field") on the induced field b, with u frozen; each
+ *      sweep is followed by the explicit immersed-boundary corrector for b
+ *      (Sec. V.D, scaled as in Sec. V.F, Eq. "IB corrected for magnetic field").
+ *   2. The Lorentz force J x B with J = curl b by isotropic differences and the
+ *      body force (Sec. V.A, Eq. "variable force").
+ *   3. The single-step flow update with GZS forcing and the discrete-effect
+ *      correction (Sec. III.E Eq. "single-step algorithm complete" for rho,
+ *      Sec. V.A Eq. "Single-step algorithm with lattice discrete effect").
+ *   4. The explicit immersed-boundary corrector for u (Sec. V.C, scaled as in
+ *      Sec. V.E, Eq. "IBM correted for velocity field").
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 (QSLBM_OK) or a negative QSLBM_E* code; no exception or
+ *     signal crosses the ABI.  qslbm_strerror() names a code.
+ *   - Host pointers are caller-owned and are read or written before the call
+ *     returns.  Field arrays are binary64, layout [component][z][y][x] with x
+ *     fastest (rho has one component, u and b three).
+ *   - The library owns all device memory of a handle: it is allocated by
+ *     qslbm_create and released by qslbm_destroy.
+ *   - Work is queued on the CUDA stream given in the parameters (NULL = the
+ *     legacy default stream).  qslbm_step and qslbm_mag_sweeps return once the
+ *     work is queued; errors raised by device work surface at the next call
+ *     that synchronises (qslbm_observables, qslbm_get_state, qslbm_sync,
+ *     qslbm_destroy).
+ *   - A handle is not thread-safe; distinct handles may be used from distinct
+ *     threads.
+ *   - The device must be an sm_103 GPU; nothing falls back to the CPU.
+ */
+#ifndef QSLBM_H
+#define QSLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define QSLBM_OK 0
+#define QSLBM_EINVAL -1    /* invalid parameter or argument                    */
+#define QSLBM_ENOMEM -2    /* device or host allocation failed                 */
+#define QSLBM_ECUDA -3     /* a CUDA call failed (message: qslbm_last_error)   */
+#define QSLBM_EUNSTABLE -4 /* non-finite field value detected                  */
+#define QSLBM_ETIMEOUT -5  /* step cap reached before the stop tolerance       */
+#define QSLBM_EBUDGET -6   /* request does not fit the device-memory budget    */
+#define QSLBM_ENOTFOUND -7 /* unknown request id                               */
+#define QSLBM_EARCH -8     /* device is not sm_103                             */
+
+#define QSLBM_CHANNEL 0  /* two flat walls y = cy -/+ D/2, markers on x        */
+#define QSLBM_PIPE 1     /* circular pipe of diameter D along z (x in 2-D)    */
+#define QSLBM_PERIODIC 2 /* periodic box without walls                        */
+
+#define QSLBM_B0_UNIFORM 0 /* B^ext = B0 * b0_dir                              */
+#define QSLBM_B0_TANH 1    /* B^ext = B0 * 0.5 (1 + tanh((z - zc)/w)) * b0_dir  */
+
+#define QSLBM_FP32 0
+#define QSLBM_FP64 1
+
+/* Problem statement of the paper (Sec. II: Re, Rm, Ha with L = pipe radius;
+ * Sec. IV: pipe, insulating walls, pressure gradient; Sec. VI: non-uniform
+ * applied field).  qslbm_params_init fills the defaults noted here. */
+typedef struct qslbm_params {
+    int32_t dim;            /* 2 (D2Q9 + D2Q5) or 3 (D3Q19 + D3Q7); default 3      */
+    int32_t nx, ny, nz;     /* periodic box in lattice nodes; 2-D uses nz = 1      */
+    int32_t geometry;       /* QSLBM_CHANNEL | QSLBM_PIPE | QSLBM_PERIODIC         */
+    double diameter;        /* pipe diameter / wall distance D, lattice units      */
+    double center[2];       /* wall centre (x, y); NaN = ((nx-1)/2, (ny-1)/2)      */
+    double marker_spacing;  /* Lagrangian marker spacing; default 1.0              */
+    double Re, Ha, Rm;      /* L = D/2; Ha = B0 L / sqrt(eta nu)                   */
+    double U0;              /* velocity scale; 0 = min(0.05, Re/(6L), Re L/(2Ha^2)) */
+    int32_t b0_kind;        /* QSLBM_B0_UNIFORM | QSLBM_B0_TANH                    */
+    double b0_dir[3];       /* unit direction of B^ext; default (1, 0, 0)          */
+    double ramp_center;     /* zc of the tanh ramp                                 */
+    double ramp_width;      /* w of the tanh ramp                                  */
+    double force_amp;       /* F(t) = F0 (1 + amp sin(2 pi t / period)); 0 = const */
+    double force_period;    /* period T in flow steps                              */
+    int32_t n_mag;          /* sweeps per step; 0 = min(ceil(2 eta / c_m^2), cap)  */
+    int32_t n_mag_cap;      /* cap for the automatic count; <= 0 = no cap; 270     */
+    double nu_ref;          /* IB reference viscosity; 0 = nu (lambda = 1)         */
+    double eta_ref;         /* IB reference resistivity; 0 = c_m^2 / 2             */
+    int32_t precision;      /* QSLBM_FP32 (default) | QSLBM_FP64                   */
+    int32_t strict_qs;      /* 1: induction flux from B^ext only; default 0        */
+    uint64_t seed;          /* initial perturbation seed                           */
+    double perturb;         /* initial |u| noise, fraction of U0, inside the wall  */
+    void* stream;           /* cudaStream_t to queue work on, or NULL              */
+} qslbm_params;
+
+/* Lattice-unit values the parameters map to (lambda = nu/nu_ref,
+ * lambda_m = eta/eta_ref, c_mag = 2 eta / c_m^2). */
+typedef struct qslbm_units {
+    double R, U0, nu, tau, eta, B0, F0, c_mag, lambda, lambda_m, cs2, cm2;
+    int32_t n_mag, n_markers;
+    int64_t nodes;
+    int64_t device_bytes; /* device memory the handle holds */
+    int64_t shell_nodes;  /* nodes inside the support of some wall marker */
+} qslbm_units;
+
+/* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2
+ * decay"), accumulated in binary64 on the device.  Averages run over the
+ * nodes at least two lattice units inside the wall. */
+typedef struct qslbm_obs {
+    int64_t step;           /* flow steps taken                                   */
+    double mass;            /* sum of rho over the box                            */
+    double mass_drift;      /* (mass - initial mass) / initial mass               */
+    double E_k, E_m;        /* <rho |u|^2 / 2>, <|B^ext + b|^2 / 2>               */
+    double pump;            /* <F_body . u>                                       */
+    double visc;            /* -nu <u . lap u>                                    */
+    double joule;           /* -<u . (J x B)>                                     */
+    double qs_residual;     /* RMS of eta lap b - div(u B - B u)                  */
+    double steady_residual; /* |u - u_prev| / ((t - t_prev) |u|), u_prev from the
+                               previous qslbm_observables call                    */
+    int32_t nan_flag;       /* 1 if any field value is not finite                 */
+} qslbm_obs;
+
+typedef struct qslbm_handle qslbm_handle;
+
+/* Fill *p with the defaults listed in qslbm_params. */
+void qslbm_params_init(qslbm_params* p);
+
+/* Validate *p, map it to lattice units (Sec. II groups; U0 rule above), build
+ * the wall markers and their IB weights d_j, s_j, s^m_j (Sec. V.C, V.E, V.F),
+ * allocate the fields on the current CUDA device and initialise rho = 1,
+ * b = 0 and u = seeded splitmix64 noise of size perturb * U0 inside the wall.
+ * *p is copied.  On success *out owns the handle.
+ * Errors: QSLBM_EINVAL (bad parameters, wall outside the box, markers not on
+ * integer z planes), QSLBM_ENOMEM, QSLBM_ECUDA, QSLBM_EARCH. */
+int qslbm_create(const qslbm_params* p, qslbm_handle** out);
+
+/* Lattice-unit values of the handle.  Errors: QSLBM_EINVAL (NULL argument). */
+int qslbm_get_units(const qslbm_handle* h, qslbm_units* out);
+
+/* Queue nsteps >= 0 flow steps (N_mag sweeps + IB on b each, force, flow
+ * update, IB on u).  Asynchronous.  Errors: QSLBM_EINVAL, QSLBM_ECUDA. */
+int qslbm_step(qslbm_handle* h, int64_t nsteps);
+
+/* Queue nsweeps >= 0 magnetic sweeps (each followed by the IB corrector on b)
+ * with u frozen; t does not advance.  Asynchronous. */
+int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps);
+
+/* Synchronise the handle's stream and compute the diagnostics into *out
+ * (nullable).  rho [n], u [3n], b [3n] (each nullable) receive the fields in
+ * binary64.  Errors: QSLBM_EINVAL, QSLBM_ECUDA, QSLBM_EUNSTABLE (the fields
+ * hold a non-finite value; *out is still filled). */
+int qslbm_observables(qslbm_handle* h, qslbm_obs* out, double* rho, double* u, double* b);
+
+/* Copy the state out / in (binary64 host arrays as above; any may be NULL to
+ * leave that field alone).  set_state also sets the step counter to t and
+ * makes the uploaded velocity the reference of the steady residual.
+ * Synchronous.  Errors: QSLBM_EINVAL, QSLBM_ECUDA. */
+int qslbm_get_state(qslbm_handle* h, double* rho, double* u, double* b, int64_t* t);
+int qslbm_set_state(qslbm_handle* h, const double* rho, const double* u, const double* b, int64_t t);
+
+/* End-to-end step from and to host memory: upload the state (as set_state),
+ * run nsteps flow steps, compute the diagnostics and download the state.
+ * rho_in/u_in/b_in and rho_out/u_out/b_out follow the field layout above; the
+ * outputs and *obs are nullable. */
+int qslbm_step_host(qslbm_handle* h, const double* rho_in, const double* u_in, const double* b_in,
+                    int64_t t_in, int64_t nsteps, double* rho_out, double* u_out, double* b_out,
+                    qslbm_obs* obs);
+
+/* Wait for all queued work of the handle.  Errors: QSLBM_ECUDA. */
+int qslbm_sync(qslbm_handle* h);
+
+/* Release the handle and its device memory (synchronises first). */
+int qslbm_destroy(qslbm_handle* h);
+
+/* Static string for a code, and the text of the last CUDA error seen by the
+ * calling thread (empty if none). */
+const char* qslbm_strerror(int code);
+const char* qslbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSLBM_H */

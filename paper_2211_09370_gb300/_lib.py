@@ -1,0 +1,227 @@
+"""ctypes binding of the qslbm C ABI (include/qslbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The functions keep the C names (``qslbm_create``, ``qslbm_step``, ...); the
+``Solver`` class is a thin convenience over them.  Loading fails loudly if the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUDGET, ENOTFOUND, EARCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
+CHANNEL, PIPE, PERIODIC = 0, 1, 2
+B0_UNIFORM, B0_TANH = 0, 1
+FP32, FP64 = 0, 1
+GEOMETRY = {"channel": CHANNEL, "pipe": PIPE, "none": PERIODIC, "periodic": PERIODIC}
+B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH}
+PRECISION = {"fp32": FP32, "fp64": FP64}
+
+
+class qslbm_params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("geometry", C.c_int32),
+        ("diameter", C.c_double), ("center", C.c_double * 2), ("marker_spacing", C.c_double),
+        ("Re", C.c_double), ("Ha", C.c_double), ("Rm", C.c_double), ("U0", C.c_double),
+        ("b0_kind", C.c_int32), ("b0_dir", C.c_double * 3), ("ramp_center", C.c_double),
+        ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
+        ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
+        ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
+        ("stream", C.c_void_p),
+    ]
+
+
+class qslbm_units(C.Structure):
+    _fields_ = [(k, C.c_double) for k in
+                ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
+    _fields_ += [("n_mag", C.c_int32), ("n_markers", C.c_int32), ("nodes", C.c_int64), ("device_bytes", C.c_int64),
+                ("shell_nodes", C.c_int64)]
+
+
+class qslbm_obs(C.Structure):
+    _fields_ = [("step", C.c_int64)] + [(k, C.c_double) for k in (
+        "mass", "mass_drift", "E_k", "E_m", "pump", "visc", "joule", "qs_residual", "steady_residual")] + [
+        ("nan_flag", C.c_int32)]
+
+
+# every symbol the header declares (checked by the CPU test-suite)
+EXPORTS = ("qslbm_params_init", "qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps",
+           "qslbm_observables", "qslbm_get_state", "qslbm_set_state", "qslbm_step_host", "qslbm_sync",
+           "qslbm_destroy", "qslbm_strerror", "qslbm_last_error")
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libqslbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    hp = C.c_void_p
+    L.qslbm_params_init.argtypes = [C.POINTER(qslbm_params)]
+    L.qslbm_params_init.restype = None
+    L.qslbm_create.argtypes = [C.POINTER(qslbm_params), C.POINTER(hp)]
+    L.qslbm_get_units.argtypes = [hp, C.POINTER(qslbm_units)]
+    L.qslbm_step.argtypes = [hp, C.c_int64]
+    L.qslbm_mag_sweeps.argtypes = [hp, C.c_int32]
+    L.qslbm_observables.argtypes = [hp, C.POINTER(qslbm_obs), dp, dp, dp]
+    L.qslbm_get_state.argtypes = [hp, dp, dp, dp, C.POINTER(C.c_int64)]
+    L.qslbm_set_state.argtypes = [hp, dp, dp, dp, C.c_int64]
+    L.qslbm_step_host.argtypes = [hp, dp, dp, dp, C.c_int64, C.c_int64, dp, dp, dp, C.POINTER(qslbm_obs)]
+    L.qslbm_sync.argtypes = [hp]
+    L.qslbm_destroy.argtypes = [hp]
+    L.qslbm_strerror.argtypes = [C.c_int]
+    L.qslbm_strerror.restype = C.c_char_p
+    L.qslbm_last_error.argtypes = []
+    L.qslbm_last_error.restype = C.c_char_p
+    for name in ("qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps", "qslbm_observables",
+                 "qslbm_get_state", "qslbm_set_state", "qslbm_step_host", "qslbm_sync", "qslbm_destroy"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+class QSLBMError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        L = load()
+        msg = L.qslbm_strerror(code).decode()
+        last = L.qslbm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code})" + (f": {last}" if last else ""))
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code != OK:
+        raise QSLBMError(code, where)
+    return code
+
+
+def make_params(p: dict, stream: int | None = None) -> qslbm_params:
+    """Fill the C parameter struct from a workload dictionary."""
+    q = qslbm_params()
+    load().qslbm_params_init(C.byref(q))
+    q.dim = int(p.get("dim", 3))
+    q.nx, q.ny = int(p["nx"]), int(p["ny"])
+    q.nz = int(p.get("nz", 1)) if q.dim == 3 else 1
+    g = p.get("geometry", "pipe")
+    q.geometry = GEOMETRY[g] if isinstance(g, str) else int(g)
+    q.diameter = float(p["diameter"])
+    c = p.get("center") or (math.nan, math.nan)
+    q.center[0], q.center[1] = float(c[0]), float(c[1])
+    q.marker_spacing = float(p.get("marker_spacing", 1.0))
+    q.Re, q.Ha, q.Rm = float(p["Re"]), float(p["Ha"]), float(p["Rm"])
+    q.U0 = float(p.get("U0", 0.0))
+    k = p.get("b0_kind", "uniform")
+    q.b0_kind = B0_KIND[k] if isinstance(k, str) else int(k)
+    d = p.get("b0_dir", (1.0, 0.0, 0.0))
+    for i in range(3):
+        q.b0_dir[i] = float(d[i])
+    q.ramp_center = float(p.get("ramp_center", 0.0))
+    q.ramp_width = float(p.get("ramp_width", 1.0))
+    q.force_amp = float(p.get("force_amp", 0.0))
+    q.force_period = float(p.get("force_period", 0.0))
+    q.n_mag = int(p.get("n_mag", 0))
+    q.n_mag_cap = int(p.get("n_mag_cap", 270))
+    q.nu_ref = float(p.get("nu_ref", 0.0))
+    q.eta_ref = float(p.get("eta_ref", 0.0))
+    pr = p.get("precision", "fp32")
+    q.precision = PRECISION[pr] if isinstance(pr, str) else int(pr)
+    q.strict_qs = int(p.get("strict_qs", 0))
+    q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
+    q.perturb = float(p.get("perturb", 0.0))
+    q.stream = stream
+    return q
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+OBS_KEYS = ("step", "mass", "mass_drift", "E_k", "E_m", "pump", "visc", "joule", "qs_residual",
+            "steady_residual", "nan_flag")
+
+
+def obs_dict(o: qslbm_obs) -> dict:
+    return {k: getattr(o, k) for k in OBS_KEYS}
+
+
+class Solver:
+    """One simulated pipe (or channel) held on the GPU by the C library."""
+
+    def __init__(self, params: dict, stream: int | None = None):
+        self.L = load()
+        self.params = dict(params)
+        self._q = make_params(params, stream)
+        h = C.c_void_p()
+        check(self.L.qslbm_create(C.byref(self._q), C.byref(h)), "qslbm_create")
+        self.h = h
+        u = qslbm_units()
+        check(self.L.qslbm_get_units(self.h, C.byref(u)), "qslbm_get_units")
+        self.units = {k: getattr(u, k) for k, _ in qslbm_units._fields_}
+        self.units["lambda"] = self.units.pop("lambda_")
+        self.n = int(u.nodes)
+        self.shape = (self._q.nz, self._q.ny, self._q.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qslbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n: int = 1):
+        check(self.L.qslbm_step(self.h, int(n)), "qslbm_step")
+
+    def mag_sweeps(self, n: int):
+        check(self.L.qslbm_mag_sweeps(self.h, int(n)), "qslbm_mag_sweeps")
+
+    def sync(self):
+        check(self.L.qslbm_sync(self.h), "qslbm_sync")
+
+    def observables(self, fields: bool = False, allow_unstable: bool = False):
+        o = qslbm_obs()
+        rho = u = b = None
+        if fields:
+            rho, u, b = np.empty(self.n), np.empty(3 * self.n), np.empty(3 * self.n)
+        rc = self.L.qslbm_observables(self.h, C.byref(o), _dptr(rho), _dptr(u), _dptr(b))
+        if not (allow_unstable and rc == EUNSTABLE):
+            check(rc, "qslbm_observables")
+        d = obs_dict(o)
+        if fields:
+            return d, (rho.reshape(self.shape), u.reshape((3,) + self.shape), b.reshape((3,) + self.shape))
+        return d
+
+    def state(self):
+        rho, u, b = np.empty(self.n), np.empty(3 * self.n), np.empty(3 * self.n)
+        t = C.c_int64()
+        check(self.L.qslbm_get_state(self.h, _dptr(rho), _dptr(u), _dptr(b), C.byref(t)), "qslbm_get_state")
+        return rho.reshape(self.shape), u.reshape((3,) + self.shape), b.reshape((3,) + self.shape)
+
+    @property
+    def t(self) -> int:
+        t = C.c_int64()
+        check(self.L.qslbm_get_state(self.h, None, None, None, C.byref(t)), "qslbm_get_state")
+        return t.value
+
+    def set_state(self, rho=None, u=None, b=None, t: int = 0):
+        a = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (rho, u, b)]
+        check(self.L.qslbm_set_state(self.h, _dptr(a[0]), _dptr(a[1]), _dptr(a[2]), int(t)), "qslbm_set_state")

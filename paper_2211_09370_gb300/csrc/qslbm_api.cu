@@ -1,0 +1,636 @@
+// qslbm C ABI: parameter mapping, wall markers and IB weights, device memory,
+// CUDA-graph stepping, diagnostics and state transfer.  See include/qslbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qslbm.h"
+#include "qslbm_internal.h"
+
+using qslbm::State;
+
+struct qslbm_handle {
+    State s;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return QSLBM_ECUDA;
+}
+
+#define QCHK(call)                                      \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+const qslbm::Ops& ops(const State& s) {
+    return s.p.precision == QSLBM_FP64 ? qslbm::ops_f64() : qslbm::ops_f32();
+}
+
+int dev_alloc(State& s, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cuda_fail(e, "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? QSLBM_ENOMEM : QSLBM_ECUDA;
+    }
+    s.allocations.push_back(*p);
+    s.device_bytes += (long long)bytes;
+    return QSLBM_OK;
+}
+
+template <typename V>
+int upload(State& s, void** dst, const std::vector<V>& v) {
+    size_t bytes = std::max<size_t>(1, v.size()) * sizeof(V);
+    int rc = dev_alloc(s, dst, bytes);
+    if (rc) return rc;
+    if (!v.empty()) QCHK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return QSLBM_OK;
+}
+
+// Upload a binary64 host vector in the handle's storage precision.
+int upload_real(State& s, void** dst, const std::vector<double>& v) {
+    if (s.p.precision == QSLBM_FP64) return upload(s, dst, v);
+    std::vector<float> f(v.begin(), v.end());
+    return upload(s, dst, f);
+}
+
+// N_mag = ceil(c) with c = 2 eta / c_m^2 (Sec. V.G); a c within a relative
+// 1e-12 of an integer counts as that integer.
+int ceil_rel(double v) {
+    double r = std::nearbyint(v);
+    if (std::fabs(v - r) <= 1e-12 * std::fabs(v)) return (int)r;
+    return (int)std::ceil(v);
+}
+
+// Map the problem statement to lattice units.  L = D/2 (Sec. II groups with the
+// pipe radius as length, Sec. IV); U0 rule: Mach, tau <= 1 and an explicit
+// Lorentz drag B0^2/eta <= 1/2 per step.
+int map_units(const qslbm_params& p, qslbm_units& u) {
+    std::memset(&u, 0, sizeof(u));
+    u.cs2 = 1.0 / 3.0;
+    u.cm2 = p.dim == 2 ? 1.0 / 3.0 : 1.0 / 4.0;
+    u.R = 0.5 * p.diameter;
+    double U0 = p.U0;
+    if (!(U0 > 0)) {
+        U0 = 0.05;
+        U0 = std::min(U0, p.Re * u.cs2 / (2.0 * u.R));
+        if (p.Ha > 0) U0 = std::min(U0, p.Re * u.R / (2.0 * p.Ha * p.Ha));
+    }
+    u.U0 = U0;
+    u.nu = U0 * u.R / p.Re;
+    u.tau = u.nu / u.cs2 + 0.5;
+    u.eta = U0 * u.R / p.Rm;
+    u.B0 = p.Ha * std::sqrt(u.eta * u.nu) / u.R;
+    u.F0 = (p.geometry == QSLBM_CHANNEL ? 2.0 : 4.0) * u.nu * U0 / (u.R * u.R);
+    u.c_mag = 2.0 * u.eta / u.cm2;
+    int n = p.n_mag > 0 ? p.n_mag : ceil_rel(u.c_mag);
+    if (p.n_mag <= 0 && p.n_mag_cap > 0) n = std::min(n, p.n_mag_cap);
+    u.n_mag = std::max(n, 1);
+    double nu_ref = p.nu_ref > 0 ? p.nu_ref : u.nu;
+    double eta_ref = p.eta_ref > 0 ? p.eta_ref : 0.5 * u.cm2;
+    u.lambda = u.nu / nu_ref;
+    u.lambda_m = u.eta / eta_ref;
+    return QSLBM_OK;
+}
+
+int validate(const qslbm_params& p) {
+    if (p.dim != 2 && p.dim != 3) return QSLBM_EINVAL;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return QSLBM_EINVAL;
+    if (p.dim == 2 && p.nz != 1) return QSLBM_EINVAL;
+    if (p.geometry < QSLBM_CHANNEL || p.geometry > QSLBM_PERIODIC) return QSLBM_EINVAL;
+    if (!(p.diameter > 0) || !(p.Re > 0) || !(p.Rm > 0) || !(p.Ha >= 0)) return QSLBM_EINVAL;
+    if (!(p.marker_spacing > 0)) return QSLBM_EINVAL;
+    if (p.b0_kind != QSLBM_B0_UNIFORM && p.b0_kind != QSLBM_B0_TANH) return QSLBM_EINVAL;
+    if (p.b0_kind == QSLBM_B0_TANH && !(p.ramp_width > 0)) return QSLBM_EINVAL;
+    if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
+    if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
+    if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
+    long long n = (long long)p.nx * p.ny * p.nz;
+    if (n > (1LL << 31) - 1) return QSLBM_EINVAL;
+    return QSLBM_OK;
+}
+
+// Base node and 1-D weights of the Lagrange kernel (Sec. V.B) for coordinate
+// X: n0 is the node with n0 - X in (-1/2, 1/2]; the weights of n0 - 1, n0,
+// n0 + 1 are r(r+1)/2, 1 - r^2, r(r-1)/2 with r = n0 - X.
+void kernel_weights(double X, int& n0, double w[3]) {
+    long long k = (long long)std::floor(X + 0.5);
+    double r = (double)k - X;
+    if (r > 0.5) {
+        --k;
+        r = (double)k - X;
+    } else if (r <= -0.5) {
+        ++k;
+        r = (double)k - X;
+    }
+    n0 = (int)k;
+    w[0] = 0.5 * r * (r + 1.0);
+    w[1] = 1.0 - r * r;
+    w[2] = 0.5 * r * (r - 1.0);
+}
+
+int wrapn(long long i, int n) {
+    long long r = i % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+// Markers: channel walls y = cy -/+ D/2 with one marker per spacing along x on
+// every z plane; pipe rings of round(pi D / spacing) markers at every integer
+// z (Sec. V.B, Fig. 3).  Then W = sum_j D(. - X_j), d_j = sum_k D(x_k - X_j)
+// W(x_k) (Sec. V.C), s_j and s^m_j (Sec. V.E, V.F), and the shell CSR.
+int build_markers(State& s) {
+    qslbm::HostIB& h = s.hib;
+    const qslbm_params& p = s.p;
+    const int planes = s.nz;
+    h.ring_off.assign(planes + 1, 0);
+    if (p.geometry == QSLBM_CHANNEL) {
+        long long per = std::llround(p.nx / p.marker_spacing);
+        for (int z = 0; z < planes; ++z) {
+            for (int w = 0; w < 2; ++w)
+                for (long long i = 0; i < per; ++i) {
+                    h.X.push_back((double)i * p.marker_spacing);
+                    h.Y.push_back(w == 0 ? s.cy - s.R : s.cy + s.R);
+                    h.zplane.push_back(z);
+                }
+            h.ring_off[z + 1] = (int)h.X.size();
+        }
+    } else if (p.geometry == QSLBM_PIPE) {
+        long long nth = std::llround(M_PI * p.diameter / p.marker_spacing);
+        if (nth < 3) return QSLBM_EINVAL;
+        for (int z = 0; z < planes; ++z) {
+            for (long long i = 0; i < nth; ++i) {
+                double th = 2.0 * M_PI * (double)i / (double)nth;
+                h.X.push_back(s.cx + s.R * std::cos(th));
+                h.Y.push_back(s.cy + s.R * std::sin(th));
+                h.zplane.push_back(z);
+            }
+            h.ring_off[z + 1] = (int)h.X.size();
+        }
+    } else {
+        for (int z = 0; z < planes; ++z) h.ring_off[z + 1] = 0;
+    }
+    const int nm = (int)h.X.size();
+    h.ix.resize(3 * nm);
+    h.iy.resize(3 * nm);
+    h.wx.resize(3 * nm);
+    h.wy.resize(3 * nm);
+    for (int j = 0; j < nm; ++j) {
+        int x0, y0;
+        kernel_weights(h.X[j], x0, &h.wx[3 * j]);
+        kernel_weights(h.Y[j], y0, &h.wy[3 * j]);
+        for (int a = 0; a < 3; ++a) {
+            h.ix[3 * j + a] = wrapn((long long)x0 - 1 + a, s.nx);
+            h.iy[3 * j + a] = wrapn((long long)y0 - 1 + a, s.ny);
+        }
+    }
+    h.max_ring = 0;
+    for (int z = 0; z < planes; ++z) h.max_ring = std::max(h.max_ring, h.ring_off[z + 1] - h.ring_off[z]);
+    if ((size_t)3 * h.max_ring * (p.precision == QSLBM_FP64 ? 8 : 4) > 48 * 1024) return QSLBM_EINVAL;
+    // d_j and the scalings
+    const long long P = (long long)s.nx * s.ny;
+    std::vector<double> W;
+    h.shell_off.assign(planes + 1, 0);
+    h.d.assign(nm, 0.0);
+    h.s.assign(nm, 0.0);
+    h.sm.assign(nm, 0.0);
+    for (int z = 0; z < planes; ++z) {
+        const int m0 = h.ring_off[z], m1 = h.ring_off[z + 1];
+        h.shell_off[z] = (int)h.shell_xy.size();
+        h.shell_off[z + 1] = (int)h.shell_xy.size();
+        if (m0 == m1) continue;
+        W.assign(P, 0.0);
+        for (int j = m0; j < m1; ++j)
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) W[(long long)h.iy[3 * j + b] * s.nx + h.ix[3 * j + a]] += h.wx[3 * j + a] * h.wy[3 * j + b];
+        for (int j = m0; j < m1; ++j) {
+            double acc = 0.0;
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a)
+                    acc += h.wx[3 * j + a] * h.wy[3 * j + b] * W[(long long)h.iy[3 * j + b] * s.nx + h.ix[3 * j + a]];
+            h.d[j] = acc;
+            const double l = s.units.lambda, lm = s.units.lambda_m;
+            h.s[j] = l / (acc * (1.0 + acc * (l - 1.0)));
+            h.sm[j] = lm / (acc * (1.0 + acc * (lm - 1.0)));
+        }
+        // shell CSR of plane z: nodes with a nonzero weight, markers in ring order
+        struct Ent {
+            int xy, l;
+            double w;
+        };
+        std::vector<Ent> ents;
+        for (int j = m0; j < m1; ++j)
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    double w = h.wx[3 * j + a] * h.wy[3 * j + b];
+                    if (w != 0.0) ents.push_back({h.iy[3 * j + b] * s.nx + h.ix[3 * j + a], j - m0, w});
+                }
+        std::stable_sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) { return x.xy < y.xy; });
+        for (size_t e = 0; e < ents.size(); ++e) {
+            if (e == 0 || ents[e].xy != ents[e - 1].xy) {
+                h.shell_xy.push_back(ents[e].xy);
+                h.csr_off.push_back((int)h.csr_m.size());
+            }
+            h.csr_m.push_back(ents[e].l);
+            h.csr_w.push_back(ents[e].w);
+        }
+        h.shell_off[z + 1] = (int)h.shell_xy.size();
+    }
+    h.csr_off.push_back((int)h.csr_m.size());
+    for (double v : h.d)
+        if (!(v > 0)) return QSLBM_EINVAL;
+    return QSLBM_OK;
+}
+
+int upload_ib(State& s) {
+    qslbm::HostIB& h = s.hib;
+    qslbm::DeviceIB& d = s.ib;
+    int rc;
+    if ((rc = upload(s, (void**)&d.ring_off, h.ring_off))) return rc;
+    if ((rc = upload(s, (void**)&d.mk_ix, h.ix))) return rc;
+    if ((rc = upload(s, (void**)&d.mk_iy, h.iy))) return rc;
+    if ((rc = upload_real(s, &d.mk_wx, h.wx))) return rc;
+    if ((rc = upload_real(s, &d.mk_wy, h.wy))) return rc;
+    if ((rc = upload_real(s, &d.mk_s, h.s))) return rc;
+    if ((rc = upload_real(s, &d.mk_sm, h.sm))) return rc;
+    if ((rc = upload(s, (void**)&d.shell_off, h.shell_off))) return rc;
+    if ((rc = upload(s, (void**)&d.shell_xy, h.shell_xy))) return rc;
+    if ((rc = upload(s, (void**)&d.csr_off, h.csr_off))) return rc;
+    if ((rc = upload(s, (void**)&d.csr_m, h.csr_m))) return rc;
+    if ((rc = upload_real(s, &d.csr_w, h.csr_w))) return rc;
+    d.nm = (int)h.X.size();
+    d.ns = (int)h.shell_xy.size();
+    d.nnz = (int)h.csr_m.size();
+    d.max_ring = h.max_ring;
+    return QSLBM_OK;
+}
+
+double body_force(const State& s, long long t) {
+    double f = s.units.F0;
+    if (s.p.force_amp != 0.0) f *= 1.0 + s.p.force_amp * std::sin(s.omega * (double)t);
+    return f;
+}
+
+void release(State& s) {
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (s.graph[a][b]) cudaGraphExecDestroy(s.graph[a][b]);
+    for (void* p : s.allocations) cudaFree(p);
+    s.allocations.clear();
+    if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
+    s.stream = nullptr;
+}
+
+int check_device() {
+    int dev = 0;
+    QCHK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    QCHK(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        g_last_error = std::string("device is sm_") + std::to_string(prop.major) + std::to_string(prop.minor) +
+                       ", the library is built for sm_103a only";
+        return QSLBM_EARCH;
+    }
+    return QSLBM_OK;
+}
+
+int create_impl(const qslbm_params* pin, qslbm_handle** out) {
+    if (!pin || !out) return QSLBM_EINVAL;
+    *out = nullptr;
+    int rc = validate(*pin);
+    if (rc) return rc;
+    if ((rc = check_device())) return rc;
+    qslbm_handle* h = new (std::nothrow) qslbm_handle();
+    if (!h) return QSLBM_ENOMEM;
+    State& s = h->s;
+    s.p = *pin;
+    s.dim = s.p.dim;
+    s.nx = s.p.nx;
+    s.ny = s.p.ny;
+    s.nz = s.p.dim == 2 ? 1 : s.p.nz;
+    s.n = (long long)s.nx * s.ny * s.nz;
+    s.esz = s.p.precision == QSLBM_FP64 ? 8 : 4;
+    map_units(s.p, s.units);
+    s.units.nodes = s.n;
+    s.cx = std::isnan(s.p.center[0]) ? 0.5 * (s.nx - 1) : s.p.center[0];
+    s.cy = std::isnan(s.p.center[1]) ? 0.5 * (s.ny - 1) : s.p.center[1];
+    s.R = s.units.R;
+    s.axis = s.dim == 3 ? 2 : 0;
+    s.omega = s.p.force_amp != 0.0 ? 2.0 * M_PI / s.p.force_period : 0.0;
+    if (s.dim == 3) {
+        s.w0 = 0.25;
+        s.w1 = 0.125;
+    } else {
+        s.w0 = 1.0 / 3.0;
+        s.w1 = 1.0 / 6.0;
+    }
+    s.kappa = 1.0 / (s.units.c_mag * s.units.cm2);
+    for (int a = 0; a < 3; ++a) s.be[a] = s.units.B0 * s.p.b0_dir[a];
+    if ((rc = build_markers(s))) {
+        delete h;
+        return rc;
+    }
+    s.units.n_markers = (int)s.hib.X.size();
+    s.units.shell_nodes = (long long)s.hib.shell_xy.size();
+    if (s.p.stream) {
+        s.stream = (cudaStream_t)s.p.stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&s.stream);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        s.own_stream = true;
+    }
+    const size_t fb = (size_t)s.n * s.esz;
+    void** fields[] = {&s.drho[0], &s.drho[1]};
+    for (void** f : fields)
+        if ((rc = dev_alloc(s, f, fb))) goto fail;
+    for (int i = 0; i < 2; ++i) {
+        if ((rc = dev_alloc(s, &s.u[i], 3 * fb))) goto fail;
+        if ((rc = dev_alloc(s, &s.b[i], 3 * fb))) goto fail;
+    }
+    if ((rc = dev_alloc(s, &s.F, 3 * fb))) goto fail;
+    if ((rc = dev_alloc(s, &s.usnap, 3 * fb))) goto fail;
+    if ((rc = dev_alloc(s, (void**)&s.tdev, sizeof(long long)))) goto fail;
+    s.nblocks_obs = (int)std::min<long long>(1024, (s.n + qslbm::kReduceThreads - 1) / qslbm::kReduceThreads);
+    if ((rc = dev_alloc(s, (void**)&s.partial, (size_t)s.nblocks_obs * qslbm::kObs * sizeof(double)))) goto fail;
+    if ((rc = dev_alloc(s, (void**)&s.obs_dev, qslbm::kObs * sizeof(double)))) goto fail;
+    if (s.p.b0_kind == QSLBM_B0_TANH) {
+        s.bext_host.resize(3 * s.nz);
+        for (int z = 0; z < s.nz; ++z) {
+            double amp = s.units.B0 * 0.5 * (1.0 + std::tanh(((double)z - s.p.ramp_center) / s.p.ramp_width));
+            for (int a = 0; a < 3; ++a) s.bext_host[3 * z + a] = amp * s.p.b0_dir[a];
+        }
+        if ((rc = upload_real(s, &s.bext_z, s.bext_host))) goto fail;
+    }
+    if ((rc = upload_ib(s))) goto fail;
+    {
+        long long zero = 0;
+        cudaError_t e = cudaMemcpyAsync(s.tdev, &zero, sizeof(zero), cudaMemcpyHostToDevice, s.stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemcpyAsync");
+            goto fail;
+        }
+        ops(s).init(s, s.stream);
+        e = cudaMemcpyAsync(s.usnap, s.u[0], 3 * fb, cudaMemcpyDeviceToDevice, s.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "init");
+            goto fail;
+        }
+        // initial mass: rho = 1 everywhere
+        s.mass0 = (double)s.n;
+    }
+    s.units.device_bytes = s.device_bytes;
+    *out = h;
+    return QSLBM_OK;
+fail:
+    release(s);
+    delete h;
+    return rc;
+}
+
+// Steps per captured graph; each graph starts from a given ping-pong parity.
+constexpr int kGraphSteps = 1;
+
+int capture_chunk(State& s, int bc, int fc, cudaGraphExec_t* exec) {
+    const int save_b = s.bcur, save_f = s.fcur;
+    s.bcur = bc;
+    s.fcur = fc;
+    cudaGraph_t g = nullptr;
+    QCHK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kGraphSteps; ++i) {
+        ops(s).sweeps(s, s.units.n_mag, s.stream);
+        ops(s).force_flow(s, s.stream);
+    }
+    cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    s.bcur = save_b;
+    s.fcur = save_f;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return QSLBM_OK;
+}
+
+int step_impl(State& s, long long nsteps) {
+    if (nsteps < 0) return QSLBM_EINVAL;
+    const qslbm::Ops& o = ops(s);
+    long long done = 0;
+    while (nsteps - done >= kGraphSteps) {
+        cudaGraphExec_t& ex = s.graph[s.bcur][s.fcur];
+        if (!ex) {
+            int rc = capture_chunk(s, s.bcur, s.fcur, &ex);
+            if (rc) return rc;
+        }
+        QCHK(cudaGraphLaunch(ex, s.stream));
+        s.bcur ^= (int)(((long long)kGraphSteps * s.units.n_mag) & 1);
+        s.fcur ^= kGraphSteps & 1;
+        done += kGraphSteps;
+    }
+    for (; done < nsteps; ++done) {
+        o.sweeps(s, s.units.n_mag, s.stream);
+        o.force_flow(s, s.stream);
+    }
+    QCHK(cudaGetLastError());
+    s.t += nsteps;
+    return QSLBM_OK;
+}
+
+int ensure_staging(State& s) {
+    if (s.staging) return QSLBM_OK;
+    return dev_alloc(s, (void**)&s.staging, (size_t)7 * s.n * sizeof(double));
+}
+
+int observe_impl(State& s, qslbm_obs* out) {
+    double r[qslbm::kObs];
+    ops(s).observe(s, body_force(s, s.t), s.stream);
+    QCHK(cudaGetLastError());
+    QCHK(cudaMemcpyAsync(r, s.obs_dev, sizeof(r), cudaMemcpyDeviceToHost, s.stream));
+    QCHK(cudaMemcpyAsync(s.usnap, s.u[s.fcur], 3 * (size_t)s.n * s.esz, cudaMemcpyDeviceToDevice, s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    const long long dt = s.t - s.tsnap;
+    s.tsnap = s.t;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        const double inv = r[9] > 0 ? 1.0 / r[9] : 0.0;
+        out->step = s.t;
+        out->mass = r[0];
+        out->mass_drift = (r[0] - s.mass0) / s.mass0;
+        out->E_k = r[1] * inv;
+        out->E_m = r[2] * inv;
+        out->pump = r[3] * inv;
+        out->visc = -s.units.nu * r[4] * inv;
+        out->joule = r[5] * inv;
+        out->qs_residual = std::sqrt(r[6] * inv);
+        out->steady_residual = (dt > 0 && r[8] > 0) ? std::sqrt(r[7]) / ((double)dt * std::sqrt(r[8])) : 0.0;
+        out->nan_flag = r[10] > 0 ? 1 : 0;
+    }
+    return r[10] > 0 ? QSLBM_EUNSTABLE : QSLBM_OK;
+}
+
+int get_fields(State& s, double* rho, double* u, double* b) {
+    if (!rho && !u && !b) return QSLBM_OK;
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    ops(s).to_f64(s, s.stream);
+    QCHK(cudaGetLastError());
+    const size_t n = (size_t)s.n;
+    if (rho) QCHK(cudaMemcpyAsync(rho, s.staging, n * 8, cudaMemcpyDeviceToHost, s.stream));
+    if (u) QCHK(cudaMemcpyAsync(u, s.staging + n, 3 * n * 8, cudaMemcpyDeviceToHost, s.stream));
+    if (b) QCHK(cudaMemcpyAsync(b, s.staging + 4 * n, 3 * n * 8, cudaMemcpyDeviceToHost, s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    return QSLBM_OK;
+}
+
+int set_fields(State& s, const double* rho, const double* u, const double* b, long long t) {
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    const size_t n = (size_t)s.n;
+    int mask = 0;
+    if (rho) {
+        QCHK(cudaMemcpyAsync(s.staging, rho, n * 8, cudaMemcpyHostToDevice, s.stream));
+        mask |= 1;
+    }
+    if (u) {
+        QCHK(cudaMemcpyAsync(s.staging + n, u, 3 * n * 8, cudaMemcpyHostToDevice, s.stream));
+        mask |= 2;
+    }
+    if (b) {
+        QCHK(cudaMemcpyAsync(s.staging + 4 * n, b, 3 * n * 8, cudaMemcpyHostToDevice, s.stream));
+        mask |= 4;
+    }
+    if (mask) ops(s).from_f64(s, mask, s.stream);
+    QCHK(cudaGetLastError());
+    QCHK(cudaMemcpyAsync(s.tdev, &t, sizeof(t), cudaMemcpyHostToDevice, s.stream));
+    QCHK(cudaMemcpyAsync(s.usnap, s.u[s.fcur], 3 * n * s.esz, cudaMemcpyDeviceToDevice, s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    s.t = t;
+    s.tsnap = t;
+    return QSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qslbm_params_init(qslbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 3;
+    p->nx = p->ny = p->nz = 1;
+    p->geometry = QSLBM_PIPE;
+    p->center[0] = p->center[1] = NAN;
+    p->marker_spacing = 1.0;
+    p->b0_kind = QSLBM_B0_UNIFORM;
+    p->b0_dir[0] = 1.0;
+    p->ramp_width = 1.0;
+    p->n_mag_cap = 270;
+    p->precision = QSLBM_FP32;
+}
+
+int qslbm_create(const qslbm_params* p, qslbm_handle** out) {
+    try {
+        return create_impl(p, out);
+    } catch (...) {
+        return QSLBM_ENOMEM;
+    }
+}
+
+int qslbm_get_units(const qslbm_handle* h, qslbm_units* out) {
+    if (!h || !out) return QSLBM_EINVAL;
+    *out = h->s.units;
+    out->device_bytes = h->s.device_bytes;
+    return QSLBM_OK;
+}
+
+int qslbm_step(qslbm_handle* h, int64_t nsteps) {
+    if (!h) return QSLBM_EINVAL;
+    return step_impl(h->s, nsteps);
+}
+
+int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps) {
+    if (!h || nsweeps < 0) return QSLBM_EINVAL;
+    ops(h->s).sweeps(h->s, nsweeps, h->s.stream);
+    QCHK(cudaGetLastError());
+    return QSLBM_OK;
+}
+
+int qslbm_observables(qslbm_handle* h, qslbm_obs* out, double* rho, double* u, double* b) {
+    if (!h) return QSLBM_EINVAL;
+    int rc = observe_impl(h->s, out);
+    if (rc && rc != QSLBM_EUNSTABLE) return rc;
+    int rc2 = get_fields(h->s, rho, u, b);
+    return rc2 ? rc2 : rc;
+}
+
+int qslbm_get_state(qslbm_handle* h, double* rho, double* u, double* b, int64_t* t) {
+    if (!h) return QSLBM_EINVAL;
+    int rc = get_fields(h->s, rho, u, b);
+    if (rc) return rc;
+    QCHK(cudaStreamSynchronize(h->s.stream));
+    if (t) *t = h->s.t;
+    return QSLBM_OK;
+}
+
+int qslbm_set_state(qslbm_handle* h, const double* rho, const double* u, const double* b, int64_t t) {
+    if (!h || t < 0) return QSLBM_EINVAL;
+    return set_fields(h->s, rho, u, b, t);
+}
+
+int qslbm_step_host(qslbm_handle* h, const double* rho_in, const double* u_in, const double* b_in, int64_t t_in,
+                    int64_t nsteps, double* rho_out, double* u_out, double* b_out, qslbm_obs* obs) {
+    if (!h) return QSLBM_EINVAL;
+    int rc = set_fields(h->s, rho_in, u_in, b_in, t_in);
+    if (rc) return rc;
+    if ((rc = step_impl(h->s, nsteps))) return rc;
+    return qslbm_observables(h, obs, rho_out, u_out, b_out);
+}
+
+int qslbm_sync(qslbm_handle* h) {
+    if (!h) return QSLBM_EINVAL;
+    QCHK(cudaStreamSynchronize(h->s.stream));
+    QCHK(cudaGetLastError());
+    return QSLBM_OK;
+}
+
+int qslbm_destroy(qslbm_handle* h) {
+    if (!h) return QSLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->s.stream);
+    release(h->s);
+    delete h;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return QSLBM_OK;
+}
+
+const char* qslbm_strerror(int code) {
+    switch (code) {
+        case QSLBM_OK: return "ok";
+        case QSLBM_EINVAL: return "invalid argument";
+        case QSLBM_ENOMEM: return "out of memory";
+        case QSLBM_ECUDA: return "CUDA error";
+        case QSLBM_EUNSTABLE: return "non-finite field value";
+        case QSLBM_ETIMEOUT: return "step cap reached before the stop tolerance";
+        case QSLBM_EBUDGET: return "request exceeds the device-memory budget";
+        case QSLBM_ENOTFOUND: return "unknown request";
+        case QSLBM_EARCH: return "device is not sm_103";
+        default: return "unknown error";
+    }
+}
+
+const char* qslbm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal host-side structures of the qslbm library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "qslbm.h"
+
+namespace qslbm {
+
+// Diagnostics slots and the reduction block size (see k_observe).
+constexpr int kObs = 11;
+constexpr int kReduceThreads = 256;
+
+// Marker and shell tables of the IB corrector (device pointers).  The same
+// tables serve u and b; only the per-marker scaling differs (mk_s, mk_sm).
+struct DeviceIB {
+    int *ring_off = nullptr, *mk_ix = nullptr, *mk_iy = nullptr;
+    int *shell_off = nullptr, *shell_xy = nullptr, *csr_off = nullptr, *csr_m = nullptr;
+    void *mk_wx = nullptr, *mk_wy = nullptr, *mk_s = nullptr, *mk_sm = nullptr, *csr_w = nullptr;
+    int nm = 0, ns = 0, nnz = 0, max_ring = 0;
+};
+
+// Host copy of the marker geometry and IB weights (binary64).
+struct HostIB {
+    std::vector<double> X, Y;   // marker positions
+    std::vector<int> zplane;    // plane of each marker
+    std::vector<int> ring_off;  // [nz + 1]
+    std::vector<int> ix, iy;    // [3 nm] wrapped node indices
+    std::vector<double> wx, wy; // [3 nm] 1-D kernel weights
+    std::vector<double> d, s, sm;
+    std::vector<int> shell_off, shell_xy, csr_off, csr_m;
+    std::vector<double> csr_w;
+    int max_ring = 0;
+};
+
+struct State {
+    qslbm_params p{};
+    qslbm_units units{};
+    int dim = 3, nx = 0, ny = 0, nz = 0;
+    long long n = 0;
+    size_t esz = 4;
+    double cx = 0, cy = 0, R = 0;
+    double w0 = 0, w1 = 0, kappa = 0;  // field lattice weights, 1/(2 eta)
+    double be[3] = {0, 0, 0};          // uniform B^ext
+    int axis = 2;                      // body-force direction
+    double omega = 0;                  // 2 pi / period
+    void *drho[2] = {nullptr, nullptr}, *u[2] = {nullptr, nullptr}, *b[2] = {nullptr, nullptr};
+    void *F = nullptr, *usnap = nullptr, *bext_z = nullptr;
+    long long* tdev = nullptr;
+    double *partial = nullptr, *obs_dev = nullptr, *staging = nullptr;
+    int nblocks_obs = 0;
+    int fcur = 0, bcur = 0;
+    long long t = 0, tsnap = 0;
+    double mass0 = 0;
+    std::vector<double> bext_host;  // [3 nz] when the field is a ramp
+    HostIB hib;
+    DeviceIB ib;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int graph_steps = 0;
+    std::vector<void*> allocations;
+    long long device_bytes = 0;
+};
+
+// Kernel launchers, one table per storage precision.
+struct Ops {
+    void (*init)(State&, cudaStream_t);
+    void (*sweeps)(State&, int nsweeps, cudaStream_t);  // flips bcur per sweep
+    void (*force_flow)(State&, cudaStream_t);           // flips fcur
+    void (*observe)(State&, double fb, cudaStream_t);   // obs_dev[0..10]
+    void (*to_f64)(State&, cudaStream_t);               // staging <- state
+    void (*from_f64)(State&, int mask, cudaStream_t);   // state <- staging
+};
+
+const Ops& ops_f32();
+const Ops& ops_f64();
+
+}  // namespace qslbm

@@ -1,0 +1,599 @@
+// CUDA kernels of the single-step simplified LBM for quasi-static MHD pipe flow
+// (arXiv 2211.09370), written for sm_103a.  Templated on the storage/arithmetic
+// type T (float or double) and the dimension DIM (2: D2Q9 + D2Q5, 3: D3Q19 +
+// D3Q7).
+//
+// Layout in device memory: structure of arrays, one array per component,
+// index k = (z * ny + y) * nx + x (x fastest), periodic in every direction.
+// The density is stored as drho = rho - 1 so that FP32 keeps the small density
+// variations; the field evolved by the magnetic sweep is the induced part b of
+// B = B^ext + b, B^ext being analytic (uniform, or a tanh ramp in z held as one
+// value per z plane).
+//
+// Wall markers sit on integer z planes (rings of a pipe, lines of a channel),
+// so the z factor of the interpolation kernel D = D_x D_y D_z is a Kronecker
+// delta and the immersed-boundary operator couples nodes of one plane only.
+// Every kernel that applies the IB therefore gives one CTA a whole z plane: the
+// CTA first writes the plane's predictor values, then interpolates them at the
+// plane's markers (all markers before any spreading, as the explicit scheme
+// requires), then adds the spread corrections to the plane's shell nodes with
+// a node-side gather (node -> marker list), which needs no atomics and is
+// deterministic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qslbm_internal.h"
+
+namespace qslbm {
+
+constexpr int kPlaneThreads = 512;
+
+struct Geo {
+    int nx, ny, nz;
+    long long n;  // nx * ny * nz
+};
+
+// Marker / shell tables of one field's IB corrector, in device memory.
+template <typename T>
+struct IBView {
+    const int* ring_off;   // [nz + 1]: markers of plane z are ring_off[z] .. ring_off[z+1]-1
+    const int* mk_ix;      // [3 * nm]: wrapped x node of the three x weights
+    const int* mk_iy;      // [3 * nm]
+    const T* mk_wx;        // [3 * nm]: 1-D kernel weights (Sec. V.B)
+    const T* mk_wy;        // [3 * nm]
+    const T* mk_s;         // [nm]: lambda / (d (1 + d (lambda - 1)))
+    const int* shell_off;  // [nz + 1]: shell nodes of plane z
+    const int* shell_xy;   // [ns]: in-plane index y * nx + x of each shell node
+    const int* csr_off;    // [ns + 1]: entries of shell node s
+    const int* csr_m;      // [nnz]: marker index relative to its ring
+    const T* csr_w;        // [nnz]: D(x_k - X_j) for that pair
+    int nm;
+};
+
+// Coefficients of the tau_m = 1 magnetic sweep (Sec. V.G).
+template <typename T>
+struct SweepCoef {
+    T w0, w1;      // field-lattice weights: rest, axis
+    T kappa;       // 1 / (c c_m^2) = 1 / (2 eta)
+    T be[3];       // uniform B^ext (used when bext_z == nullptr)
+    const T* bext_z;  // [3 * nz] B^ext per plane for the ramp, or nullptr
+    int strict_qs;
+};
+
+// Coefficients of the flow update (Sec. III.E, V.A).
+template <typename T>
+struct FlowCoef {
+    T tau;        // relaxation time
+    T kforce;     // 1 - 1/(2 tau)
+};
+
+template <typename T>
+struct ForceCoef {
+    double F0, amp, omega;  // F_body(t) = F0 (1 + amp sin(omega t))
+    int axis;               // direction of the body force
+    T be[3];
+    const T* bext_z;
+};
+
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <typename T>
+__device__ __forceinline__ void bext_at(const T* bext_z, const T* be, int z, T out[3]) {
+    if (bext_z) {
+        out[0] = bext_z[3 * z + 0];
+        out[1] = bext_z[3 * z + 1];
+        out[2] = bext_z[3 * z + 2];
+    } else {
+        out[0] = be[0];
+        out[1] = be[1];
+        out[2] = be[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IB corrector on plane z of field f[3] (f[c] + k), run by a whole CTA after
+// the plane's predictor values are written.  sdelta: shared [3 * ring size].
+// Sec. V.C-V.F: delta_j = s_j (0 - D f*), then f += D^T delta.
+template <typename T>
+__device__ __forceinline__ void ib_plane(const IBView<T>& ib, T* f0, T* f1, T* f2, long long plane_base,
+                                         int nx, int z, T* sdelta) {
+    const int m0 = ib.ring_off[z], m1 = ib.ring_off[z + 1];
+    if (m1 == m0) return;  // uniform across the CTA: no divergence around barriers
+    __syncthreads();
+    for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const T wy = ib.mk_wy[3 * m + b];
+            const long long row = plane_base + (long long)ib.mk_iy[3 * m + b] * nx;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T w = ib.mk_wx[3 * m + a] * wy;
+                const long long q = row + ib.mk_ix[3 * m + a];
+                a0 += w * f0[q];
+                a1 += w * f1[q];
+                a2 += w * f2[q];
+            }
+        }
+        const T s = ib.mk_s[m];
+        const int l = m - m0;
+        sdelta[3 * l + 0] = -s * a0;
+        sdelta[3 * l + 1] = -s * a1;
+        sdelta[3 * l + 2] = -s * a2;
+    }
+    __syncthreads();
+    const int s0 = ib.shell_off[z], s1 = ib.shell_off[z + 1];
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        T c0 = T(0), c1 = T(0), c2 = T(0);
+        const int e0 = ib.csr_off[s], e1 = ib.csr_off[s + 1];
+        for (int e = e0; e < e1; ++e) {
+            const T w = ib.csr_w[e];
+            const int l = ib.csr_m[e];
+            c0 += w * sdelta[3 * l + 0];
+            c1 += w * sdelta[3 * l + 1];
+            c2 += w * sdelta[3 * l + 2];
+        }
+        const long long q = plane_base + ib.shell_xy[s];
+        f0[q] += c0;
+        f1[q] += c1;
+        f2[q] += c2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Magnetic sweep + IB on b for one z plane per CTA.
+// b_alpha(x) <- w0 b_alpha(x) + w1 sum_beta [ b_alpha(x - e_beta) + b_alpha(x + e_beta)
+//               + kappa (Phi_ab(x - e_beta) - Phi_ab(x + e_beta)) ],
+// Phi_ab = u_beta B_alpha - u_alpha B_beta, B = B^ext + b (B^ext only if
+// strict_qs).  This is sum_i g^eq_i(x - e_i) of Sec. V.G written per axis.
+template <typename T>
+__device__ __forceinline__ void flux_pair(const T u[3], const T B[3], int beta, T phi[3]) {
+    // phi[alpha] = u_beta B_alpha - u_alpha B_beta
+#pragma unroll
+    for (int a = 0; a < 3; ++a) phi[a] = u[beta] * B[a] - u[a] * B[beta];
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPlaneThreads) k_sweep_ib(Geo g, const T* __restrict__ bin, T* bout,
+                                                            const T* __restrict__ u, SweepCoef<T> c,
+                                                            IBView<T> ib) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int z = blockIdx.x;
+    const long long n = g.n;
+    const long long P = (long long)nx * ny;
+    const long long base = (long long)z * P;
+    const int zm = DIM == 3 ? wrap_dec(z, nz) : z, zp = DIM == 3 ? wrap_inc(z, nz) : z;
+    T be_c[3], be_m[3], be_p[3];
+    bext_at(c.bext_z, c.be, z, be_c);
+    bext_at(c.bext_z, c.be, zm, be_m);
+    bext_at(c.bext_z, c.be, zp, be_p);
+    const T* b0 = bin;
+    const T* b1 = bin + n;
+    const T* b2 = bin + 2 * n;
+    const T* u0 = u;
+    const T* u1 = u + n;
+    const T* u2 = u + 2 * n;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int x = p % nx, y = p / nx;
+        const long long k = base + p;
+        long long nb[2 * DIM];  // -x, +x, -y, +y, (-z, +z)
+        nb[0] = base + (long long)y * nx + wrap_dec(x, nx);
+        nb[1] = base + (long long)y * nx + wrap_inc(x, nx);
+        nb[2] = base + (long long)wrap_dec(y, ny) * nx + x;
+        nb[3] = base + (long long)wrap_inc(y, ny) * nx + x;
+        if (DIM == 3) {
+            nb[4] = (long long)zm * P + p;
+            nb[5] = (long long)zp * P + p;
+        }
+        T acc[3];
+        acc[0] = c.w0 * b0[k];
+        acc[1] = c.w0 * b1[k];
+        acc[2] = c.w0 * b2[k];
+        T diff[3] = {T(0), T(0), T(0)};  // sum_beta Phi_ab(x - e_beta) - Phi_ab(x + e_beta)
+#pragma unroll
+        for (int d = 0; d < 2 * DIM; ++d) {
+            const long long q = nb[d];
+            const T bq[3] = {b0[q], b1[q], b2[q]};
+            acc[0] += c.w1 * bq[0];
+            acc[1] += c.w1 * bq[1];
+            acc[2] += c.w1 * bq[2];
+            const T uq[3] = {u0[q], u1[q], u2[q]};
+            const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
+            T B[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+            T phi[3];
+            flux_pair(uq, B, d >> 1, phi);
+            const T sgn = (d & 1) ? T(-1) : T(1);  // x - e_beta enters with +, x + e_beta with -
+#pragma unroll
+            for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] += c.w1 * c.kappa * diff[a];
+        bout[k] = acc[0];
+        bout[k + n] = acc[1];
+        bout[k + 2 * n] = acc[2];
+    }
+    ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, nx, z, sdelta);
+}
+
+// ---------------------------------------------------------------------------
+// Lattice tables for the flow update.
+template <int DIM>
+struct FlowLattice;
+
+template <>
+struct FlowLattice<3> {
+    static constexpr int Q = 19;
+};
+template <>
+struct FlowLattice<2> {
+    static constexpr int Q = 9;
+};
+
+__device__ __forceinline__ void flow_dir3(int j, int& cx, int& cy, int& cz) {
+    // D3Q19 non-rest directions 1..18: 6 axis then 12 edge directions
+    const int tx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    const int ty[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    const int tz[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    cx = tx[j];
+    cy = ty[j];
+    cz = tz[j];
+}
+__device__ __forceinline__ void flow_dir2(int j, int& cx, int& cy, int& cz) {
+    const int tx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ty[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    cx = tx[j];
+    cy = ty[j];
+    cz = 0;
+}
+
+template <int DIM>
+__device__ __forceinline__ double flow_w(int j) {
+    if (DIM == 3) return j == 0 ? 1.0 / 3.0 : (j <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    return j == 0 ? 4.0 / 9.0 : (j <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------------------
+// Force: J = curl b by isotropic differences on the flow lattice
+// (d_beta phi = 3 sum_i w_i c_i,beta phi(x + c_i)), F = F_body(t) e_axis +
+// J x (B^ext + b).  One thread per node.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T* __restrict__ F,
+                                               ForceCoef<T> c, const long long* __restrict__ tstep) {
+    const long long n = g.n;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long t = *tstep;
+    const double fb_d = c.amp != 0.0 ? c.F0 * (1.0 + c.amp * sin(c.omega * (double)t)) : c.F0;
+    const T fb = (T)fb_d;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx);
+        const int y = (int)((k / nx) % ny);
+        const int z = (int)(k / ((long long)nx * ny));
+        T db[3][3];  // db[beta][alpha] = d_beta b_alpha
+#pragma unroll
+        for (int be = 0; be < 3; ++be)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) db[be][a] = T(0);
+#pragma unroll
+        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+            int cx, cy, cz;
+            if (DIM == 3)
+                flow_dir3(j, cx, cy, cz);
+            else
+                flow_dir2(j, cx, cy, cz);
+            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+            const T w = (T)(3.0 * flow_w<DIM>(j));
+            const T bq[3] = {b[q], b[q + n], b[q + 2 * n]};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (cx) db[0][a] += (w * (T)cx) * bq[a];
+                if (cy) db[1][a] += (w * (T)cy) * bq[a];
+                if (cz) db[2][a] += (w * (T)cz) * bq[a];
+            }
+        }
+        const T J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
+        T Be[3];
+        bext_at(c.bext_z, c.be, z, Be);
+        const T B[3] = {Be[0] + b[k], Be[1] + b[k + n], Be[2] + b[k + 2 * n]};
+        T L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
+        L[c.axis] += fb;
+        F[k] = L[0];
+        F[k + n] = L[1];
+        F[k + 2 * n] = L[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-step flow update + IB on u, one z plane per CTA.  For each neighbour
+// y = x + c_j the equilibria of direction j (as f_j(x + c_j)) and of the
+// opposite direction (as f_jbar(x - c_jbar)) are formed from one load of y:
+//   drho* = 2 f~_0(x) - drho(x) + sum_j [ 0.5 f~_j(y) + 1.5 f~_jbar(y) ]
+//   m*    = sum_j c_j [ (tau - 1) f~_j(y) - tau f~_jbar(y) ] - 2 (tau - 1) rho u(x)
+//           - (tau/2) sum_j c_j [ F_j(y) + F_jbar(y) ] + F(x)
+// with f~_i = f_i^eq - w_i = w_i (drho + q_i + drho q_i),
+// q_i = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u, and the GZS terms
+// F_j + F_jbar = (1 - 1/2tau) w_j (-6 u.F + 18 (c_j.u)(c_j.F)).  This uses
+// sum_i f_i^eq(x) = rho and sum_i c_i f_i^eq(x) = rho u, exact on the lattice.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __restrict__ drho,
+                                                           const T* __restrict__ u, const T* __restrict__ F,
+                                                           T* __restrict__ drho_out, T* uout, FlowCoef<T> c,
+                                                           IBView<T> ib, long long* tstep) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int z = blockIdx.x;
+    const long long n = g.n;
+    const long long P = (long long)nx * ny;
+    const long long base = (long long)z * P;
+    const T tau = c.tau, tm1 = c.tau - T(1), half_tau = T(0.5) * c.tau;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int x = p % nx, y = p / nx;
+        const long long k = base + p;
+        const T dr0 = drho[k];
+        const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
+        const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
+        const T q0 = T(-1.5) * uu0;
+        const T w0 = (T)flow_w<DIM>(0);
+        T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
+        T m[3] = {T(0), T(0), T(0)};
+        T corr[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+            int cx, cy, cz;
+            if (DIM == 3)
+                flow_dir3(j, cx, cy, cz);
+            else
+                flow_dir2(j, cx, cy, cz);
+            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+            const T dr = drho[q];
+            const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
+            const T Fq[3] = {F[q], F[q + n], F[q + 2 * n]};
+            const T a = (T)cx * uq[0] + (T)cy * uq[1] + (T)cz * uq[2];
+            const T uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
+            const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
+            const T uF = uq[0] * Fq[0] + uq[1] * Fq[1] + uq[2] * Fq[2];
+            const T w = (T)flow_w<DIM>(j);
+            const T sq = T(4.5) * a * a - T(1.5) * uu;
+            const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
+            const T fj = w * (dr + qp + dr * qp);
+            const T fjb = w * (dr + qm + dr * qm);
+            rho_acc += T(0.5) * fj + T(1.5) * fjb;
+            const T mom = tm1 * fj - tau * fjb;
+            const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF);
+            if (cx) {
+                m[0] += (T)cx * mom;
+                corr[0] += (T)cx * fs;
+            }
+            if (cy) {
+                m[1] += (T)cy * mom;
+                corr[1] += (T)cy * fs;
+            }
+            if (cz) {
+                m[2] += (T)cz * mom;
+                corr[2] += (T)cz * fs;
+            }
+        }
+        const T rho0 = T(1) + dr0;
+        const T rho_new = T(1) + rho_acc;
+        const T inv = T(1) / rho_new;
+        const T Fk[3] = {F[k], F[k + n], F[k + 2 * n]};
+        const T u0v[3] = {ux0, uy0, uz0};
+        drho_out[k] = rho_acc;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T mm = m[a] - T(2) * tm1 * rho0 * u0v[a] - half_tau * corr[a] + Fk[a];
+            uout[k + a * n] = mm * inv;
+        }
+    }
+    ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, nx, z, sdelta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *tstep += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: drho = 0, b = 0, u = splitmix64 noise (Steele, Lea, Flood)
+// of the counter seed ^ (3 k + component), top 53 bits to [-1, 1), times amp,
+// on nodes within radius R of the wall centre (between the walls for a channel).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_init(Geo g, T* drho, T* u, T* b, unsigned long long seed, double amp, int ncomp,
+                       int geometry, double cx, double cy, double R) {
+    const long long n = g.n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        drho[k] = T(0);
+        const int x = (int)(k % g.nx);
+        const int y = (int)((k / g.nx) % g.ny);
+        bool inside;
+        if (geometry == 2)
+            inside = true;
+        else if (geometry == 0)
+            inside = fabs((double)y - cy) <= R;
+        else
+            inside = sqrt(((double)x - cx) * ((double)x - cx) + ((double)y - cy) * ((double)y - cy)) <= R;
+        for (int a = 0; a < 3; ++a) {
+            b[k + a * n] = T(0);
+            double v = 0.0;
+            if (amp != 0.0 && inside && a < ncomp) {
+                const unsigned long long r = splitmix64(seed ^ (unsigned long long)(3 * k + a));
+                v = amp * ((double)(r >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+            }
+            u[k + a * n] = (T)v;
+        }
+    }
+}
+
+// Conversions between the device state and binary64 staging arrays.
+template <typename T>
+__global__ void k_to_f64(long long n, const T* drho, const T* u, const T* b, double* out) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        out[k] = 1.0 + (double)drho[k];
+        for (int a = 0; a < 3; ++a) {
+            out[(1 + a) * n + k] = (double)u[a * n + k];
+            out[(4 + a) * n + k] = (double)b[a * n + k];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_from_f64(long long n, const double* in, T* drho, T* u, T* b, int mask) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (mask & 1) drho[k] = (T)(in[k] - 1.0);
+        for (int a = 0; a < 3; ++a) {
+            if (mask & 2) u[a * n + k] = (T)in[(1 + a) * n + k];
+            if (mask & 4) b[a * n + k] = (T)in[(4 + a) * n + k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics in binary64: per-block partial sums, then one block folds them
+// in a fixed order (deterministic).  Slots:
+// 0 mass, 1 E_k, 2 E_m, 3 pump, 4 visc (u . lap u), 5 joule, 6 qs^2,
+// 7 |u - usnap|^2, 8 |u|^2, 9 count, 10 non-finite count.
+template <typename T>
+struct ObsCoef {
+    double eta, fb;  // resistivity, F_body at the current step
+    int axis, geometry, strict_qs, dim;
+    double cx, cy, rin;  // region: distance from the centre <= rin
+    T be[3];
+    const T* bext_z;
+};
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __restrict__ drho,
+                                                            const T* __restrict__ u, const T* __restrict__ b,
+                                                            const T* __restrict__ usnap, ObsCoef<T> c,
+                                                            double* partial) {
+    __shared__ double red[kObs][kReduceThreads / 32];
+    double acc[kObs];
+#pragma unroll
+    for (int i = 0; i < kObs; ++i) acc[i] = 0.0;
+    const long long n = g.n;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx);
+        const int y = (int)((k / nx) % ny);
+        const int z = (int)(k / ((long long)nx * ny));
+        const double rho = 1.0 + (double)drho[k];
+        const double uk[3] = {(double)u[k], (double)u[k + n], (double)u[k + 2 * n]};
+        const double bk[3] = {(double)b[k], (double)b[k + n], (double)b[k + 2 * n]};
+        acc[0] += rho;
+        bool bad = !isfinite(rho);
+        for (int a = 0; a < 3; ++a) {
+            bad = bad || !isfinite(uk[a]) || !isfinite(bk[a]);
+            const double du = uk[a] - (double)usnap[k + a * n];
+            acc[7] += du * du;
+            acc[8] += uk[a] * uk[a];
+        }
+        if (bad) acc[10] += 1.0;
+        bool inside;
+        if (c.geometry == 2)
+            inside = true;
+        else if (c.geometry == 0)
+            inside = fabs((double)y - c.cy) <= c.rin;
+        else
+            inside = sqrt(((double)x - c.cx) * ((double)x - c.cx) + ((double)y - c.cy) * ((double)y - c.cy)) <= c.rin;
+        if (!inside) continue;
+        acc[9] += 1.0;
+        T Be_t[3];
+        bext_at(c.bext_z, c.be, z, Be_t);
+        const double Be[3] = {(double)Be_t[0], (double)Be_t[1], (double)Be_t[2]};
+        const double B[3] = {Be[0] + bk[0], Be[1] + bk[1], Be[2] + bk[2]};
+        acc[1] += 0.5 * rho * (uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+        acc[2] += 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        acc[3] += c.fb * uk[c.axis];
+        // flow-lattice Laplacian of u and isotropic gradient of b
+        double lap[3] = {0.0, 0.0, 0.0};
+        double db[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+            int cx, cy, cz;
+            if (DIM == 3)
+                flow_dir3(j, cx, cy, cz);
+            else
+                flow_dir2(j, cx, cy, cz);
+            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+            const double w = flow_w<DIM>(j);
+            for (int a = 0; a < 3; ++a) {
+                lap[a] += w * ((double)u[q + a * n] - uk[a]);
+                const double bq = (double)b[q + a * n];
+                db[0][a] += 3.0 * w * cx * bq;
+                db[1][a] += 3.0 * w * cy * bq;
+                db[2][a] += 3.0 * w * cz * bq;
+            }
+        }
+        double ulap = 0.0;
+        for (int a = 0; a < 3; ++a) ulap += uk[a] * 6.0 * lap[a];
+        acc[4] += ulap;
+        const double J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
+        const double L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
+        acc[5] += -(uk[0] * L[0] + uk[1] * L[1] + uk[2] * L[2]);
+        // QS residual with the field lattice's operators
+        for (int a = 0; a < 3; ++a) {
+            double lapb = 0.0, div = 0.0;
+            for (int be = 0; be < DIM; ++be) {
+                const int ex = be == 0, ey = be == 1, ez = be == 2;
+                const int zpp = wrapi(z + ez, nz), zmm = wrapi(z - ez, nz);
+                const long long kp = ((long long)zpp * ny + wrapi(y + ey, ny)) * nx + wrapi(x + ex, nx);
+                const long long km = ((long long)zmm * ny + wrapi(y - ey, ny)) * nx + wrapi(x - ex, nx);
+                lapb += (double)b[kp + a * n] + (double)b[km + a * n] - 2.0 * bk[a];
+                T Bep_t[3], Bem_t[3];
+                bext_at(c.bext_z, c.be, zpp, Bep_t);
+                bext_at(c.bext_z, c.be, zmm, Bem_t);
+                double Bp[3], Bm[3];
+                for (int cc = 0; cc < 3; ++cc) {
+                    Bp[cc] = (double)Bep_t[cc] + (c.strict_qs ? 0.0 : (double)b[kp + cc * n]);
+                    Bm[cc] = (double)Bem_t[cc] + (c.strict_qs ? 0.0 : (double)b[km + cc * n]);
+                }
+                const double phip = (double)u[kp + be * n] * Bp[a] - (double)u[kp + a * n] * Bp[be];
+                const double phim = (double)u[km + be * n] * Bm[a] - (double)u[km + a * n] * Bm[be];
+                div += 0.5 * (phip - phim);
+            }
+            const double r = c.eta * lapb - div;
+            acc[6] += r * r;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kObs; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kObs) {
+        double v = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) v += red[threadIdx.x][w];
+        partial[(long long)blockIdx.x * kObs + threadIdx.x] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_fold(const double* partial, int nblocks, double* out) {
+    // one warp per slot, fixed order within each lane, fixed shuffle tree
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (i >= kObs) return;
+    double v = 0.0;
+    for (int b = lane; b < nblocks; b += 32) v += partial[(long long)b * kObs + i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[i] = v;
+}
+
+}  // namespace qslbm

@@ -1,0 +1,138 @@
+// Kernel launchers for one storage precision T; included by qslbm_f32.cu and
+// qslbm_f64.cu, which instantiate it for float and double.
+#pragma once
+
+#include "qslbm_internal.h"
+#include "qslbm_kernels.cuh"
+
+namespace qslbm {
+
+template <typename T>
+struct Launch {
+    static Geo geo(const State& s) { return Geo{s.nx, s.ny, s.nz, s.n}; }
+
+    static IBView<T> view(const State& s, bool magnetic) {
+        IBView<T> v;
+        v.ring_off = s.ib.ring_off;
+        v.mk_ix = s.ib.mk_ix;
+        v.mk_iy = s.ib.mk_iy;
+        v.mk_wx = static_cast<const T*>(s.ib.mk_wx);
+        v.mk_wy = static_cast<const T*>(s.ib.mk_wy);
+        v.mk_s = static_cast<const T*>(magnetic ? s.ib.mk_sm : s.ib.mk_s);
+        v.shell_off = s.ib.shell_off;
+        v.shell_xy = s.ib.shell_xy;
+        v.csr_off = s.ib.csr_off;
+        v.csr_m = s.ib.csr_m;
+        v.csr_w = static_cast<const T*>(s.ib.csr_w);
+        v.nm = s.ib.nm;
+        return v;
+    }
+
+    static size_t ib_smem(const State& s) { return (size_t)3 * (s.ib.max_ring > 0 ? s.ib.max_ring : 1) * sizeof(T); }
+
+    static int grid_for(long long n, int threads) {
+        long long b = (n + threads - 1) / threads;
+        if (b > 152LL * 16) b = 152LL * 16;
+        if (b < 1) b = 1;
+        return (int)b;
+    }
+
+    static void init(State& s, cudaStream_t st) {
+        int ncomp = s.dim == 3 ? 3 : 2;
+        k_init<T><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), (T*)s.drho[0], (T*)s.u[0], (T*)s.b[0], s.p.seed,
+                                                       s.p.perturb * s.units.U0, ncomp, s.p.geometry, s.cx,
+                                                       s.cy, s.R);
+    }
+
+    static void sweeps(State& s, int nsweeps, cudaStream_t st) {
+        SweepCoef<T> c;
+        c.w0 = (T)s.w0;
+        c.w1 = (T)s.w1;
+        c.kappa = (T)s.kappa;
+        for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
+        c.bext_z = static_cast<const T*>(s.bext_z);
+        c.strict_qs = s.p.strict_qs;
+        const IBView<T> v = view(s, true);
+        const size_t smem = ib_smem(s);
+        for (int i = 0; i < nsweeps; ++i) {
+            const T* bin = (const T*)s.b[s.bcur];
+            T* bout = (T*)s.b[1 - s.bcur];
+            const T* u = (const T*)s.u[s.fcur];
+            if (s.dim == 3)
+                k_sweep_ib<T, 3><<<s.nz, kPlaneThreads, smem, st>>>(geo(s), bin, bout, u, c, v);
+            else
+                k_sweep_ib<T, 2><<<s.nz, kPlaneThreads, smem, st>>>(geo(s), bin, bout, u, c, v);
+            s.bcur ^= 1;
+        }
+    }
+
+    static void force_flow(State& s, cudaStream_t st) {
+        ForceCoef<T> fc;
+        fc.F0 = s.units.F0;
+        fc.amp = s.p.force_amp;
+        fc.omega = s.omega;
+        fc.axis = s.axis;
+        for (int a = 0; a < 3; ++a) fc.be[a] = (T)s.be[a];
+        fc.bext_z = static_cast<const T*>(s.bext_z);
+        FlowCoef<T> c;
+        c.tau = (T)s.units.tau;
+        c.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+        const IBView<T> v = view(s, false);
+        const T* b = (const T*)s.b[s.bcur];
+        const T* dr = (const T*)s.drho[s.fcur];
+        const T* u = (const T*)s.u[s.fcur];
+        T* dro = (T*)s.drho[1 - s.fcur];
+        T* uo = (T*)s.u[1 - s.fcur];
+        T* F = (T*)s.F;
+        if (s.dim == 3) {
+            k_force<T, 3><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), b, F, fc, s.tdev);
+            k_flow_ib<T, 3><<<s.nz, kPlaneThreads, ib_smem(s), st>>>(geo(s), dr, u, F, dro, uo, c, v, s.tdev);
+        } else {
+            k_force<T, 2><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), b, F, fc, s.tdev);
+            k_flow_ib<T, 2><<<s.nz, kPlaneThreads, ib_smem(s), st>>>(geo(s), dr, u, F, dro, uo, c, v, s.tdev);
+        }
+        s.fcur ^= 1;
+    }
+
+    static void observe(State& s, double fb, cudaStream_t st) {
+        ObsCoef<T> c;
+        c.eta = s.units.eta;
+        c.fb = fb;
+        c.axis = s.axis;
+        c.geometry = s.p.geometry;
+        c.strict_qs = s.p.strict_qs;
+        c.dim = s.dim;
+        c.cx = s.cx;
+        c.cy = s.cy;
+        c.rin = s.R - 2.0;
+        for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
+        c.bext_z = static_cast<const T*>(s.bext_z);
+        const T* dr = (const T*)s.drho[s.fcur];
+        const T* u = (const T*)s.u[s.fcur];
+        const T* b = (const T*)s.b[s.bcur];
+        if (s.dim == 3)
+            k_observe<T, 3><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
+                                                                    s.partial);
+        else
+            k_observe<T, 2><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
+                                                                    s.partial);
+        k_fold<T><<<1, 32 * kObs, 0, st>>>(s.partial, s.nblocks_obs, s.obs_dev);
+    }
+
+    static void to_f64(State& s, cudaStream_t st) {
+        k_to_f64<T><<<grid_for(s.n, 256), 256, 0, st>>>(s.n, (const T*)s.drho[s.fcur], (const T*)s.u[s.fcur],
+                                                        (const T*)s.b[s.bcur], s.staging);
+    }
+
+    static void from_f64(State& s, int mask, cudaStream_t st) {
+        k_from_f64<T><<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.staging, (T*)s.drho[s.fcur], (T*)s.u[s.fcur],
+                                                          (T*)s.b[s.bcur], mask);
+    }
+
+    static const Ops& table() {
+        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64};
+        return o;
+    }
+};
+
+}  // namespace qslbm

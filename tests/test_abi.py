@@ -1,0 +1,61 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every symbol the header declares, and rejects invalid parameters
+before touching the device."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+from paper_2211_09370_gb300 import _lib
+from paper_2211_09370_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "qslbm.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"\b(qslbm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(_lib.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_struct_layouts_match_header_sizes():
+    # defaults written by the library match the header comments
+    p = _lib.qslbm_params()
+    _lib.load().qslbm_params_init(C.byref(p))
+    assert p.dim == 3 and p.geometry == _lib.PIPE and p.n_mag_cap == 270 and p.marker_spacing == 1.0
+    assert math.isnan(p.center[0]) and p.b0_dir[0] == 1.0 and p.precision == _lib.FP32
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(nx=0), dict(diameter=-1.0), dict(Re=0.0), dict(Rm=-1.0), dict(Ha=-2.0),
+    dict(marker_spacing=0.0), dict(b0_kind=7), dict(b0_kind="tanh", ramp_width=0.0),
+    dict(force_amp=0.2, force_period=0.0), dict(precision=5), dict(n_mag=-3), dict(perturb=-1.0),
+])
+def test_invalid_parameters_rejected_before_device(bad):
+    p = W.small_pipe(**bad)
+    q = _lib.make_params(p)
+    h = C.c_void_p()
+    rc = _lib.load().qslbm_create(C.byref(q), C.byref(h))
+    assert rc == _lib.EINVAL
+    assert not h.value
+
+
+def test_null_arguments():
+    L = _lib.load()
+    assert L.qslbm_create(None, None) == _lib.EINVAL
+    assert L.qslbm_step(None, 1) == _lib.EINVAL
+    assert L.qslbm_observables(None, None, None, None, None) == _lib.EINVAL
+    assert L.qslbm_destroy(None) == _lib.EINVAL
+    assert L.qslbm_strerror(_lib.EBUDGET).decode().startswith("request exceeds")

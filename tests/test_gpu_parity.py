@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU oracle.
+
+Tolerances (relative L2 over the compared nodes): FP64 path <= 1e-12 on rho,
+u and b; FP32 path <= 1e-4 on u and b (and <= 1e-4 on drho relative to the
+largest |drho| scale, since FP32 stores rho - 1).  The FP64 oracle stores rho
+itself, so drho = rho - 1 taken from it carries an absolute rounding of about
+1e-16, which is why the FP64 drho check is relative to the drho scale at 1e-9.
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_09370_gb300 import workloads as W
+from paper_2211_09370_gb300._lib import EUNSTABLE, QSLBMError, Solver
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+golden = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(golden)
+
+TOL = {"fp64": 1e-12, "fp32": 1e-4}
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def check_fields(got, want, precision, what=""):
+    rho, u, b = got
+    orho, ou, ob = want
+    tol = TOL[precision]
+    assert rel(u, ou) <= tol, f"{what} u rel-L2 {rel(u, ou):.3e}"
+    if np.linalg.norm(ob) > 0:
+        assert rel(b, ob) <= tol, f"{what} b rel-L2 {rel(b, ob):.3e}"
+    else:
+        assert np.abs(b).max() == 0.0
+    if precision == "fp64":
+        assert rel(rho, orho) <= 1e-12, f"{what} rho rel-L2 {rel(rho, orho):.3e}"
+        scale = max(np.abs(orho - 1).max(), 1e-300)
+        assert np.abs((rho - 1) - (orho - 1)).max() / scale <= 1e-9
+    else:
+        scale = max(np.abs(orho - 1).max(), 1e-300)
+        assert np.abs(rho - orho).max() / scale <= 1e-3 or np.abs(rho - orho).max() <= 1e-7
+
+
+def run_both(p, steps, t0=0):
+    o = oracle.Oracle(p)
+    with Solver(p) as s:
+        if t0:
+            rho, u, b = s.state()
+            s.set_state(rho, u, b, t=t0)
+            r, uu, bb = o.state()
+            o.set_state(r, uu, bb, t=t0)
+        s.step(steps)
+        got = s.state()
+    o.step(steps)
+    return got, o.state(), o
+
+
+# ------------------------------------------------------- small, ragged sizes
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_pipe_matches_oracle(precision):
+    # 29 x 27 planes: 783 nodes, two strides of 512 threads with a ragged tail
+    p = W.small_pipe(nx=29, ny=27, nz=11, diameter=19.0, precision=precision)
+    got, want, _ = run_both(p, 12)
+    check_fields(got, want, precision, "small pipe")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_ramp_pulsating_pipe(precision):
+    p = W.small_pipe(nx=24, ny=22, nz=40, diameter=16.0, Re=500.0, Ha=50.0, Rm=0.1, b0_kind="tanh",
+                     ramp_center=20.0, ramp_width=4.0, force_amp=0.2, force_period=50.0, perturb=0.01,
+                     seed=9, precision=precision)
+    got, want, _ = run_both(p, 8, t0=13)
+    check_fields(got, want, precision, "ramp")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_channel_2d_odd_size(precision):
+    p = W.hartmann_channel_2d(nx=37, ny=20, diameter=19.0, n_mag=60, precision=precision, perturb=0.02,
+                              seed=3)
+    got, want, _ = run_both(p, 40)
+    check_fields(got, want, precision, "channel")
+
+
+@pytest.mark.parametrize("case", ["periodic", "single_plane", "strict_qs", "no_field", "one_sweep"])
+def test_degenerate_cases_fp64(case):
+    base = dict(nx=13, ny=11, nz=7, diameter=8.0, precision="fp64", perturb=0.05, seed=11, n_mag=20)
+    extra = {"periodic": dict(geometry="none"), "single_plane": dict(nz=1), "strict_qs": dict(strict_qs=1),
+             "no_field": dict(Ha=0.0), "one_sweep": dict(n_mag=1)}[case]
+    base.update(extra)
+    p = W.small_pipe(**base)
+    got, want, _ = run_both(p, 10)
+    check_fields(got, want, "fp64", case)
+
+
+def test_mag_sweeps_with_frozen_velocity_fp64():
+    p = W.small_pipe(nx=22, ny=22, nz=6, diameter=15.0, precision="fp64")
+    z, y, x = np.meshgrid(np.arange(6.0), np.arange(22.0), np.arange(22.0), indexing="ij")
+    u = np.stack([0.01 * np.sin(2 * np.pi * y / 22), 0.02 * np.cos(2 * np.pi * x / 22), 0.03 + 0.0 * x])
+    o = oracle.Oracle(p)
+    o.set_state(np.ones_like(x), u, np.zeros_like(u), t=0)
+    o.mag_sweeps(300)
+    with Solver(p) as s:
+        s.set_state(np.ones_like(x), u, np.zeros_like(u), t=0)
+        s.mag_sweeps(300)
+        _, gu, gb = s.state()
+    _, ou, ob = o.state()
+    assert rel(gb, ob) <= 1e-12
+    np.testing.assert_array_equal(gu, u)
+
+
+def test_observables_match_oracle_fp64():
+    p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2)
+    o = oracle.Oracle(p)
+    with Solver(p) as s:
+        s.step(10)
+        s.observables()
+        o.step(10)
+        o.observables()
+        s.step(7)
+        o.step(7)
+        g = s.observables()
+        w = o.observables()
+    assert g["step"] == 17
+    for k in ("mass", "E_k", "E_m", "pump", "visc", "joule", "qs_residual", "steady_residual"):
+        assert g[k] == pytest.approx(w[k], rel=1e-9, abs=1e-300), k
+    assert abs(g["mass_drift"]) < 1e-13 and g["nan_flag"] == 0
+
+
+# ---------------------------------------------------------- full workloads
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hartmann_channel_full_horizon(precision):
+    g = golden.load("hartmann_2000")
+    p = W.hartmann_channel_2d(precision=precision)
+    with Solver(p) as s:
+        s.step(int(g["steps"]))
+        got = s.state()
+    check_fields(got, (g["rho"], g["u"], g["b"]), precision, "hartmann 2000")
+
+
+def _sampled(p, g, precision):
+    with Solver(p) as s:
+        t0 = int(g["t0"])
+        if t0:
+            rho, u, b = s.state()
+            s.set_state(rho, u, b, t=t0)
+        s.step(int(g["steps"]))
+        rho, u, b = s.state()
+    idx = g["idx"]
+    got = np.concatenate([rho.reshape(1, -1), u.reshape(3, -1), b.reshape(3, -1)])[:, idx]
+    want = g["fields"]
+    check_fields((got[0], got[1:4], got[4:7]), (want[0], want[1:4], want[4:7]), precision, "sampled")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pipe_64x64x128_full_size_sampled(precision):
+    g = golden.load("pipe_64x64x128")
+    _sampled(W.pipe_64x64x128(precision=precision), g, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ramp_96x96x512_full_size_sampled(precision):
+    g = golden.load("ramp_96x96x512")
+    _sampled(W.pipe_ramp_96x96x512(Rm=1e-2, precision=precision, perturb=0.01, seed=7), g, precision)
+
+
+# ------------------------------------------------------------- API behaviour
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_host_equals_device_stepping(precision):
+    p = W.small_pipe(nx=20, ny=20, nz=9, diameter=14.0, precision=precision, n_mag=30)
+    with Solver(p) as a, Solver(p) as b:
+        rho, u, bb = a.state()
+        a.step(9)
+        ra, ua, ba = a.state()
+        import ctypes as C
+        ro, uo, bo = np.empty(a.n), np.empty(3 * a.n), np.empty(3 * a.n)
+        from paper_2211_09370_gb300 import _lib
+        obs = _lib.qslbm_obs()
+        dp = lambda z: z.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+        rc = b.L.qslbm_step_host(b.h, dp(rho.ravel().copy()), dp(u.ravel().copy()), dp(bb.ravel().copy()), 0, 9,
+                                 dp(ro), dp(uo), dp(bo), C.byref(obs))
+        assert rc == 0 and obs.step == 9
+    np.testing.assert_array_equal(uo.reshape(ua.shape), ua)
+    np.testing.assert_array_equal(bo.reshape(ba.shape), ba)
+    np.testing.assert_array_equal(ro.reshape(ra.shape), ra)
+
+
+def test_fp32_runs_are_deterministic():
+    p = W.small_pipe(nx=30, ny=30, nz=10, diameter=22.0, n_mag=50)
+    outs = []
+    for _ in range(2):
+        with Solver(p) as s:
+            s.step(11)
+            outs.append(s.state())
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_zero_steps_and_state_roundtrip():
+    p = W.small_pipe(nx=16, ny=16, nz=5, diameter=10.0, precision="fp64")
+    rng = np.random.default_rng(0)
+    with Solver(p) as s:
+        s.step(0)
+        assert s.t == 0
+        rho = 1 + 1e-3 * rng.standard_normal((5, 16, 16))
+        u = 1e-2 * rng.standard_normal((3, 5, 16, 16))
+        b = 1e-4 * rng.standard_normal((3, 5, 16, 16))
+        s.set_state(rho, u, b, t=42)
+        r2, u2, b2 = s.state()
+        assert s.t == 42
+    np.testing.assert_array_equal(u2, u)
+    np.testing.assert_array_equal(b2, b)
+    np.testing.assert_allclose(r2, rho, rtol=0, atol=2e-16)
+
+
+def test_non_finite_state_is_reported():
+    # fault injected on the host: a NaN in the uploaded velocity
+    p = W.small_pipe(nx=12, ny=12, nz=4, diameter=8.0)
+    with Solver(p) as s:
+        rho, u, b = s.state()
+        u[1, 2, 3, 4] = np.nan
+        s.set_state(rho, u, b, t=0)
+        with pytest.raises(QSLBMError) as e:
+            s.observables()
+        assert e.value.code == EUNSTABLE
+        assert s.observables(allow_unstable=True)["nan_flag"] == 1
