@@ -19,6 +19,8 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUDGET, ENOTFOUND, EARCH = 0, -
 CHANNEL, PIPE, PERIODIC = 0, 1, 2
 B0_UNIFORM, B0_TANH = 0, 1
 FP32, FP64 = 0, 1
+SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT = 0, 1, 2
+SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT}
 GEOMETRY = {"channel": CHANNEL, "pipe": PIPE, "none": PERIODIC, "periodic": PERIODIC}
 B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH}
 PRECISION = {"fp32": FP32, "fp64": FP64}
@@ -33,7 +35,7 @@ class qslbm_params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
-        ("stream", C.c_void_p),
+        ("sweep_kernel", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -41,7 +43,7 @@ class qslbm_units(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
     _fields_ += [("n_mag", C.c_int32), ("n_markers", C.c_int32), ("nodes", C.c_int64), ("device_bytes", C.c_int64),
-                ("shell_nodes", C.c_int64)]
+                ("shell_nodes", C.c_int64), ("sweep_kernel", C.c_int32)]
 
 
 class qslbm_obs(C.Structure):
@@ -138,6 +140,8 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.strict_qs = int(p.get("strict_qs", 0))
     q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
     q.perturb = float(p.get("perturb", 0.0))
+    k = p.get("sweep_kernel", "auto")
+    q.sweep_kernel = SWEEP_KERNEL[k] if isinstance(k, str) else int(k)
     q.stream = stream
     return q
 
@@ -168,6 +172,7 @@ class Solver:
         check(self.L.qslbm_get_units(self.h, C.byref(u)), "qslbm_get_units")
         self.units = {k: getattr(u, k) for k, _ in qslbm_units._fields_}
         self.units["lambda"] = self.units.pop("lambda_")
+        self.units["sweep_kernel"] = {SWEEP_PLANES: "planes", SWEEP_RESIDENT: "resident"}.get(u.sweep_kernel)
         self.n = int(u.nodes)
         self.shape = (self._q.nz, self._q.ny, self._q.nx)
 

@@ -117,6 +117,7 @@ int validate(const qslbm_params& p) {
     if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
     if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
+    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_RESIDENT) return QSLBM_EINVAL;
     long long n = (long long)p.nx * p.ny * p.nz;
     if (n > (1LL << 31) - 1) return QSLBM_EINVAL;
     return QSLBM_OK;
@@ -376,6 +377,30 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         if ((rc = upload_real(s, &s.bext_z, s.bext_host))) goto fail;
     }
     if ((rc = upload_ib(s))) goto fail;
+    if (s.p.sweep_kernel != QSLBM_SWEEP_PLANES) {
+        cudaError_t e = ops(s).plan_resident(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "plan_resident");
+            goto fail;
+        }
+        if (!s.resident && s.p.sweep_kernel == QSLBM_SWEEP_RESIDENT) {
+            g_last_error = "the resident sweep kernel does not fit this domain";
+            rc = QSLBM_EINVAL;
+            goto fail;
+        }
+    }
+    if (s.resident) {
+        const size_t xb = (size_t)2 * 3 * s.n * s.esz;
+        const size_t sb = sizeof(unsigned int) * (4 + (size_t)s.nz);
+        if ((rc = dev_alloc(s, &s.xbuf, xb))) goto fail;
+        if ((rc = dev_alloc(s, &s.rsync, sb))) goto fail;
+        cudaError_t e = cudaMemsetAsync(s.rsync, 0, sb, s.stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync");
+            goto fail;
+        }
+    }
+    s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : QSLBM_SWEEP_PLANES;
     {
         long long zero = 0;
         cudaError_t e = cudaMemcpyAsync(s.tdev, &zero, sizeof(zero), cudaMemcpyHostToDevice, s.stream);
@@ -450,6 +475,21 @@ int step_impl(State& s, long long nsteps) {
     return QSLBM_OK;
 }
 
+// A resident launch whose neighbour wait timed out leaves err = 1 in the sync
+// block; report it once and reset the counters so the handle stays usable.
+int check_resident(State& s) {
+    if (!s.resident) return QSLBM_OK;
+    int err = 0;
+    QCHK(cudaMemcpyAsync(&err, (char*)s.rsync + 2 * sizeof(unsigned int), sizeof(int), cudaMemcpyDeviceToHost,
+                         s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    if (!err) return QSLBM_OK;
+    QCHK(cudaMemsetAsync(s.rsync, 0, sizeof(unsigned int) * (4 + (size_t)s.nz), s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    g_last_error = "resident sweep kernel: neighbour wait timed out";
+    return QSLBM_ETIMEOUT;
+}
+
 int ensure_staging(State& s) {
     if (s.staging) return QSLBM_OK;
     return dev_alloc(s, (void**)&s.staging, (size_t)7 * s.n * sizeof(double));
@@ -462,6 +502,7 @@ int observe_impl(State& s, qslbm_obs* out) {
     QCHK(cudaMemcpyAsync(r, s.obs_dev, sizeof(r), cudaMemcpyDeviceToHost, s.stream));
     QCHK(cudaMemcpyAsync(s.usnap, s.u[s.fcur], 3 * (size_t)s.n * s.esz, cudaMemcpyDeviceToDevice, s.stream));
     QCHK(cudaStreamSynchronize(s.stream));
+    if (int rc = check_resident(s)) return rc;
     const long long dt = s.t - s.tsnap;
     s.tsnap = s.t;
     if (out) {
@@ -604,7 +645,7 @@ int qslbm_sync(qslbm_handle* h) {
     if (!h) return QSLBM_EINVAL;
     QCHK(cudaStreamSynchronize(h->s.stream));
     QCHK(cudaGetLastError());
-    return QSLBM_OK;
+    return check_resident(h->s);
 }
 
 int qslbm_destroy(qslbm_handle* h) {

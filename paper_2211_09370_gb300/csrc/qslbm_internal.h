@@ -61,6 +61,12 @@ struct State {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    // resident sub-iteration (all sweeps of a step in one cooperative launch)
+    bool resident = false;
+    bool resident_uhalo = false;
+    size_t resident_smem = 0;
+    void* xbuf = nullptr;   // [2][nz][3][P] plane exchange
+    void* rsync = nullptr;  // ResidentSync + flags[nz]
     int graph_steps = 0;
     std::vector<void*> allocations;
     long long device_bytes = 0;
@@ -74,6 +80,9 @@ struct Ops {
     void (*observe)(State&, double fb, cudaStream_t);   // obs_dev[0..10]
     void (*to_f64)(State&, cudaStream_t);               // staging <- state
     void (*from_f64)(State&, int mask, cudaStream_t);   // state <- staging
+    // decide whether the resident sweep kernel fits this domain; sets
+    // s.resident, s.resident_uhalo, s.resident_smem (no allocation)
+    cudaError_t (*plan_resident)(State&);
 };
 
 const Ops& ops_f32();

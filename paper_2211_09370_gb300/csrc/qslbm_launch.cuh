@@ -4,6 +4,7 @@
 
 #include "qslbm_internal.h"
 #include "qslbm_kernels.cuh"
+#include "qslbm_resident.cuh"
 
 namespace qslbm {
 
@@ -54,6 +55,11 @@ struct Launch {
         c.strict_qs = s.p.strict_qs;
         const IBView<T> v = view(s, true);
         const size_t smem = ib_smem(s);
+        if (s.resident && nsweeps > 0) {
+            launch_resident(s, nsweeps, c, v, st);
+            s.bcur ^= 1;
+            return;
+        }
         for (int i = 0; i < nsweeps; ++i) {
             const T* bin = (const T*)s.b[s.bcur];
             T* bout = (T*)s.b[1 - s.bcur];
@@ -64,6 +70,94 @@ struct Launch {
                 k_sweep_ib<T, 2><<<s.nz, kPlaneThreads, smem, st>>>(geo(s), bin, bout, u, c, v);
             s.bcur ^= 1;
         }
+    }
+
+    template <int DIM, bool UHALO>
+    static void resident_launch_one(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
+                                    cudaStream_t st) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)s.nz);
+        cfg.blockDim = dim3(ResidentShape<T>::threads);
+        cfg.dynamicSmemBytes = s.resident_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const T* bin = (const T*)s.b[s.bcur];
+        T* bout = (T*)s.b[1 - s.bcur];
+        const T* u = (const T*)s.u[s.fcur];
+        cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO>, geo(s), bin, bout, u, c, v, (T*)s.xbuf,
+                           (ResidentSync*)s.rsync, nsweeps);
+    }
+
+    static void launch_resident(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
+                                cudaStream_t st) {
+        if (s.dim == 3) {
+            if (s.resident_uhalo)
+                resident_launch_one<3, true>(s, nsweeps, c, v, st);
+            else
+                resident_launch_one<3, false>(s, nsweeps, c, v, st);
+        } else {
+            resident_launch_one<2, false>(s, nsweeps, c, v, st);
+        }
+    }
+
+    template <int DIM, bool UHALO>
+    static cudaError_t try_resident(State& s, size_t smem, bool& ok) {
+        ok = false;
+        auto kern = k_sweeps_resident<T, DIM, UHALO>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cudaSuccess;  // too much shared memory: not resident
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ResidentShape<T>::threads, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        ok = per_sm >= 1 && (long long)per_sm * sms >= s.nz;
+        return cudaSuccess;
+    }
+
+    static cudaError_t plan_resident(State& s) {
+        s.resident = false;
+        const long long P = (long long)s.nx * s.ny;
+        if (P > (long long)kResidentMaxPlane) return cudaSuccess;
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return e;
+        const size_t ring = (size_t)3 * (s.ib.max_ring > 0 ? s.ib.max_ring : 1) * sizeof(T);
+        const size_t base = (size_t)6 * P * sizeof(T) + ring;
+        const size_t halo = (size_t)6 * P * sizeof(T);
+        const size_t reserve = 1024;  // static shared variables and the runtime's own share
+        bool ok = false;
+        if (s.dim == 3 && base + halo + reserve <= (size_t)optin) {
+            if ((e = try_resident<3, true>(s, base + halo, ok)) != cudaSuccess) return e;
+            if (ok) {
+                s.resident = true;
+                s.resident_uhalo = true;
+                s.resident_smem = base + halo;
+                return cudaSuccess;
+            }
+        }
+        if (base + reserve > (size_t)optin) return cudaSuccess;
+        if (s.dim == 3)
+            e = try_resident<3, false>(s, base, ok);
+        else
+            e = try_resident<2, false>(s, base, ok);
+        if (e != cudaSuccess) return e;
+        if (ok) {
+            s.resident = true;
+            s.resident_uhalo = false;
+            s.resident_smem = base;
+        }
+        return cudaSuccess;
     }
 
     static void force_flow(State& s, cudaStream_t st) {
@@ -130,7 +224,7 @@ struct Launch {
     }
 
     static const Ops& table() {
-        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64};
+        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64, &plan_resident};
         return o;
     }
 };

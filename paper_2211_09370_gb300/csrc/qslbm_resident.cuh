@@ -1,0 +1,204 @@
+// Resident magnetic sub-iteration: one launch runs all N_mag sweeps (Sec. V.G)
+// with the IB corrector on b after each (Sec. V.D, V.F), for domains whose z
+// planes fit one per CTA with every CTA co-resident (cooperative launch).
+//
+// Each CTA keeps its plane's b and u in shared memory for the whole launch.
+// Per sweep it needs only the two neighbouring planes' b from the previous
+// sweep; those travel through a double-buffered exchange array in global
+// memory.  A CTA publishes its plane by bumping a per-plane counter with a
+// release store after writing it, and waits (acquire loads, bounded by a
+// one-second timeout that raises an error flag instead of hanging) for its two
+// neighbours' counters before reading their planes.  Plane-local IB (markers on
+// integer z) runs entirely in shared memory.
+#pragma once
+
+#include "qslbm_kernels.cuh"
+
+namespace qslbm {
+
+// Launch shape: FP32 uses 512 threads with up to 16 nodes each (registers
+// hold a thread's new values until the whole plane has been read); FP64 uses
+// 1024 threads with up to 8 nodes each.  Either covers planes of 8192 nodes.
+template <typename T>
+struct ResidentShape {
+    static constexpr int threads = sizeof(T) == 4 ? 512 : 1024;
+    static constexpr int npt = sizeof(T) == 4 ? 16 : 8;
+};
+constexpr int kResidentMaxPlane = 8192;
+constexpr unsigned long long kWaitTimeoutNs = 1000000000ULL;
+
+// Counters in device memory: flags[z] counts the planes CTA z has published;
+// epoch is the count at the start of the current launch.
+struct ResidentSync {
+    unsigned int epoch;
+    unsigned int done;
+    int err;   // 1: a wait timed out
+    int pad;
+    unsigned int flags[1];  // [nz]
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+    return __ldcg(p);
+}
+
+template <typename T, int DIM, bool UHALO, int kResidentThreads = ResidentShape<T>::threads,
+          int kResidentMaxNpt = ResidentShape<T>::npt>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+    k_sweeps_resident(Geo g, const T* __restrict__ b_in, T* __restrict__ b_out, const T* __restrict__ u,
+                      SweepCoef<T> c, IBView<T> ib, T* xbuf, ResidentSync* sync, int nsweeps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned int s_epoch;
+    __shared__ int s_abort;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int P = nx * ny;
+    const long long n = g.n;
+    const int z = blockIdx.x;
+    const int zm = DIM == 3 ? wrap_dec(z, nz) : z, zp = DIM == 3 ? wrap_inc(z, nz) : z;
+    T* sb = reinterpret_cast<T*>(smem_raw);  // [3][P] own b
+    T* su = sb + 3 * P;                      // [3][P] own u
+    T* suh = su + 3 * P;                     // [2][3][P] u of planes zm, zp (UHALO)
+    T* sdelta = UHALO ? suh + 6 * P : suh;   // [3 * ring]
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_epoch = *(volatile unsigned int*)&sync->epoch;
+        s_abort = 0;
+    }
+    const long long base = (long long)z * P;
+    for (int p = tid; p < P; p += kResidentThreads) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            sb[a * P + p] = b_in[a * n + base + p];
+            su[a * P + p] = u[a * n + base + p];
+            if (UHALO) {
+                suh[a * P + p] = u[a * n + (long long)zm * P + p];
+                suh[(3 + a) * P + p] = u[a * n + (long long)zp * P + p];
+            }
+        }
+    }
+    T be_c[3], be_m[3], be_p[3];
+    bext_at(c.bext_z, c.be, z, be_c);
+    bext_at(c.bext_z, c.be, zm, be_m);
+    bext_at(c.bext_z, c.be, zp, be_p);
+    __syncthreads();
+    const unsigned int epoch = s_epoch;
+    const long long xplane = 3LL * P;
+    for (int s = 0; s < nsweeps; ++s) {
+        // neighbour planes of the previous sweep
+        if (DIM == 3 && s > 0) {
+            if (tid == 0) {
+                const unsigned int target = epoch + (unsigned int)s;
+                const unsigned long long t0 = globaltimer_ns();
+                while ((int)(ld_acquire_u32(&sync->flags[zm]) - target) < 0 ||
+                       (int)(ld_acquire_u32(&sync->flags[zp]) - target) < 0) {
+                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+                        atomicExch(&sync->err, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __syncthreads();
+            if (s_abort) return;
+        }
+        const T* xin = xbuf + (long long)((s - 1) & 1) * nz * xplane;
+        T nv[kResidentMaxNpt][3];
+#pragma unroll
+        for (int k = 0; k < kResidentMaxNpt; ++k) {
+            const int p = tid + k * kResidentThreads;
+            if (p < P) {
+            const int x = p % nx, y = p / nx;
+            const int qn[4] = {y * nx + wrap_dec(x, nx), y * nx + wrap_inc(x, nx), wrap_dec(y, ny) * nx + x,
+                               wrap_inc(y, ny) * nx + x};
+            T acc[3] = {c.w0 * sb[p], c.w0 * sb[P + p], c.w0 * sb[2 * P + p]};
+            T diff[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int d = 0; d < 2 * DIM; ++d) {
+                T bq[3], uq[3];
+                const T* bez = be_c;
+                if (d < 4) {
+                    const int q = qn[d];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        bq[a] = sb[a * P + q];
+                        uq[a] = su[a * P + q];
+                    }
+                } else {
+                    const int zn = d == 4 ? zm : zp;
+                    bez = d == 4 ? be_m : be_p;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        bq[a] = s == 0 ? b_in[a * n + (long long)zn * P + p]
+                                       : ldcg(xin + (long long)zn * xplane + (long long)a * P + p);
+                        uq[a] = UHALO ? suh[((d == 4 ? 0 : 3) + a) * P + p] : u[a * n + (long long)zn * P + p];
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
+                T B[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+                T phi[3];
+                flux_pair(uq, B, d >> 1, phi);
+                const T sgn = (d & 1) ? T(-1) : T(1);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nv[k][a] = acc[a] + c.w1 * c.kappa * diff[a];
+            }
+        }
+        __syncthreads();  // every read of the old plane is done
+#pragma unroll
+        for (int k = 0; k < kResidentMaxNpt; ++k) {
+            const int p = tid + k * kResidentThreads;
+            if (p < P) {
+                sb[p] = nv[k][0];
+                sb[P + p] = nv[k][1];
+                sb[2 * P + p] = nv[k][2];
+            }
+        }
+        ib_plane<T>(ib, sb, sb + P, sb + 2 * P, 0, nx, z, sdelta);
+        __syncthreads();
+        if (DIM == 3 && s + 1 < nsweeps) {
+            T* xout = xbuf + (long long)(s & 1) * nz * xplane + (long long)z * xplane;
+            for (int p = tid; p < 3 * P; p += kResidentThreads) __stcg(xout + p, sb[p]);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release_u32(&sync->flags[z], epoch + (unsigned int)s + 1u);
+            }
+        }
+    }
+    for (int p = tid; p < P; p += kResidentThreads) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) b_out[a * n + base + p] = sb[a * P + p];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(&sync->done, 1u);
+        if (prev == gridDim.x - 1) {
+            sync->done = 0;
+            sync->epoch = epoch + (unsigned int)nsweeps;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace qslbm

@@ -15,6 +15,7 @@ import pytest
 import oracle
 from paper_2211_09370_gb300 import workloads as W
 from paper_2211_09370_gb300._lib import EUNSTABLE, QSLBMError, Solver
+from tests.parity_cases import DEGENERATE, FP64_CASES, degenerate
 
 pytestmark = pytest.mark.gpu
 
@@ -65,44 +66,32 @@ def run_both(p, steps, t0=0):
 
 # ------------------------------------------------------- small, ragged sizes
 
+KERNELS = ["planes", "resident"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_small_pipe_matches_oracle(precision):
-    # 29 x 27 planes: 783 nodes, two strides of 512 threads with a ragged tail
-    p = W.small_pipe(nx=29, ny=27, nz=11, diameter=19.0, precision=precision)
-    got, want, _ = run_both(p, 12)
-    check_fields(got, want, precision, "small pipe")
+@pytest.mark.parametrize("name", sorted(FP64_CASES))
+def test_parity_cases(name, precision, kernel):
+    # ragged planes (e.g. 29 x 27 = 783 nodes: two 512-thread strides plus a
+    # tail), ramped field with a pulsating force, an odd 2-D channel, and a
+    # smooth start over 150 steps; each on both sweep kernels
+    p, steps, t0 = FP64_CASES[name]
+    got, want, _ = run_both(dict(p, precision=precision, sweep_kernel=kernel), steps, t0=t0)
+    check_fields(got, want, precision, name)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_small_ramp_pulsating_pipe(precision):
-    p = W.small_pipe(nx=24, ny=22, nz=40, diameter=16.0, Re=500.0, Ha=50.0, Rm=0.1, b0_kind="tanh",
-                     ramp_center=20.0, ramp_width=4.0, force_amp=0.2, force_period=50.0, perturb=0.01,
-                     seed=9, precision=precision)
-    got, want, _ = run_both(p, 8, t0=13)
-    check_fields(got, want, precision, "ramp")
-
-
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_channel_2d_odd_size(precision):
-    p = W.hartmann_channel_2d(nx=37, ny=20, diameter=19.0, n_mag=60, precision=precision, perturb=0.02,
-                              seed=3)
-    got, want, _ = run_both(p, 40)
-    check_fields(got, want, precision, "channel")
-
-
-@pytest.mark.parametrize("case", ["periodic", "single_plane", "strict_qs", "no_field", "one_sweep"])
-def test_degenerate_cases_fp64(case):
-    base = dict(nx=13, ny=11, nz=7, diameter=8.0, precision="fp64", perturb=0.05, seed=11, n_mag=20)
-    extra = {"periodic": dict(geometry="none"), "single_plane": dict(nz=1), "strict_qs": dict(strict_qs=1),
-             "no_field": dict(Ha=0.0), "one_sweep": dict(n_mag=1)}[case]
-    base.update(extra)
-    p = W.small_pipe(**base)
-    got, want, _ = run_both(p, 10)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("case", sorted(DEGENERATE))
+def test_degenerate_cases_fp64(case, kernel):
+    p, steps = degenerate(case)
+    got, want, _ = run_both(dict(p, precision="fp64", sweep_kernel=kernel), steps)
     check_fields(got, want, "fp64", case)
 
 
-def test_mag_sweeps_with_frozen_velocity_fp64():
-    p = W.small_pipe(nx=22, ny=22, nz=6, diameter=15.0, precision="fp64")
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mag_sweeps_with_frozen_velocity_fp64(kernel):
+    p = W.small_pipe(nx=22, ny=22, nz=6, diameter=15.0, precision="fp64", sweep_kernel=kernel)
     z, y, x = np.meshgrid(np.arange(6.0), np.arange(22.0), np.arange(22.0), indexing="ij")
     u = np.stack([0.01 * np.sin(2 * np.pi * y / 22), 0.02 * np.cos(2 * np.pi * x / 22), 0.03 + 0.0 * x])
     o = oracle.Oracle(p)
@@ -118,7 +107,7 @@ def test_mag_sweeps_with_frozen_velocity_fp64():
 
 
 def test_observables_match_oracle_fp64():
-    p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2)
+    p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
     with Solver(p) as s:
         s.step(10)
@@ -195,8 +184,9 @@ def test_step_host_equals_device_stepping(precision):
     np.testing.assert_array_equal(ro.reshape(ra.shape), ra)
 
 
-def test_fp32_runs_are_deterministic():
-    p = W.small_pipe(nx=30, ny=30, nz=10, diameter=22.0, n_mag=50)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_runs_are_deterministic(kernel):
+    p = W.small_pipe(nx=30, ny=30, nz=10, diameter=22.0, n_mag=50, sweep_kernel=kernel)
     outs = []
     for _ in range(2):
         with Solver(p) as s:
@@ -234,3 +224,28 @@ def test_non_finite_state_is_reported():
             s.observables()
         assert e.value.code == EUNSTABLE
         assert s.observables(allow_unstable=True)["nan_flag"] == 1
+
+
+def test_kernel_selection_reported():
+    with Solver(W.pipe_64x64x128(nz=16)) as s:
+        assert s.units["sweep_kernel"] == "resident"
+    with Solver(W.pipe_64x64x128(nz=16, sweep_kernel="planes")) as s:
+        assert s.units["sweep_kernel"] == "planes"
+    # 96 x 96 planes exceed the resident kernel's 8192-node plane limit
+    with Solver(W.pipe_ramp_96x96x512(nz=8)) as s:
+        assert s.units["sweep_kernel"] == "planes"
+    with pytest.raises(QSLBMError):
+        Solver(W.pipe_ramp_96x96x512(nz=8, sweep_kernel="resident"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_resident_and_plane_kernels_agree(precision):
+    # the two sweep kernels evaluate the same expressions in the same order
+    p = W.small_pipe(nx=40, ny=36, nz=12, diameter=28.0, precision=precision, n_mag=80)
+    outs = []
+    for k in KERNELS:
+        with Solver(dict(p, sweep_kernel=k)) as s:
+            s.step(6)
+            outs.append(s.state())
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
