@@ -442,6 +442,8 @@ int capture_chunk(State& s, int bc, int fc, cudaGraphExec_t* exec) {
         ops(s).force_flow(s, s.stream);
     }
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    s.graph_next[bc][fc][0] = s.bcur;
+    s.graph_next[bc][fc][1] = s.fcur;
     s.bcur = save_b;
     s.fcur = save_f;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -462,8 +464,9 @@ int step_impl(State& s, long long nsteps) {
             if (rc) return rc;
         }
         QCHK(cudaGraphLaunch(ex, s.stream));
-        s.bcur ^= (int)(((long long)kGraphSteps * s.units.n_mag) & 1);
-        s.fcur ^= kGraphSteps & 1;
+        const int nb = s.graph_next[s.bcur][s.fcur][0], nf = s.graph_next[s.bcur][s.fcur][1];
+        s.bcur = nb;
+        s.fcur = nf;
         done += kGraphSteps;
     }
     for (; done < nsteps; ++done) {
@@ -471,6 +474,11 @@ int step_impl(State& s, long long nsteps) {
         o.force_flow(s, s.stream);
     }
     QCHK(cudaGetLastError());
+    if (s.launch_error) {
+        s.launch_error = false;
+        g_last_error = "cudaLaunchKernelEx failed for the resident sweep kernel";
+        return QSLBM_ECUDA;
+    }
     s.t += nsteps;
     return QSLBM_OK;
 }
@@ -607,6 +615,11 @@ int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps) {
     if (!h || nsweeps < 0) return QSLBM_EINVAL;
     ops(h->s).sweeps(h->s, nsweeps, h->s.stream);
     QCHK(cudaGetLastError());
+    if (h->s.launch_error) {
+        h->s.launch_error = false;
+        g_last_error = "cudaLaunchKernelEx failed for the resident sweep kernel";
+        return QSLBM_ECUDA;
+    }
     return QSLBM_OK;
 }
 

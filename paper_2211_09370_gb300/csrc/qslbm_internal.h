@@ -61,8 +61,10 @@ struct State {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int graph_next[2][2][2] = {};  // ping-pong parity (bcur, fcur) after each graph
     // resident sub-iteration (all sweeps of a step in one cooperative launch)
     bool resident = false;
+    bool launch_error = false;  // a cudaLaunchKernelEx call failed
     bool resident_uhalo = false;
     size_t resident_smem = 0;
     void* xbuf = nullptr;   // [2][nz][3][P] plane exchange

@@ -88,8 +88,10 @@ struct Launch {
         const T* bin = (const T*)s.b[s.bcur];
         T* bout = (T*)s.b[1 - s.bcur];
         const T* u = (const T*)s.u[s.fcur];
-        cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO>, geo(s), bin, bout, u, c, v, (T*)s.xbuf,
-                           (ResidentSync*)s.rsync, nsweeps);
+        // a failed launch is recorded for cudaGetLastError, which the caller checks
+        if (cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO>, geo(s), bin, bout, u, c, v,
+                               (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps) != cudaSuccess)
+            s.launch_error = true;
     }
 
     static void launch_resident(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
