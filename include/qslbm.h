@@ -182,6 +182,43 @@ int qslbm_sync(qslbm_handle* h);
 /* Release the handle and its device memory (synchronises first). */
 int qslbm_destroy(qslbm_handle* h);
 
+/* Allocation-free diagnostics (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory when they need the
+ * diagnostics: code recording a CUDA graph, where cudaMalloc is refused while
+ * the stream is captured; code whose device memory belongs to another
+ * allocator that already holds the pool; loops that must not enter the
+ * driver's allocator).
+ *
+ * Computes the diagnostics of qslbm_observables for fields the caller passes,
+ * writing into out[0..9], on the device, in this order: mass, mass_drift, E_k,
+ * E_m, pump, visc, joule, qs_residual, steady_residual, nan_flag (1.0 or 0.0).
+ *   h                 handle giving geometry, coefficients and the initial mass;
+ *                     its own fields are not read or written
+ *   drho, u, b        device arrays in the handle's precision (float for
+ *                     QSLBM_FP32, double for QSLBM_FP64), layout
+ *                     [component][z][y][x]; drho = rho - 1, u and b three
+ *                     components each
+ *   u_prev            device array like u: the velocity steps_since_prev steps
+ *                     earlier (for the steady residual; 0 steps gives 0)
+ *   fb                body force for the pumping term (F0 (1 + amp sin(...)))
+ *   out               device pointer to 10 doubles, written by the call
+ *   stream            cudaStream_t to queue the work on, or NULL
+ * The partial sums live in one fixed array inside the library, sized for
+ * QSLBM_STATIC_MAX_PLANES z planes (one reduction block per plane,
+ * (4096 + 1) x 11 doubles, about 360 KB held by every GPU that loads the
+ * library until the process exits).  A domain with more planes is rejected
+ * with QSLBM_EINVAL (qslbm_last_error names the limit).  No device memory is
+ * allocated or freed.  The first call on a device looks up that array's
+ * device address and should be made before any stream capture starts.  Every
+ * call on a device shares the array (each call overwrites what it uses, nothing
+ * has to start at zero): calls that may run at the same time on the GPU
+ * (unordered streams) race and must be serialised by the caller.
+ * Asynchronous; errors: QSLBM_EINVAL (NULL argument, too many planes),
+ * QSLBM_ECUDA. */
+#define QSLBM_STATIC_MAX_PLANES 4096
+int qslbm_observables_static(const qslbm_handle* h, const void* drho, const void* u, const void* b,
+                             const void* u_prev, double fb, int64_t steps_since_prev, double* out, void* stream);
+
 /* Static string for a code, and the text of the last CUDA error seen by the
  * calling thread (empty if none). */
 const char* qslbm_strerror(int code);

@@ -55,7 +55,7 @@ class qslbm_obs(C.Structure):
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = ("qslbm_params_init", "qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps",
            "qslbm_observables", "qslbm_get_state", "qslbm_set_state", "qslbm_step_host", "qslbm_sync",
-           "qslbm_destroy", "qslbm_strerror", "qslbm_last_error")
+           "qslbm_destroy", "qslbm_strerror", "qslbm_last_error", "qslbm_observables_static")
 
 _lib = None
 
@@ -83,6 +83,9 @@ def load(path: str | None = None):
     L.qslbm_destroy.argtypes = [hp]
     L.qslbm_strerror.argtypes = [C.c_int]
     L.qslbm_strerror.restype = C.c_char_p
+    L.qslbm_observables_static.argtypes = [hp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                           C.c_int64, C.c_void_p, C.c_void_p]
+    L.qslbm_observables_static.restype = C.c_int
     L.qslbm_last_error.argtypes = []
     L.qslbm_last_error.restype = C.c_char_p
     for name in ("qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps", "qslbm_observables",

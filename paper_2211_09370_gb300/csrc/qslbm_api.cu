@@ -574,6 +574,11 @@ int set_fields(State& s, const double* rho, const double* u, const double* b, lo
 
 }  // namespace
 
+namespace qslbm {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const State& handle_state(const qslbm_handle* h) { return h->s; }
+}  // namespace qslbm
+
 extern "C" {
 
 void qslbm_params_init(qslbm_params* p) {
