@@ -64,13 +64,15 @@ extern "C" {
 #define QSLBM_FP64 1
 
 /* Magnetic sub-iteration kernels.  PLANES: one launch per sweep, one CTA per
- * z plane.  RESIDENT: one cooperative launch per step keeps every plane in
- * shared memory (needs nz co-resident CTAs and a plane of at most 8192 nodes;
- * create fails with QSLBM_EINVAL if the domain does not fit).  AUTO picks
- * RESIDENT when it fits. */
+ * z plane (sweep and IB fused).  RESIDENT: one cooperative launch per step
+ * keeps every plane in shared memory (needs nz co-resident CTAs and a plane of
+ * at most 8192 nodes; create fails with QSLBM_EINVAL if the domain does not
+ * fit).  SPLIT: per sweep a node-parallel sweep launch and a per-plane IB
+ * launch.  AUTO picks RESIDENT when it fits, otherwise SPLIT. */
 #define QSLBM_SWEEP_AUTO 0
 #define QSLBM_SWEEP_PLANES 1
 #define QSLBM_SWEEP_RESIDENT 2
+#define QSLBM_SWEEP_SPLIT 3
 
 /* Problem statement of the paper (Sec. II: Re, Rm, Ha with L = pipe radius;
  * Sec. IV: pipe, insulating walls, pressure gradient; Sec. VI: non-uniform
@@ -98,7 +100,7 @@ typedef struct qslbm_params {
     int32_t strict_qs;      /* 1: induction flux from B^ext only; default 0        */
     uint64_t seed;          /* initial perturbation seed                           */
     double perturb;         /* initial |u| noise, fraction of U0, inside the wall  */
-    int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT    */
+    int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT | _SPLIT */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 
@@ -110,7 +112,7 @@ typedef struct qslbm_units {
     int64_t nodes;
     int64_t device_bytes; /* device memory the handle holds */
     int64_t shell_nodes;  /* nodes inside the support of some wall marker */
-    int32_t sweep_kernel; /* QSLBM_SWEEP_PLANES or QSLBM_SWEEP_RESIDENT in use  */
+    int32_t sweep_kernel; /* the QSLBM_SWEEP_* kernel in use (never AUTO)        */
 } qslbm_units;
 
 /* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2

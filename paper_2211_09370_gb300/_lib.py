@@ -19,8 +19,8 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUDGET, ENOTFOUND, EARCH = 0, -
 CHANNEL, PIPE, PERIODIC = 0, 1, 2
 B0_UNIFORM, B0_TANH = 0, 1
 FP32, FP64 = 0, 1
-SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT = 0, 1, 2
-SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT}
+SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT, SWEEP_SPLIT = 0, 1, 2, 3
+SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT, "split": SWEEP_SPLIT}
 GEOMETRY = {"channel": CHANNEL, "pipe": PIPE, "none": PERIODIC, "periodic": PERIODIC}
 B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH}
 PRECISION = {"fp32": FP32, "fp64": FP64}
@@ -175,7 +175,8 @@ class Solver:
         check(self.L.qslbm_get_units(self.h, C.byref(u)), "qslbm_get_units")
         self.units = {k: getattr(u, k) for k, _ in qslbm_units._fields_}
         self.units["lambda"] = self.units.pop("lambda_")
-        self.units["sweep_kernel"] = {SWEEP_PLANES: "planes", SWEEP_RESIDENT: "resident"}.get(u.sweep_kernel)
+        self.units["sweep_kernel"] = {SWEEP_PLANES: "planes", SWEEP_RESIDENT: "resident",
+                                      SWEEP_SPLIT: "split"}.get(u.sweep_kernel)
         self.n = int(u.nodes)
         self.shape = (self._q.nz, self._q.ny, self._q.nx)
 

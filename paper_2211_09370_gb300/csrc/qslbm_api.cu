@@ -117,7 +117,7 @@ int validate(const qslbm_params& p) {
     if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
     if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
-    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_RESIDENT) return QSLBM_EINVAL;
+    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_SPLIT) return QSLBM_EINVAL;
     long long n = (long long)p.nx * p.ny * p.nz;
     if (n > (1LL << 31) - 1) return QSLBM_EINVAL;
     return QSLBM_OK;
@@ -377,7 +377,7 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         if ((rc = upload_real(s, &s.bext_z, s.bext_host))) goto fail;
     }
     if ((rc = upload_ib(s))) goto fail;
-    if (s.p.sweep_kernel != QSLBM_SWEEP_PLANES) {
+    if (s.p.sweep_kernel == QSLBM_SWEEP_AUTO || s.p.sweep_kernel == QSLBM_SWEEP_RESIDENT) {
         cudaError_t e = ops(s).plan_resident(s);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "plan_resident");
@@ -400,7 +400,8 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
             goto fail;
         }
     }
-    s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : QSLBM_SWEEP_PLANES;
+    if (!s.resident && s.p.sweep_kernel == QSLBM_SWEEP_AUTO) s.p.sweep_kernel = QSLBM_SWEEP_SPLIT;
+    s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : s.p.sweep_kernel;
     {
         long long zero = 0;
         cudaError_t e = cudaMemcpyAsync(s.tdev, &zero, sizeof(zero), cudaMemcpyHostToDevice, s.stream);

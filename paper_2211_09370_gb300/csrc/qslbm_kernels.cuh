@@ -157,6 +157,48 @@ __device__ __forceinline__ void flux_pair(const T u[3], const T B[3], int beta, 
     for (int a = 0; a < 3; ++a) phi[a] = u[beta] * B[a] - u[a] * B[beta];
 }
 
+// One node of the sweep: in-plane index p of the plane at base, z neighbours
+// at zmbase / zpbase.  Neighbours enter in the order -x, +x, -y, +y, -z, +z.
+template <typename T, int DIM>
+__device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* __restrict__ u, long long n, int nx,
+                                           int ny, long long base, long long zmbase, long long zpbase, int p,
+                                           const SweepCoef<T>& c, const T be_c[3], const T be_m[3],
+                                           const T be_p[3], T out[3]) {
+    const int y = p / nx;
+    const int x = p - y * nx;
+    const long long k = base + p;
+    long long nb[6];  // -x, +x, -y, +y, -z, +z
+    nb[0] = base + (long long)y * nx + wrap_dec(x, nx);
+    nb[1] = base + (long long)y * nx + wrap_inc(x, nx);
+    nb[2] = base + (long long)wrap_dec(y, ny) * nx + x;
+    nb[3] = base + (long long)wrap_inc(y, ny) * nx + x;
+    nb[4] = zmbase + p;
+    nb[5] = zpbase + p;
+    T acc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[a] = c.w0 * bin[k + a * n];
+    T diff[3] = {T(0), T(0), T(0)};  // sum_beta Phi_ab(x - e_beta) - Phi_ab(x + e_beta)
+#pragma unroll
+    for (int d = 0; d < 2 * DIM; ++d) {
+        const long long q = nb[d];
+        const T bq[3] = {bin[q], bin[q + n], bin[q + 2 * n]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
+        const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
+        const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
+        T B[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+        T phi[3];
+        flux_pair(uq, B, d >> 1, phi);
+        const T sgn = (d & 1) ? T(-1) : T(1);  // x - e_beta enters with +, x + e_beta with -
+#pragma unroll
+        for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = acc[a] + c.w1 * c.kappa * diff[a];
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kPlaneThreads) k_sweep_ib(Geo g, const T* __restrict__ bin, T* bout,
                                                             const T* __restrict__ u, SweepCoef<T> c,
@@ -173,54 +215,52 @@ __global__ void __launch_bounds__(kPlaneThreads) k_sweep_ib(Geo g, const T* __re
     bext_at(c.bext_z, c.be, z, be_c);
     bext_at(c.bext_z, c.be, zm, be_m);
     bext_at(c.bext_z, c.be, zp, be_p);
-    const T* b0 = bin;
-    const T* b1 = bin + n;
-    const T* b2 = bin + 2 * n;
-    const T* u0 = u;
-    const T* u1 = u + n;
-    const T* u2 = u + 2 * n;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const int x = p % nx, y = p / nx;
-        const long long k = base + p;
-        long long nb[2 * DIM];  // -x, +x, -y, +y, (-z, +z)
-        nb[0] = base + (long long)y * nx + wrap_dec(x, nx);
-        nb[1] = base + (long long)y * nx + wrap_inc(x, nx);
-        nb[2] = base + (long long)wrap_dec(y, ny) * nx + x;
-        nb[3] = base + (long long)wrap_inc(y, ny) * nx + x;
-        if (DIM == 3) {
-            nb[4] = (long long)zm * P + p;
-            nb[5] = (long long)zp * P + p;
-        }
-        T acc[3];
-        acc[0] = c.w0 * b0[k];
-        acc[1] = c.w0 * b1[k];
-        acc[2] = c.w0 * b2[k];
-        T diff[3] = {T(0), T(0), T(0)};  // sum_beta Phi_ab(x - e_beta) - Phi_ab(x + e_beta)
-#pragma unroll
-        for (int d = 0; d < 2 * DIM; ++d) {
-            const long long q = nb[d];
-            const T bq[3] = {b0[q], b1[q], b2[q]};
-            acc[0] += c.w1 * bq[0];
-            acc[1] += c.w1 * bq[1];
-            acc[2] += c.w1 * bq[2];
-            const T uq[3] = {u0[q], u1[q], u2[q]};
-            const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
-            T B[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
-            T phi[3];
-            flux_pair(uq, B, d >> 1, phi);
-            const T sgn = (d & 1) ? T(-1) : T(1);  // x - e_beta enters with +, x + e_beta with -
-#pragma unroll
-            for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc[a] += c.w1 * c.kappa * diff[a];
-        bout[k] = acc[0];
-        bout[k + n] = acc[1];
-        bout[k + 2 * n] = acc[2];
+        T o[3];
+        sweep_node<T, DIM>(bin, u, n, nx, ny, base, (long long)zm * P, (long long)zp * P, p, c, be_c, be_m, be_p, o);
+        bout[base + p] = o[0];
+        bout[base + p + n] = o[1];
+        bout[base + p + 2 * n] = o[2];
     }
     ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, nx, z, sdelta);
+}
+
+// Node-parallel sweep without the IB (grid: in-plane blocks x z planes); the
+// IB then runs as k_ib_planes.  For domains above L2 this keeps every SM busy
+// regardless of the plane count.
+constexpr int kNodeThreads = 256;
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kNodeThreads) k_sweep_nodes(Geo g, const T* __restrict__ bin,
+                                                              T* __restrict__ bout, const T* __restrict__ u,
+                                                              SweepCoef<T> c) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int z = blockIdx.y;
+    const int P = nx * ny;
+    const int p = blockIdx.x * kNodeThreads + threadIdx.x;
+    if (p >= P) return;
+    const long long n = g.n;
+    const long long base = (long long)z * P;
+    const int zm = DIM == 3 ? wrap_dec(z, nz) : z, zp = DIM == 3 ? wrap_inc(z, nz) : z;
+    T be_c[3], be_m[3], be_p[3];
+    bext_at(c.bext_z, c.be, z, be_c);
+    bext_at(c.bext_z, c.be, zm, be_m);
+    bext_at(c.bext_z, c.be, zp, be_p);
+    T o[3];
+    sweep_node<T, DIM>(bin, u, n, nx, ny, base, (long long)zm * P, (long long)zp * P, p, c, be_c, be_m, be_p, o);
+    bout[base + p] = o[0];
+    bout[base + p + n] = o[1];
+    bout[base + p + 2 * n] = o[2];
+}
+
+// IB corrector alone, one CTA per z plane (after k_sweep_nodes).
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<T> ib) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const long long n = g.n;
+    const long long base = (long long)blockIdx.x * g.nx * g.ny;
+    ib_plane<T>(ib, f, f + n, f + 2 * n, base, g.nx, blockIdx.x, sdelta);
 }
 
 // ---------------------------------------------------------------------------

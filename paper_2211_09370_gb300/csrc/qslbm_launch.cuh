@@ -60,6 +60,22 @@ struct Launch {
             s.bcur ^= 1;
             return;
         }
+        if (s.p.sweep_kernel == QSLBM_SWEEP_SPLIT) {
+            const int P = s.nx * s.ny;
+            const dim3 grid((unsigned)((P + kNodeThreads - 1) / kNodeThreads), (unsigned)s.nz);
+            for (int i = 0; i < nsweeps; ++i) {
+                const T* bin = (const T*)s.b[s.bcur];
+                T* bout = (T*)s.b[1 - s.bcur];
+                const T* u = (const T*)s.u[s.fcur];
+                if (s.dim == 3)
+                    k_sweep_nodes<T, 3><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
+                else
+                    k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
+                if (s.ib.nm > 0) k_ib_planes<T><<<s.nz, kNodeThreads, smem, st>>>(geo(s), bout, v);
+                s.bcur ^= 1;
+            }
+            return;
+        }
         for (int i = 0; i < nsweeps; ++i) {
             const T* bin = (const T*)s.b[s.bcur];
             T* bout = (T*)s.b[1 - s.bcur];
@@ -72,12 +88,15 @@ struct Launch {
         }
     }
 
-    template <int DIM, bool UHALO>
+    static constexpr int RT = ResidentShape<T>::threads;
+    static constexpr int RN = ResidentShape<T>::npt_small;
+
+    template <int DIM, bool UHALO, int NPT>
     static void resident_launch_one(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
                                     cudaStream_t st) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)s.nz);
-        cfg.blockDim = dim3(ResidentShape<T>::threads);
+        cfg.blockDim = dim3(RT);
         cfg.dynamicSmemBytes = s.resident_smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -89,40 +108,57 @@ struct Launch {
         T* bout = (T*)s.b[1 - s.bcur];
         const T* u = (const T*)s.u[s.fcur];
         // a failed launch is recorded for cudaGetLastError, which the caller checks
-        if (cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO>, geo(s), bin, bout, u, c, v,
+        if (cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO, RT, NPT>, geo(s), bin, bout, u, c, v,
                                (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps) != cudaSuccess)
             s.launch_error = true;
     }
 
     static void launch_resident(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
                                 cudaStream_t st) {
+        const bool small = (long long)s.nx * s.ny <= (long long)RT * RN;
         if (s.dim == 3) {
-            if (s.resident_uhalo)
-                resident_launch_one<3, true>(s, nsweeps, c, v, st);
-            else
-                resident_launch_one<3, false>(s, nsweeps, c, v, st);
+            if (s.resident_uhalo) {
+                if (small)
+                    resident_launch_one<3, true, RN>(s, nsweeps, c, v, st);
+                else
+                    resident_launch_one<3, true, 2 * RN>(s, nsweeps, c, v, st);
+            } else {
+                if (small)
+                    resident_launch_one<3, false, RN>(s, nsweeps, c, v, st);
+                else
+                    resident_launch_one<3, false, 2 * RN>(s, nsweeps, c, v, st);
+            }
         } else {
-            resident_launch_one<2, false>(s, nsweeps, c, v, st);
+            if (small)
+                resident_launch_one<2, false, RN>(s, nsweeps, c, v, st);
+            else
+                resident_launch_one<2, false, 2 * RN>(s, nsweeps, c, v, st);
         }
     }
 
-    template <int DIM, bool UHALO>
-    static cudaError_t try_resident(State& s, size_t smem, bool& ok) {
+    template <int DIM, bool UHALO, int NPT>
+    static cudaError_t try_resident_npt(State& s, size_t smem, bool& ok) {
         ok = false;
-        auto kern = k_sweeps_resident<T, DIM, UHALO>;
+        auto kern = k_sweeps_resident<T, DIM, UHALO, RT, NPT>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return cudaSuccess;  // too much shared memory: not resident
         }
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ResidentShape<T>::threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         ok = per_sm >= 1 && (long long)per_sm * sms >= s.nz;
         return cudaSuccess;
+    }
+
+    template <int DIM, bool UHALO>
+    static cudaError_t try_resident(State& s, size_t smem, bool& ok) {
+        if ((long long)s.nx * s.ny <= (long long)RT * RN) return try_resident_npt<DIM, UHALO, RN>(s, smem, ok);
+        return try_resident_npt<DIM, UHALO, 2 * RN>(s, smem, ok);
     }
 
     static cudaError_t plan_resident(State& s) {

@@ -16,13 +16,14 @@
 
 namespace qslbm {
 
-// Launch shape: FP32 uses 512 threads with up to 16 nodes each (registers
-// hold a thread's new values until the whole plane has been read); FP64 uses
-// 1024 threads with up to 8 nodes each.  Either covers planes of 8192 nodes.
+// Launch shape: FP32 uses 512 threads, FP64 1024 (the register budget of a
+// thread holds its nodes' new values until the whole plane has been read).
+// Each thread takes up to NPT nodes: NPT = 8 / 4 covers planes of 4096 nodes,
+// twice that covers the 8192-node maximum.
 template <typename T>
 struct ResidentShape {
     static constexpr int threads = sizeof(T) == 4 ? 512 : 1024;
-    static constexpr int npt = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int npt_small = sizeof(T) == 4 ? 8 : 4;
 };
 constexpr int kResidentMaxPlane = 8192;
 constexpr unsigned long long kWaitTimeoutNs = 1000000000ULL;
@@ -56,8 +57,7 @@ __device__ __forceinline__ T ldcg(const T* p) {
     return __ldcg(p);
 }
 
-template <typename T, int DIM, bool UHALO, int kResidentThreads = ResidentShape<T>::threads,
-          int kResidentMaxNpt = ResidentShape<T>::npt>
+template <typename T, int DIM, bool UHALO, int kResidentThreads, int kResidentMaxNpt>
 __global__ void __launch_bounds__(kResidentThreads, 1)
     k_sweeps_resident(Geo g, const T* __restrict__ b_in, T* __restrict__ b_out, const T* __restrict__ u,
                       SweepCoef<T> c, IBView<T> ib, T* xbuf, ResidentSync* sync, int nsweeps) {
@@ -98,7 +98,44 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     const unsigned int epoch = s_epoch;
     const long long xplane = 3LL * P;
     for (int s = 0; s < nsweeps; ++s) {
-        // neighbour planes of the previous sweep
+        // (1) in-plane part of the sweep from this CTA's own plane; it overlaps
+        // the neighbours' publication of the previous sweep
+        T nv[kResidentMaxNpt][3];
+#pragma unroll
+        for (int k = 0; k < kResidentMaxNpt; ++k) {
+            const int p = tid + k * kResidentThreads;
+            if (p < P) {
+                const int y = p / nx;
+                const int x = p - y * nx;
+                const int qn[4] = {y * nx + wrap_dec(x, nx), y * nx + wrap_inc(x, nx),
+                                   wrap_dec(y, ny) * nx + x, wrap_inc(y, ny) * nx + x};
+                T acc[3], dif[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[a] = c.w0 * sb[a * P + p];
+                    dif[a] = T(0);
+                }
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    const int q = qn[d];
+                    T uq[3], B[3], phi[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const T bq = sb[a * P + q];
+                        uq[a] = su[a * P + q];
+                        acc[a] += c.w1 * bq;
+                        B[a] = c.strict_qs ? be_c[a] : be_c[a] + bq;
+                    }
+                    flux_pair(uq, B, d >> 1, phi);
+                    const T sgn = (d & 1) ? T(-1) : T(1);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dif[a] += sgn * phi[a];
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nv[k][a] = acc[a] + c.w1 * c.kappa * dif[a];
+            }
+        }
+        // (2) neighbour planes of the previous sweep
         if (DIM == 3 && s > 0) {
             if (tid == 0) {
                 const unsigned int target = epoch + (unsigned int)s;
@@ -110,57 +147,37 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                         s_abort = 1;
                         break;
                     }
-                    __nanosleep(32);
+                    __nanosleep(16);
                 }
             }
             __syncthreads();
             if (s_abort) return;
         }
+        // (3) the z terms: w1 b(z -/+ 1) and w1 kappa (+/-) Phi_az(z -/+ 1)
         const T* xin = xbuf + (long long)((s - 1) & 1) * nz * xplane;
-        T nv[kResidentMaxNpt][3];
 #pragma unroll
         for (int k = 0; k < kResidentMaxNpt; ++k) {
             const int p = tid + k * kResidentThreads;
             if (p < P) {
-            const int x = p % nx, y = p / nx;
-            const int qn[4] = {y * nx + wrap_dec(x, nx), y * nx + wrap_inc(x, nx), wrap_dec(y, ny) * nx + x,
-                               wrap_inc(y, ny) * nx + x};
-            T acc[3] = {c.w0 * sb[p], c.w0 * sb[P + p], c.w0 * sb[2 * P + p]};
-            T diff[3] = {T(0), T(0), T(0)};
+                if (DIM == 3) {
 #pragma unroll
-            for (int d = 0; d < 2 * DIM; ++d) {
-                T bq[3], uq[3];
-                const T* bez = be_c;
-                if (d < 4) {
-                    const int q = qn[d];
+                    for (int d = 4; d < 6; ++d) {
+                        const int zn = d == 4 ? zm : zp;
+                        const T* bez = d == 4 ? be_m : be_p;
+                        T uq[3], B[3], phi[3], bq[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        bq[a] = sb[a * P + q];
-                        uq[a] = su[a * P + q];
-                    }
-                } else {
-                    const int zn = d == 4 ? zm : zp;
-                    bez = d == 4 ? be_m : be_p;
+                        for (int a = 0; a < 3; ++a) {
+                            bq[a] = s == 0 ? b_in[a * n + (long long)zn * P + p]
+                                           : ldcg(xin + (long long)zn * xplane + (long long)a * P + p);
+                            uq[a] = UHALO ? suh[((d == 4 ? 0 : 3) + a) * P + p] : u[a * n + (long long)zn * P + p];
+                            B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+                        }
+                        flux_pair(uq, B, 2, phi);
+                        const T sk = d == 5 ? -c.w1 * c.kappa : c.w1 * c.kappa;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        bq[a] = s == 0 ? b_in[a * n + (long long)zn * P + p]
-                                       : ldcg(xin + (long long)zn * xplane + (long long)a * P + p);
-                        uq[a] = UHALO ? suh[((d == 4 ? 0 : 3) + a) * P + p] : u[a * n + (long long)zn * P + p];
+                        for (int a = 0; a < 3; ++a) nv[k][a] += c.w1 * bq[a] + sk * phi[a];
                     }
                 }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
-                T B[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
-                T phi[3];
-                flux_pair(uq, B, d >> 1, phi);
-                const T sgn = (d & 1) ? T(-1) : T(1);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) nv[k][a] = acc[a] + c.w1 * c.kappa * diff[a];
             }
         }
         __syncthreads();  // every read of the old plane is done
