@@ -249,6 +249,14 @@ int build_markers(State& s) {
         h.shell_off[z + 1] = (int)h.shell_xy.size();
     }
     h.csr_off.push_back((int)h.csr_m.size());
+    h.max_shell = 0;
+    h.max_nnz = 0;
+    for (int z = 0; z < planes; ++z) {
+        const int ns = h.shell_off[z + 1] - h.shell_off[z];
+        h.max_shell = std::max(h.max_shell, ns);
+        if (ns > 0)
+            h.max_nnz = std::max(h.max_nnz, h.csr_off[h.shell_off[z + 1]] - h.csr_off[h.shell_off[z]]);
+    }
     for (double v : h.d)
         if (!(v > 0)) return QSLBM_EINVAL;
     return QSLBM_OK;
@@ -258,11 +266,19 @@ int upload_ib(State& s) {
     qslbm::HostIB& h = s.hib;
     qslbm::DeviceIB& d = s.ib;
     int rc;
+    // per marker the nine in-plane node indices and weights D = D_x D_y
+    const size_t nm = h.X.size();
+    std::vector<int> q9(9 * nm);
+    std::vector<double> w9(9 * nm);
+    for (size_t j = 0; j < nm; ++j)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) {
+                q9[9 * j + 3 * b + a] = h.iy[3 * j + b] * s.nx + h.ix[3 * j + a];
+                w9[9 * j + 3 * b + a] = h.wx[3 * j + a] * h.wy[3 * j + b];
+            }
     if ((rc = upload(s, (void**)&d.ring_off, h.ring_off))) return rc;
-    if ((rc = upload(s, (void**)&d.mk_ix, h.ix))) return rc;
-    if ((rc = upload(s, (void**)&d.mk_iy, h.iy))) return rc;
-    if ((rc = upload_real(s, &d.mk_wx, h.wx))) return rc;
-    if ((rc = upload_real(s, &d.mk_wy, h.wy))) return rc;
+    if ((rc = upload(s, (void**)&d.mk_q, q9))) return rc;
+    if ((rc = upload_real(s, &d.mk_w, w9))) return rc;
     if ((rc = upload_real(s, &d.mk_s, h.s))) return rc;
     if ((rc = upload_real(s, &d.mk_sm, h.sm))) return rc;
     if ((rc = upload(s, (void**)&d.shell_off, h.shell_off))) return rc;
@@ -274,6 +290,8 @@ int upload_ib(State& s) {
     d.ns = (int)h.shell_xy.size();
     d.nnz = (int)h.csr_m.size();
     d.max_ring = h.max_ring;
+    d.max_shell = h.max_shell;
+    d.max_nnz = h.max_nnz;
     return QSLBM_OK;
 }
 

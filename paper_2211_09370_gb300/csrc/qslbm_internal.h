@@ -17,10 +17,10 @@ constexpr int kReduceThreads = 256;
 // Marker and shell tables of the IB corrector (device pointers).  The same
 // tables serve u and b; only the per-marker scaling differs (mk_s, mk_sm).
 struct DeviceIB {
-    int *ring_off = nullptr, *mk_ix = nullptr, *mk_iy = nullptr;
+    int *ring_off = nullptr, *mk_q = nullptr;
     int *shell_off = nullptr, *shell_xy = nullptr, *csr_off = nullptr, *csr_m = nullptr;
-    void *mk_wx = nullptr, *mk_wy = nullptr, *mk_s = nullptr, *mk_sm = nullptr, *csr_w = nullptr;
-    int nm = 0, ns = 0, nnz = 0, max_ring = 0;
+    void *mk_w = nullptr, *mk_s = nullptr, *mk_sm = nullptr, *csr_w = nullptr;
+    int nm = 0, ns = 0, nnz = 0, max_ring = 0, max_shell = 0, max_nnz = 0;
 };
 
 // Host copy of the marker geometry and IB weights (binary64).
@@ -33,7 +33,7 @@ struct HostIB {
     std::vector<double> d, s, sm;
     std::vector<int> shell_off, shell_xy, csr_off, csr_m;
     std::vector<double> csr_w;
-    int max_ring = 0;
+    int max_ring = 0, max_shell = 0, max_nnz = 0;
 };
 
 struct State {

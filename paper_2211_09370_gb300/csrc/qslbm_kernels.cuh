@@ -39,10 +39,8 @@ struct Geo {
 template <typename T>
 struct IBView {
     const int* ring_off;   // [nz + 1]: markers of plane z are ring_off[z] .. ring_off[z+1]-1
-    const int* mk_ix;      // [3 * nm]: wrapped x node of the three x weights
-    const int* mk_iy;      // [3 * nm]
-    const T* mk_wx;        // [3 * nm]: 1-D kernel weights (Sec. V.B)
-    const T* mk_wy;        // [3 * nm]
+    const int* mk_q;       // [9 * nm]: in-plane index y * nx + x of the marker's 3 x 3 support
+    const T* mk_w;         // [9 * nm]: D(x_k - X_j) = D_x D_y there (Sec. V.B)
     const T* mk_s;         // [nm]: lambda / (d (1 + d (lambda - 1)))
     const int* shell_off;  // [nz + 1]: shell nodes of plane z
     const int* shell_xy;   // [ns]: in-plane index y * nx + x of each shell node
@@ -100,24 +98,19 @@ __device__ __forceinline__ void bext_at(const T* bext_z, const T* be, int z, T o
 // Sec. V.C-V.F: delta_j = s_j (0 - D f*), then f += D^T delta.
 template <typename T>
 __device__ __forceinline__ void ib_plane(const IBView<T>& ib, T* f0, T* f1, T* f2, long long plane_base,
-                                         int nx, int z, T* sdelta) {
+                                         int z, T* sdelta) {
     const int m0 = ib.ring_off[z], m1 = ib.ring_off[z + 1];
     if (m1 == m0) return;  // uniform across the CTA: no divergence around barriers
     __syncthreads();
     for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
         T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const T wy = ib.mk_wy[3 * m + b];
-            const long long row = plane_base + (long long)ib.mk_iy[3 * m + b] * nx;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const T w = ib.mk_wx[3 * m + a] * wy;
-                const long long q = row + ib.mk_ix[3 * m + a];
-                a0 += w * f0[q];
-                a1 += w * f1[q];
-                a2 += w * f2[q];
-            }
+        for (int j = 0; j < 9; ++j) {
+            const T w = ib.mk_w[9 * m + j];
+            const long long q = plane_base + ib.mk_q[9 * m + j];
+            a0 += w * f0[q];
+            a1 += w * f1[q];
+            a2 += w * f2[q];
         }
         const T s = ib.mk_s[m];
         const int l = m - m0;
@@ -222,7 +215,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_sweep_ib(Geo g, const T* __re
         bout[base + p + n] = o[1];
         bout[base + p + 2 * n] = o[2];
     }
-    ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, nx, z, sdelta);
+    ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, z, sdelta);
 }
 
 // Node-parallel sweep without the IB (grid: in-plane blocks x z planes); the
@@ -260,7 +253,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<
     T* sdelta = reinterpret_cast<T*>(smem_raw);
     const long long n = g.n;
     const long long base = (long long)blockIdx.x * g.nx * g.ny;
-    ib_plane<T>(ib, f, f + n, f + 2 * n, base, g.nx, blockIdx.x, sdelta);
+    ib_plane<T>(ib, f, f + n, f + 2 * n, base, blockIdx.x, sdelta);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,49 +298,60 @@ __device__ __forceinline__ double flow_w(int j) {
 // (d_beta phi = 3 sum_i w_i c_i,beta phi(x + c_i)), F = F_body(t) e_axis +
 // J x (B^ext + b).  One thread per node.
 template <typename T, int DIM>
+__device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restrict__ F, long long n, int nx, int ny,
+                                           int nz, int x, int y, int z, long long k, const ForceCoef<T>& c,
+                                           T fb) {
+    T db[3][3];  // db[beta][alpha] = d_beta b_alpha
+#pragma unroll
+    for (int be = 0; be < 3; ++be)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) db[be][a] = T(0);
+#pragma unroll
+    for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+        int cx, cy, cz;
+        if (DIM == 3)
+            flow_dir3(j, cx, cy, cz);
+        else
+            flow_dir2(j, cx, cy, cz);
+        const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+        const T w = (T)(3.0 * flow_w<DIM>(j));
+        const T bq[3] = {b[q], b[q + n], b[q + 2 * n]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (cx) db[0][a] += (w * (T)cx) * bq[a];
+            if (cy) db[1][a] += (w * (T)cy) * bq[a];
+            if (cz) db[2][a] += (w * (T)cz) * bq[a];
+        }
+    }
+    const T J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
+    T Be[3];
+    bext_at(c.bext_z, c.be, z, Be);
+    const T B[3] = {Be[0] + b[k], Be[1] + b[k + n], Be[2] + b[k + 2 * n]};
+    T L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
+    L[c.axis] += fb;
+    F[k] = L[0];
+    F[k + n] = L[1];
+    F[k + 2 * n] = L[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T body_force_at(const ForceCoef<T>& c, long long t) {
+    const double fb_d = c.amp != 0.0 ? c.F0 * (1.0 + c.amp * sin(c.omega * (double)t)) : c.F0;
+    return (T)fb_d;
+}
+
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T* __restrict__ F,
                                                ForceCoef<T> c, const long long* __restrict__ tstep) {
     const long long n = g.n;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const long long t = *tstep;
-    const double fb_d = c.amp != 0.0 ? c.F0 * (1.0 + c.amp * sin(c.omega * (double)t)) : c.F0;
-    const T fb = (T)fb_d;
+    const T fb = body_force_at(c, *tstep);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx);
         const int y = (int)((k / nx) % ny);
         const int z = (int)(k / ((long long)nx * ny));
-        T db[3][3];  // db[beta][alpha] = d_beta b_alpha
-#pragma unroll
-        for (int be = 0; be < 3; ++be)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) db[be][a] = T(0);
-#pragma unroll
-        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
-            int cx, cy, cz;
-            if (DIM == 3)
-                flow_dir3(j, cx, cy, cz);
-            else
-                flow_dir2(j, cx, cy, cz);
-            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
-            const T w = (T)(3.0 * flow_w<DIM>(j));
-            const T bq[3] = {b[q], b[q + n], b[q + 2 * n]};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (cx) db[0][a] += (w * (T)cx) * bq[a];
-                if (cy) db[1][a] += (w * (T)cy) * bq[a];
-                if (cz) db[2][a] += (w * (T)cz) * bq[a];
-            }
-        }
-        const T J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
-        T Be[3];
-        bext_at(c.bext_z, c.be, z, Be);
-        const T B[3] = {Be[0] + b[k], Be[1] + b[k + n], Be[2] + b[k + 2 * n]};
-        T L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
-        L[c.axis] += fb;
-        F[k] = L[0];
-        F[k + n] = L[1];
-        F[k + 2 * n] = L[2];
+        force_node<T, DIM>(b, F, n, nx, ny, nz, x, y, z, k, c, fb);
     }
 }
 
@@ -363,6 +367,69 @@ __global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T
 // F_j + F_jbar = (1 - 1/2tau) w_j (-6 u.F + 18 (c_j.u)(c_j.F)).  This uses
 // sum_i f_i^eq(x) = rho and sum_i c_i f_i^eq(x) = rho u, exact on the lattice.
 template <typename T, int DIM>
+__device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* __restrict__ u,
+                                          const T* __restrict__ F, T* __restrict__ drho_out, T* uout, long long n,
+                                          int nx, int ny, int nz, int x, int y, int z, long long k,
+                                          const FlowCoef<T>& c) {
+    const T tau = c.tau, tm1 = c.tau - T(1), half_tau = T(0.5) * c.tau;
+    const T dr0 = drho[k];
+    const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
+    const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
+    const T q0 = T(-1.5) * uu0;
+    const T w0 = (T)flow_w<DIM>(0);
+    T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
+    T m[3] = {T(0), T(0), T(0)};
+    T corr[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+        int cx, cy, cz;
+        if (DIM == 3)
+            flow_dir3(j, cx, cy, cz);
+        else
+            flow_dir2(j, cx, cy, cz);
+        const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+        const T dr = drho[q];
+        const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
+        const T Fq[3] = {F[q], F[q + n], F[q + 2 * n]};
+        const T a = (T)cx * uq[0] + (T)cy * uq[1] + (T)cz * uq[2];
+        const T uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
+        const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
+        const T uF = uq[0] * Fq[0] + uq[1] * Fq[1] + uq[2] * Fq[2];
+        const T w = (T)flow_w<DIM>(j);
+        const T sq = T(4.5) * a * a - T(1.5) * uu;
+        const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
+        const T fj = w * (dr + qp + dr * qp);
+        const T fjb = w * (dr + qm + dr * qm);
+        rho_acc += T(0.5) * fj + T(1.5) * fjb;
+        const T mom = tm1 * fj - tau * fjb;
+        const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF);
+        if (cx) {
+            m[0] += (T)cx * mom;
+            corr[0] += (T)cx * fs;
+        }
+        if (cy) {
+            m[1] += (T)cy * mom;
+            corr[1] += (T)cy * fs;
+        }
+        if (cz) {
+            m[2] += (T)cz * mom;
+            corr[2] += (T)cz * fs;
+        }
+    }
+    const T rho0 = T(1) + dr0;
+    const T rho_new = T(1) + rho_acc;
+    const T inv = T(1) / rho_new;
+    const T Fk[3] = {F[k], F[k + n], F[k + 2 * n]};
+    const T u0v[3] = {ux0, uy0, uz0};
+    drho_out[k] = rho_acc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T mm = m[a] - T(2) * tm1 * rho0 * u0v[a] - half_tau * corr[a] + Fk[a];
+        uout[k + a * n] = mm * inv;
+    }
+}
+
+template <typename T, int DIM>
 __global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __restrict__ drho,
                                                            const T* __restrict__ u, const T* __restrict__ F,
                                                            T* __restrict__ drho_out, T* uout, FlowCoef<T> c,
@@ -374,67 +441,12 @@ __global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __res
     const long long n = g.n;
     const long long P = (long long)nx * ny;
     const long long base = (long long)z * P;
-    const T tau = c.tau, tm1 = c.tau - T(1), half_tau = T(0.5) * c.tau;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const int x = p % nx, y = p / nx;
-        const long long k = base + p;
-        const T dr0 = drho[k];
-        const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
-        const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
-        const T q0 = T(-1.5) * uu0;
-        const T w0 = (T)flow_w<DIM>(0);
-        T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
-        T m[3] = {T(0), T(0), T(0)};
-        T corr[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
-            int cx, cy, cz;
-            if (DIM == 3)
-                flow_dir3(j, cx, cy, cz);
-            else
-                flow_dir2(j, cx, cy, cz);
-            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
-            const T dr = drho[q];
-            const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
-            const T Fq[3] = {F[q], F[q + n], F[q + 2 * n]};
-            const T a = (T)cx * uq[0] + (T)cy * uq[1] + (T)cz * uq[2];
-            const T uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
-            const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
-            const T uF = uq[0] * Fq[0] + uq[1] * Fq[1] + uq[2] * Fq[2];
-            const T w = (T)flow_w<DIM>(j);
-            const T sq = T(4.5) * a * a - T(1.5) * uu;
-            const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
-            const T fj = w * (dr + qp + dr * qp);
-            const T fjb = w * (dr + qm + dr * qm);
-            rho_acc += T(0.5) * fj + T(1.5) * fjb;
-            const T mom = tm1 * fj - tau * fjb;
-            const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF);
-            if (cx) {
-                m[0] += (T)cx * mom;
-                corr[0] += (T)cx * fs;
-            }
-            if (cy) {
-                m[1] += (T)cy * mom;
-                corr[1] += (T)cy * fs;
-            }
-            if (cz) {
-                m[2] += (T)cz * mom;
-                corr[2] += (T)cz * fs;
-            }
-        }
-        const T rho0 = T(1) + dr0;
-        const T rho_new = T(1) + rho_acc;
-        const T inv = T(1) / rho_new;
-        const T Fk[3] = {F[k], F[k + n], F[k + 2 * n]};
-        const T u0v[3] = {ux0, uy0, uz0};
-        drho_out[k] = rho_acc;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const T mm = m[a] - T(2) * tm1 * rho0 * u0v[a] - half_tau * corr[a] + Fk[a];
-            uout[k + a * n] = mm * inv;
-        }
+        const int y = p / nx;
+        const int x = p - y * nx;
+        flow_node<T, DIM>(drho, u, F, drho_out, uout, n, nx, ny, nz, x, y, z, base + p, c);
     }
-    ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, nx, z, sdelta);
+    ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, z, sdelta);
     if (blockIdx.x == 0 && threadIdx.x == 0) *tstep += 1;
 }
 

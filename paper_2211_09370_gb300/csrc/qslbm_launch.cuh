@@ -15,10 +15,8 @@ struct Launch {
     static IBView<T> view(const State& s, bool magnetic) {
         IBView<T> v;
         v.ring_off = s.ib.ring_off;
-        v.mk_ix = s.ib.mk_ix;
-        v.mk_iy = s.ib.mk_iy;
-        v.mk_wx = static_cast<const T*>(s.ib.mk_wx);
-        v.mk_wy = static_cast<const T*>(s.ib.mk_wy);
+        v.mk_q = s.ib.mk_q;
+        v.mk_w = static_cast<const T*>(s.ib.mk_w);
         v.mk_s = static_cast<const T*>(magnetic ? s.ib.mk_sm : s.ib.mk_s);
         v.shell_off = s.ib.shell_off;
         v.shell_xy = s.ib.shell_xy;
@@ -109,7 +107,8 @@ struct Launch {
         const T* u = (const T*)s.u[s.fcur];
         // a failed launch is recorded for cudaGetLastError, which the caller checks
         if (cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO, RT, NPT>, geo(s), bin, bout, u, c, v,
-                               (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps) != cudaSuccess)
+                               (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps, s.ib.max_ring, s.ib.max_shell,
+                               s.ib.max_nnz) != cudaSuccess)
             s.launch_error = true;
     }
 
@@ -170,8 +169,7 @@ struct Launch {
         if (e != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
             return e;
-        const size_t ring = (size_t)3 * (s.ib.max_ring > 0 ? s.ib.max_ring : 1) * sizeof(T);
-        const size_t base = (size_t)6 * P * sizeof(T) + ring;
+        const size_t base = resident_smem_bytes<T>((int)P, false, s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz);
         const size_t halo = (size_t)6 * P * sizeof(T);
         const size_t reserve = 1024;  // static shared variables and the runtime's own share
         bool ok = false;

@@ -57,10 +57,72 @@ __device__ __forceinline__ T ldcg(const T* p) {
     return __ldcg(p);
 }
 
+// Shared-memory copy of one plane's IB tables (ring markers and shell CSR).
+template <typename T>
+struct LocalIB {
+    int R, S;               // markers in the ring, shell nodes of the plane
+    const int* q;           // [9 R] in-plane support indices
+    const T* w;             // [9 R] weights
+    const T* sc;            // [R] scaling s^m_j
+    const int* shell;       // [S] in-plane index of each shell node
+    const int* off;         // [S + 1] CSR offsets (local)
+    const int* cm;          // CSR marker (local to the ring)
+    const T* cw;            // CSR weight
+};
+
+// Explicit IB corrector on a plane held in shared memory (Sec. V.D, V.F):
+// delta_j = s_j (0 - D f*) for every marker first, then f += D^T delta.
+template <typename T, int THREADS>
+__device__ __forceinline__ void ib_local(const LocalIB<T>& t, T* f0, T* f1, T* f2, T* sdelta) {
+    if (t.R == 0) return;
+    __syncthreads();
+    for (int m = threadIdx.x; m < t.R; m += THREADS) {
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const T w = t.w[9 * m + j];
+            const int q = t.q[9 * m + j];
+            a0 += w * f0[q];
+            a1 += w * f1[q];
+            a2 += w * f2[q];
+        }
+        const T sm = t.sc[m];
+        sdelta[3 * m + 0] = -sm * a0;
+        sdelta[3 * m + 1] = -sm * a1;
+        sdelta[3 * m + 2] = -sm * a2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < t.S; i += THREADS) {
+        T c0 = T(0), c1 = T(0), c2 = T(0);
+        for (int e = t.off[i]; e < t.off[i + 1]; ++e) {
+            const T w = t.cw[e];
+            const int l = t.cm[e];
+            c0 += w * sdelta[3 * l + 0];
+            c1 += w * sdelta[3 * l + 1];
+            c2 += w * sdelta[3 * l + 2];
+        }
+        const int q = t.shell[i];
+        f0[q] += c0;
+        f1[q] += c1;
+        f2[q] += c2;
+    }
+}
+
+// Bytes of shared memory the resident kernel needs (the host uses the same
+// function to plan the launch).
+template <typename T>
+__host__ __device__ inline size_t resident_smem_bytes(int P, bool uhalo, int max_ring, int max_shell, int max_nnz) {
+    size_t nT = (size_t)6 * P + (uhalo ? (size_t)6 * P : 0) + (size_t)3 * max_ring + (size_t)9 * max_ring +
+                (size_t)max_ring + (size_t)max_nnz;
+    size_t nI = (size_t)9 * max_ring + (size_t)max_shell + (size_t)max_shell + 1 + (size_t)max_nnz;
+    return nT * sizeof(T) + nI * sizeof(int);
+}
+
 template <typename T, int DIM, bool UHALO, int kResidentThreads, int kResidentMaxNpt>
 __global__ void __launch_bounds__(kResidentThreads, 1)
     k_sweeps_resident(Geo g, const T* __restrict__ b_in, T* __restrict__ b_out, const T* __restrict__ u,
-                      SweepCoef<T> c, IBView<T> ib, T* xbuf, ResidentSync* sync, int nsweeps) {
+                      SweepCoef<T> c, IBView<T> ib, T* xbuf, ResidentSync* sync, int nsweeps, int max_ring,
+                      int max_shell, int max_nnz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned int s_epoch;
     __shared__ int s_abort;
@@ -69,10 +131,18 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     const long long n = g.n;
     const int z = blockIdx.x;
     const int zm = DIM == 3 ? wrap_dec(z, nz) : z, zp = DIM == 3 ? wrap_inc(z, nz) : z;
-    T* sb = reinterpret_cast<T*>(smem_raw);  // [3][P] own b
-    T* su = sb + 3 * P;                      // [3][P] own u
-    T* suh = su + 3 * P;                     // [2][3][P] u of planes zm, zp (UHALO)
-    T* sdelta = UHALO ? suh + 6 * P : suh;   // [3 * ring]
+    // shared memory: values of type T first, then int tables
+    T* sb = reinterpret_cast<T*>(smem_raw);   // [3][P] own b
+    T* su = sb + 3 * P;                       // [3][P] own u
+    T* suh = su + 3 * P;                      // [2][3][P] u of planes zm, zp (UHALO)
+    T* sdelta = UHALO ? suh + 6 * P : suh;    // [3 R]
+    T* tw = sdelta + 3 * max_ring;            // [9 R]
+    T* tsc = tw + 9 * max_ring;               // [R]
+    T* tcw = tsc + max_ring;                  // [E]
+    int* tq = reinterpret_cast<int*>(tcw + max_nnz);  // [9 R]
+    int* tshell = tq + 9 * max_ring;          // [S]
+    int* toff = tshell + max_shell;           // [S + 1]
+    int* tcm = toff + max_shell + 1;          // [E]
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_epoch = *(volatile unsigned int*)&sync->epoch;
@@ -89,6 +159,33 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 suh[(3 + a) * P + p] = u[a * n + (long long)zp * P + p];
             }
         }
+    }
+    LocalIB<T> lib;
+    {
+        const int m0 = ib.ring_off[z];
+        lib.R = ib.ring_off[z + 1] - m0;
+        const int s0 = ib.shell_off[z];
+        lib.S = ib.shell_off[z + 1] - s0;
+        const int e0 = lib.S > 0 ? ib.csr_off[s0] : 0;
+        const int E = lib.S > 0 ? ib.csr_off[s0 + lib.S] - e0 : 0;
+        for (int i = tid; i < 9 * lib.R; i += kResidentThreads) {
+            tq[i] = ib.mk_q[9 * m0 + i];
+            tw[i] = ib.mk_w[9 * m0 + i];
+        }
+        for (int i = tid; i < lib.R; i += kResidentThreads) tsc[i] = ib.mk_s[m0 + i];
+        for (int i = tid; i < lib.S; i += kResidentThreads) tshell[i] = ib.shell_xy[s0 + i];
+        for (int i = tid; i <= lib.S; i += kResidentThreads) toff[i] = ib.csr_off[s0 + i] - e0;
+        for (int i = tid; i < E; i += kResidentThreads) {
+            tcm[i] = ib.csr_m[e0 + i];
+            tcw[i] = ib.csr_w[e0 + i];
+        }
+        lib.q = tq;
+        lib.w = tw;
+        lib.sc = tsc;
+        lib.shell = tshell;
+        lib.off = toff;
+        lib.cm = tcm;
+        lib.cw = tcw;
     }
     T be_c[3], be_m[3], be_p[3];
     bext_at(c.bext_z, c.be, z, be_c);
@@ -181,20 +278,29 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             }
         }
         __syncthreads();  // every read of the old plane is done
+        const bool publish = DIM == 3 && s + 1 < nsweeps;
+        T* xout = xbuf + (long long)(s & 1) * nz * xplane + (long long)z * xplane;
 #pragma unroll
         for (int k = 0; k < kResidentMaxNpt; ++k) {
             const int p = tid + k * kResidentThreads;
             if (p < P) {
-                sb[p] = nv[k][0];
-                sb[P + p] = nv[k][1];
-                sb[2 * P + p] = nv[k][2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    sb[a * P + p] = nv[k][a];
+                    // nodes off the wall shell are final now; shell nodes are
+                    // rewritten after the IB correction below
+                    if (publish) __stcg(xout + a * P + p, nv[k][a]);
+                }
             }
         }
-        ib_plane<T>(ib, sb, sb + P, sb + 2 * P, 0, nx, z, sdelta);
+        ib_local<T, kResidentThreads>(lib, sb, sb + P, sb + 2 * P, sdelta);
         __syncthreads();
-        if (DIM == 3 && s + 1 < nsweeps) {
-            T* xout = xbuf + (long long)(s & 1) * nz * xplane + (long long)z * xplane;
-            for (int p = tid; p < 3 * P; p += kResidentThreads) __stcg(xout + p, sb[p]);
+        if (publish) {
+            for (int i = tid; i < lib.S; i += kResidentThreads) {
+                const int q = lib.shell[i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) __stcg(xout + a * P + q, sb[a * P + q]);
+            }
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
