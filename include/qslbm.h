@@ -69,6 +69,11 @@ extern "C" {
  * at most 8192 nodes; create fails with QSLBM_EINVAL if the domain does not
  * fit).  SPLIT: per sweep a node-parallel sweep launch and a per-plane IB
  * launch.  AUTO picks RESIDENT when it fits, otherwise SPLIT. */
+/* Initial velocity: rest (plus the seeded noise), or the Ha = 0 profile
+ * U0 (1 - r^2/R^2) along the axis inside the wall (plus the noise). */
+#define QSLBM_INIT_REST 0
+#define QSLBM_INIT_POISEUILLE 1
+
 #define QSLBM_SWEEP_AUTO 0
 #define QSLBM_SWEEP_PLANES 1
 #define QSLBM_SWEEP_RESIDENT 2
@@ -100,6 +105,7 @@ typedef struct qslbm_params {
     int32_t strict_qs;      /* 1: induction flux from B^ext only; default 0        */
     uint64_t seed;          /* initial perturbation seed                           */
     double perturb;         /* initial |u| noise, fraction of U0, inside the wall  */
+    int32_t init_kind;      /* QSLBM_INIT_REST (default) | QSLBM_INIT_POISEUILLE   */
     int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT | _SPLIT */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
@@ -220,6 +226,97 @@ int qslbm_destroy(qslbm_handle* h);
 #define QSLBM_STATIC_MAX_PLANES 4096
 int qslbm_observables_static(const qslbm_handle* h, const void* drho, const void* u, const void* b,
                              const void* u_prev, double fb, int64_t steps_since_prev, double* out, void* stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent instances (3-D, one precision) advanced together: every
+ * phase of a flow step is one fused launch over all instances' work (the
+ * magnetic sweep s only over instances with N_mag > s), the step is replayed
+ * from a CUDA graph, and the node-parallel sweep's block size and persistent
+ * grid are chosen by timing candidates on the batch at creation.  Each
+ * instance follows the same arithmetic as a handle created alone with
+ * QSLBM_SWEEP_SPLIT. */
+typedef struct qslbm_batch qslbm_batch;
+
+typedef struct qslbm_batch_info_t {
+    int32_t count, max_n_mag;
+    int32_t sweep_threads, sweep_grid;  /* tuned launch; grid 0 = one block per work item */
+    int32_t launches_per_step;
+    int64_t nodes, node_sweeps_per_step, device_bytes, steps;
+    double tune_us[8];                  /* microseconds per sweep of each candidate tried  */
+} qslbm_batch_info_t;
+
+/* Create count instances from params[0..count-1] (their stream fields are
+ * ignored; work goes to `stream`, NULL = a stream the batch creates).  All
+ * must have dim = 3 and one precision (else QSLBM_EINVAL).  Errors as for
+ * qslbm_create. */
+int qslbm_batch_create(const qslbm_params* params, int32_t count, void* stream, qslbm_batch** out);
+
+/* Queue nsteps flow steps of every instance (asynchronous). */
+int qslbm_batch_step(qslbm_batch* b, int64_t nsteps);
+
+/* The handle of instance i (in creation order), after synchronising the
+ * batch's stream: use it with qslbm_observables, qslbm_get_state,
+ * qslbm_set_state and qslbm_get_units; stepping it on its own would leave the
+ * batch out of step.  The batch owns it. */
+int qslbm_batch_handle(qslbm_batch* b, int32_t i, qslbm_handle** out);
+
+/* Sizes, tuned launch and timing of the batch. */
+int qslbm_batch_info(const qslbm_batch* b, qslbm_batch_info_t* info);
+
+/* Release every instance and the batch. */
+int qslbm_batch_destroy(qslbm_batch* b);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop with continuous batching.  Requests (a problem and a stop
+ * tolerance on the steady residual) may be submitted from any thread; each
+ * qslbm_server_run admits queued requests whose device memory fits the
+ * budget, advances every running request by chunk_steps flow steps in the
+ * batched launches, and retires requests whose FP64 steady residual fell below
+ * their tolerance (status QSLBM_OK), that reached max_steps (QSLBM_ETIMEOUT),
+ * or whose fields went non-finite (QSLBM_EUNSTABLE).  A request larger than
+ * the whole budget finishes at once with QSLBM_EBUDGET.  Times are seconds on
+ * the server's monotonic clock. */
+typedef struct qslbm_server qslbm_server;
+
+typedef struct qslbm_server_config {
+    int64_t hbm_budget_bytes; /* device memory the running requests may hold  */
+    int32_t chunk_steps;      /* flow steps between residual checks            */
+    int32_t max_running;      /* 0 = limited by the budget only                */
+    int32_t precision;        /* QSLBM_FP32 | QSLBM_FP64 for every request     */
+    void* stream;             /* cudaStream_t or NULL (the server creates one) */
+} qslbm_server_config;
+
+typedef struct qslbm_result {
+    int64_t id;
+    int32_t status;           /* QSLBM_OK, QSLBM_ETIMEOUT, QSLBM_EUNSTABLE, ... */
+    int64_t steps;            /* flow steps taken                               */
+    int64_t nodes;
+    double residual;          /* last steady residual                           */
+    double t_submit, t_admit, t_done;
+    qslbm_obs obs;            /* diagnostics at retirement                      */
+} qslbm_result;
+
+typedef struct qslbm_server_stats_t {
+    int32_t running, pending, sweep_threads, sweep_grid;
+    int64_t chunks, rebuilds, steps, node_steps, device_bytes;
+} qslbm_server_stats_t;
+
+int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out);
+/* Queue a request (dim 3; precision and stream are the server's).  keep_fields
+ * keeps the finished fields on the device for qslbm_server_fields until
+ * qslbm_server_release.  Thread-safe. */
+int qslbm_server_submit(qslbm_server* s, const qslbm_params* p, double tol, int64_t max_steps, int32_t keep_fields,
+                        int64_t* id);
+/* One admission + chunk + retirement round (blocks until the chunk is done). */
+int qslbm_server_run(qslbm_server* s, int32_t* n_running, int32_t* n_pending);
+/* Move up to max finished results into out; *n = how many. */
+int qslbm_server_poll(qslbm_server* s, qslbm_result* out, int32_t max, int32_t* n);
+/* Fields of a finished request submitted with keep_fields (binary64 host
+ * arrays as in qslbm_get_state); QSLBM_ENOTFOUND otherwise. */
+int qslbm_server_fields(qslbm_server* s, int64_t id, double* rho, double* u, double* b);
+int qslbm_server_release(qslbm_server* s, int64_t id);
+int qslbm_server_stats(const qslbm_server* s, qslbm_server_stats_t* st);
+int qslbm_server_destroy(qslbm_server* s);
 
 /* Static string for a code, and the text of the last CUDA error seen by the
  * calling thread (empty if none). */

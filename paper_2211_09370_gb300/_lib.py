@@ -35,7 +35,7 @@ class qslbm_params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
-        ("sweep_kernel", C.c_int32), ("stream", C.c_void_p),
+        ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -52,10 +52,38 @@ class qslbm_obs(C.Structure):
         ("nan_flag", C.c_int32)]
 
 
+class qslbm_batch_info_t(C.Structure):
+    _fields_ = [("count", C.c_int32), ("max_n_mag", C.c_int32), ("sweep_threads", C.c_int32),
+                ("sweep_grid", C.c_int32), ("launches_per_step", C.c_int32), ("nodes", C.c_int64),
+                ("node_sweeps_per_step", C.c_int64), ("device_bytes", C.c_int64), ("steps", C.c_int64),
+                ("tune_us", C.c_double * 8)]
+
+
+class qslbm_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("chunk_steps", C.c_int32), ("max_running", C.c_int32),
+                ("precision", C.c_int32), ("stream", C.c_void_p)]
+
+
+class qslbm_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("steps", C.c_int64), ("nodes", C.c_int64),
+                ("residual", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("obs", qslbm_obs)]
+
+
+class qslbm_server_stats_t(C.Structure):
+    _fields_ = [("running", C.c_int32), ("pending", C.c_int32), ("sweep_threads", C.c_int32),
+                ("sweep_grid", C.c_int32), ("chunks", C.c_int64), ("rebuilds", C.c_int64), ("steps", C.c_int64),
+                ("node_steps", C.c_int64), ("device_bytes", C.c_int64)]
+
+
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = ("qslbm_params_init", "qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps",
            "qslbm_observables", "qslbm_get_state", "qslbm_set_state", "qslbm_step_host", "qslbm_sync",
-           "qslbm_destroy", "qslbm_strerror", "qslbm_last_error", "qslbm_observables_static")
+           "qslbm_destroy", "qslbm_strerror", "qslbm_last_error", "qslbm_observables_static",
+           "qslbm_batch_create", "qslbm_batch_step", "qslbm_batch_handle", "qslbm_batch_info",
+           "qslbm_batch_destroy", "qslbm_server_create", "qslbm_server_submit", "qslbm_server_run",
+           "qslbm_server_poll", "qslbm_server_fields", "qslbm_server_release", "qslbm_server_stats",
+           "qslbm_server_destroy")
 
 _lib = None
 
@@ -86,6 +114,28 @@ def load(path: str | None = None):
     L.qslbm_observables_static.argtypes = [hp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                            C.c_int64, C.c_void_p, C.c_void_p]
     L.qslbm_observables_static.restype = C.c_int
+    L.qslbm_batch_create.argtypes = [C.POINTER(qslbm_params), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
+    L.qslbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
+    L.qslbm_batch_handle.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]
+    L.qslbm_batch_info.argtypes = [C.c_void_p, C.POINTER(qslbm_batch_info_t)]
+    L.qslbm_batch_destroy.argtypes = [C.c_void_p]
+    for name in ("qslbm_batch_create", "qslbm_batch_step", "qslbm_batch_handle", "qslbm_batch_info",
+                 "qslbm_batch_destroy", "qslbm_server_create", "qslbm_server_submit", "qslbm_server_run",
+           "qslbm_server_poll", "qslbm_server_fields", "qslbm_server_release", "qslbm_server_stats",
+           "qslbm_server_destroy"):
+        getattr(L, name).restype = C.c_int
+    L.qslbm_server_create.argtypes = [C.POINTER(qslbm_server_config), C.POINTER(C.c_void_p)]
+    L.qslbm_server_submit.argtypes = [C.c_void_p, C.POINTER(qslbm_params), C.c_double, C.c_int64, C.c_int32,
+                                      C.POINTER(C.c_int64)]
+    L.qslbm_server_run.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.qslbm_server_poll.argtypes = [C.c_void_p, C.POINTER(qslbm_result), C.c_int32, C.POINTER(C.c_int32)]
+    L.qslbm_server_fields.argtypes = [C.c_void_p, C.c_int64, dp, dp, dp]
+    L.qslbm_server_release.argtypes = [C.c_void_p, C.c_int64]
+    L.qslbm_server_stats.argtypes = [C.c_void_p, C.POINTER(qslbm_server_stats_t)]
+    L.qslbm_server_destroy.argtypes = [C.c_void_p]
+    for name in ("qslbm_server_create", "qslbm_server_submit", "qslbm_server_run", "qslbm_server_poll",
+                 "qslbm_server_fields", "qslbm_server_release", "qslbm_server_stats", "qslbm_server_destroy"):
+        getattr(L, name).restype = C.c_int
     L.qslbm_last_error.argtypes = []
     L.qslbm_last_error.restype = C.c_char_p
     for name in ("qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps", "qslbm_observables",
@@ -143,6 +193,8 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.strict_qs = int(p.get("strict_qs", 0))
     q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
     q.perturb = float(p.get("perturb", 0.0))
+    ik = p.get("init_kind", "rest")
+    q.init_kind = {"rest": 0, "poiseuille": 1}[ik] if isinstance(ik, str) else int(ik)
     k = p.get("sweep_kernel", "auto")
     q.sweep_kernel = SWEEP_KERNEL[k] if isinstance(k, str) else int(k)
     q.stream = stream
@@ -164,12 +216,16 @@ def obs_dict(o: qslbm_obs) -> dict:
 class Solver:
     """One simulated pipe (or channel) held on the GPU by the C library."""
 
-    def __init__(self, params: dict, stream: int | None = None):
+    def __init__(self, params: dict, stream: int | None = None, _handle=None):
         self.L = load()
         self.params = dict(params)
         self._q = make_params(params, stream)
-        h = C.c_void_p()
-        check(self.L.qslbm_create(C.byref(self._q), C.byref(h)), "qslbm_create")
+        self._owned = _handle is None
+        if _handle is None:
+            h = C.c_void_p()
+            check(self.L.qslbm_create(C.byref(self._q), C.byref(h)), "qslbm_create")
+        else:
+            h = _handle
         self.h = h
         u = qslbm_units()
         check(self.L.qslbm_get_units(self.h, C.byref(u)), "qslbm_get_units")
@@ -182,7 +238,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.qslbm_destroy(self.h)
+            if self._owned:
+                self.L.qslbm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -234,3 +291,121 @@ class Solver:
     def set_state(self, rho=None, u=None, b=None, t: int = 0):
         a = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (rho, u, b)]
         check(self.L.qslbm_set_state(self.h, _dptr(a[0]), _dptr(a[1]), _dptr(a[2]), int(t)), "qslbm_set_state")
+
+
+class Batch:
+    """Independent instances advanced together by the library's batched kernels."""
+
+    def __init__(self, params_list, stream: int | None = None):
+        self.L = load()
+        self.params = [dict(p) for p in params_list]
+        arr = (qslbm_params * len(self.params))(*[make_params(p) for p in self.params])
+        h = C.c_void_p()
+        check(self.L.qslbm_batch_create(arr, len(self.params), stream, C.byref(h)), "qslbm_batch_create")
+        self.h = h
+
+    def step(self, n: int = 1):
+        check(self.L.qslbm_batch_step(self.h, int(n)), "qslbm_batch_step")
+
+    def member(self, i: int) -> Solver:
+        """A non-owning view of instance i (observables and state transfer)."""
+        hh = C.c_void_p()
+        check(self.L.qslbm_batch_handle(self.h, int(i), C.byref(hh)), "qslbm_batch_handle")
+        return Solver(self.params[i], _handle=hh)
+
+    def info(self) -> dict:
+        inf = qslbm_batch_info_t()
+        check(self.L.qslbm_batch_info(self.h, C.byref(inf)), "qslbm_batch_info")
+        d = {k: getattr(inf, k) for k, _ in qslbm_batch_info_t._fields_ if k != "tune_us"}
+        d["tune_us"] = list(inf.tune_us)
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qslbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request loop of the library (qslbm_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, chunk_steps: int = 100, max_running: int = 0,
+                 precision: str = "fp32", stream: int | None = None):
+        self.L = load()
+        cfg = qslbm_server_config(int(hbm_budget_bytes), int(chunk_steps), int(max_running),
+                                  PRECISION[precision], stream)
+        h = C.c_void_p()
+        check(self.L.qslbm_server_create(C.byref(cfg), C.byref(h)), "qslbm_server_create")
+        self.h = h
+        self.params = {}
+
+    def submit(self, params: dict, tol: float = 1e-6, max_steps: int = 100000, keep_fields: bool = False) -> int:
+        q = make_params(params)
+        rid = C.c_int64()
+        check(self.L.qslbm_server_submit(self.h, C.byref(q), float(tol), int(max_steps), int(keep_fields),
+                                         C.byref(rid)), "qslbm_server_submit")
+        self.params[rid.value] = dict(params)
+        return rid.value
+
+    def run(self):
+        nr, npd = C.c_int32(), C.c_int32()
+        check(self.L.qslbm_server_run(self.h, C.byref(nr), C.byref(npd)), "qslbm_server_run")
+        return nr.value, npd.value
+
+    def poll(self, max_results: int = 1024):
+        arr = (qslbm_result * max_results)()
+        n = C.c_int32()
+        check(self.L.qslbm_server_poll(self.h, arr, int(max_results), C.byref(n)), "qslbm_server_poll")
+        out = []
+        for r in arr[: n.value]:
+            d = {k: getattr(r, k) for k in ("id", "status", "steps", "nodes", "residual", "t_submit", "t_admit",
+                                            "t_done")}
+            d["obs"] = obs_dict(r.obs)
+            out.append(d)
+        return out
+
+    def fields(self, rid: int):
+        p = self.params[rid]
+        nz = int(p.get("nz", 1)) if int(p.get("dim", 3)) == 3 else 1
+        n = int(p["nx"]) * int(p["ny"]) * nz
+        shape = (nz, int(p["ny"]), int(p["nx"]))
+        rho, u, b = np.empty(n), np.empty(3 * n), np.empty(3 * n)
+        check(self.L.qslbm_server_fields(self.h, int(rid), _dptr(rho), _dptr(u), _dptr(b)), "qslbm_server_fields")
+        return rho.reshape(shape), u.reshape((3,) + shape), b.reshape((3,) + shape)
+
+    def release(self, rid: int):
+        check(self.L.qslbm_server_release(self.h, int(rid)), "qslbm_server_release")
+
+    def stats(self) -> dict:
+        st = qslbm_server_stats_t()
+        check(self.L.qslbm_server_stats(self.h, C.byref(st)), "qslbm_server_stats")
+        return {k: getattr(st, k) for k, _ in qslbm_server_stats_t._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qslbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

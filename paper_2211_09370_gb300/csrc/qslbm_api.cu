@@ -118,8 +118,10 @@ int validate(const qslbm_params& p) {
     if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
     if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_SPLIT) return QSLBM_EINVAL;
+    if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
+    // kernels index the three components of a field with 32-bit offsets
     long long n = (long long)p.nx * p.ny * p.nz;
-    if (n > (1LL << 31) - 1) return QSLBM_EINVAL;
+    if (3 * n > (1LL << 31) - 1) return QSLBM_EINVAL;
     return QSLBM_OK;
 }
 
@@ -596,6 +598,7 @@ int set_fields(State& s, const double* rho, const double* u, const double* b, lo
 namespace qslbm {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 const State& handle_state(const qslbm_handle* h) { return h->s; }
+State& handle_state_mut(qslbm_handle* h) { return h->s; }
 }  // namespace qslbm
 
 extern "C" {

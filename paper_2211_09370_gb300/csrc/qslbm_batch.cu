@@ -1,0 +1,828 @@
+// Batched stepping: many independent pipes of uneven size and parameters
+// advance together, every phase of a flow step being one fused launch over all
+// instances' work.  The time loop is captured into a CUDA graph (one graph per
+// step, replayed); ping-pong parities live in device memory so the same graph
+// serves every step.  Instances are ordered by N_mag (descending): sweep s only
+// touches the prefix of instances with N_mag > s.  The node-parallel sweep
+// kernel is persistent (grid-stride over the work list) with its block size
+// and grid chosen by a timing autotuner when the batch is built.
+//
+// The per-node arithmetic is the single-instance code (sweep_node, ib_plane,
+// force_node, flow_node), so a batched instance follows the same expressions as
+// one stepped alone with the split sweep kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "qslbm.h"
+#include "qslbm_internal.h"
+#include "qslbm_kernels.cuh"
+
+namespace qslbm {
+
+void set_last_error(const std::string& msg);
+State& handle_state_mut(qslbm_handle* h);
+
+template <typename T>
+struct InstDesc {
+    Geo g;
+    int n_mag;
+    int bpar, fpar;  // parity of b and of (drho, u) at the start of the current step
+    int bpp;         // node blocks per plane
+    T* b[2];
+    T* u[2];
+    T* drho[2];
+    T* F;
+    long long* tdev;
+    SweepCoef<T> sc;
+    ForceCoef<T> fc;
+    FlowCoef<T> flc;
+    IBView<T> ibm, ibu;
+};
+
+// instance owning work item w of a prefix table first[0..k]
+__device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, int w) {
+    int lo = 0, hi = k;  // first[lo] <= w < first[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (first[mid] <= w)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch_sweep(const InstDesc<T>* __restrict__ d,
+                                                         const int* __restrict__ first, int kact, int s) {
+    const int total = first[kact];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int i = find_inst(first, kact, w);
+        const InstDesc<T>& D = d[i];
+        const int local = w - first[i];
+        const int z = local / D.bpp;
+        const int p = (local - z * D.bpp) * THREADS + threadIdx.x;
+        const int nx = D.g.nx, ny = D.g.ny, nz = D.g.nz, P = nx * ny;
+        if (p >= P) continue;
+        const int par = (D.bpar + s) & 1;
+        const T* bin = D.b[par];
+        T* bout = D.b[par ^ 1];
+        const T* u = D.u[D.fpar];
+        const long long base = (long long)z * P;
+        const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
+        T be_c[3], be_m[3], be_p[3];
+        bext_at(D.sc.bext_z, D.sc.be, z, be_c);
+        bext_at(D.sc.bext_z, D.sc.be, zm, be_m);
+        bext_at(D.sc.bext_z, D.sc.be, zp, be_p);
+        T o[3];
+        sweep_node<T, 3>(bin, u, D.g.n, nx, ny, base, (long long)zm * P, (long long)zp * P, p, D.sc, be_c, be_m,
+                         be_p, o);
+        bout[base + p] = o[0];
+        bout[base + p + D.g.n] = o[1];
+        bout[base + p + 2 * D.g.n] = o[2];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_batch_ib(const InstDesc<T>* __restrict__ d,
+                                                           const int* __restrict__ pfirst, int kact, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int i = find_inst(pfirst, kact, blockIdx.x);
+    const InstDesc<T>& D = d[i];
+    const int z = blockIdx.x - pfirst[i];
+    T* f = D.b[((D.bpar + s) & 1) ^ 1];
+    const long long n = D.g.n;
+    ib_plane<T>(D.ibm, f, f + n, f + 2 * n, (long long)z * D.g.nx * D.g.ny, z, sdelta);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_batch_force(const InstDesc<T>* __restrict__ d,
+                                                              const int* __restrict__ pfirst, int k) {
+    const int i = find_inst(pfirst, k, blockIdx.x);
+    const InstDesc<T>& D = d[i];
+    const int z = blockIdx.x - pfirst[i];
+    const int nx = D.g.nx, ny = D.g.ny, P = nx * ny;
+    const T fb = body_force_at(D.fc, *D.tdev);
+    const T* b = D.b[(D.bpar + D.n_mag) & 1];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int y = p / nx;
+        const int x = p - y * nx;
+        force_node<T, 3>(b, D.F, D.g.n, nx, ny, D.g.nz, x, y, z, (long long)z * P + p, D.fc, fb);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads) k_batch_flow(InstDesc<T>* __restrict__ d, const int* __restrict__ pfirst,
+                                                              int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int i = find_inst(pfirst, k, blockIdx.x);
+    const InstDesc<T>& D = d[i];
+    const int z = blockIdx.x - pfirst[i];
+    const int nx = D.g.nx, ny = D.g.ny, nz = D.g.nz;
+    const long long n = D.g.n, P = (long long)nx * ny, base = (long long)z * P;
+    const T* dr = D.drho[D.fpar];
+    const T* u = D.u[D.fpar];
+    T* dro = D.drho[D.fpar ^ 1];
+    T* uo = D.u[D.fpar ^ 1];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int y = p / nx;
+        const int x = p - y * nx;
+        flow_node<T, 3>(dr, u, D.F, dro, uo, n, nx, ny, nz, x, y, z, base + p, D.flc);
+    }
+    ib_plane<T>(D.ibu, uo, uo + n, uo + 2 * n, base, z, sdelta);
+    if (z == 0 && threadIdx.x == 0) *D.tdev += 1;
+}
+
+template <typename T>
+__global__ void k_batch_advance(InstDesc<T>* d, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    d[i].bpar ^= d[i].n_mag & 1;
+    d[i].fpar ^= 1;
+}
+
+}  // namespace qslbm
+
+using qslbm::State;
+
+struct qslbm_batch {
+    std::vector<qslbm_handle*> members;  // in N_mag-descending order
+    std::vector<int> order;              // order[k] = caller's index of member k
+    std::vector<int> rank;               // rank[caller index] = k
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int precision = QSLBM_FP32;
+    void* desc = nullptr;                // InstDesc<T>[K]
+    int* first = nullptr;                // node-block prefix [K + 1]
+    int* pfirst = nullptr;               // plane prefix [K + 1]
+    std::vector<int> h_first, h_pfirst;
+    std::vector<int> active;             // active[s] = instances with N_mag > s
+    int max_nmag = 0;
+    int capacity = 0;                    // instances the device tables can hold
+    bool owns_members = true;
+    bool tuned = false;
+    size_t ib_smem = 0;
+    int threads = 256, grid = 0;         // autotuned sweep launch
+    cudaGraphExec_t graph = nullptr;
+    long long steps = 0;
+    long long device_bytes = 0;
+    std::vector<double> tune_us;         // timing of each candidate
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int fail(cudaError_t e, const char* what) {
+    qslbm::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return QSLBM_ECUDA;
+}
+
+#define BCHK(call)                                        \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return fail(e_, #call);    \
+    } while (0)
+
+template <typename T>
+qslbm::InstDesc<T> make_desc(const State& s) {
+    qslbm::InstDesc<T> D;
+    std::memset(&D, 0, sizeof(D));
+    D.g = qslbm::Geo{s.nx, s.ny, s.nz, s.n};
+    D.n_mag = s.units.n_mag;
+    D.bpar = s.bcur;
+    D.fpar = s.fcur;
+    D.bpp = (s.nx * s.ny + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads;
+    for (int a = 0; a < 2; ++a) {
+        D.b[a] = (T*)s.b[a];
+        D.u[a] = (T*)s.u[a];
+        D.drho[a] = (T*)s.drho[a];
+    }
+    D.F = (T*)s.F;
+    D.tdev = s.tdev;
+    D.sc.w0 = (T)s.w0;
+    D.sc.w1 = (T)s.w1;
+    D.sc.kappa = (T)s.kappa;
+    for (int a = 0; a < 3; ++a) D.sc.be[a] = (T)s.be[a];
+    D.sc.bext_z = (const T*)s.bext_z;
+    D.sc.strict_qs = s.p.strict_qs;
+    D.fc.F0 = s.units.F0;
+    D.fc.amp = s.p.force_amp;
+    D.fc.omega = s.omega;
+    D.fc.axis = s.axis;
+    for (int a = 0; a < 3; ++a) D.fc.be[a] = (T)s.be[a];
+    D.fc.bext_z = (const T*)s.bext_z;
+    D.flc.tau = (T)s.units.tau;
+    D.flc.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+    for (int m = 0; m < 2; ++m) {
+        qslbm::IBView<T>& v = m ? D.ibu : D.ibm;
+        v.ring_off = s.ib.ring_off;
+        v.mk_q = s.ib.mk_q;
+        v.mk_w = (const T*)s.ib.mk_w;
+        v.mk_s = (const T*)(m ? s.ib.mk_s : s.ib.mk_sm);
+        v.shell_off = s.ib.shell_off;
+        v.shell_xy = s.ib.shell_xy;
+        v.csr_off = s.ib.csr_off;
+        v.csr_m = s.ib.csr_m;
+        v.csr_w = (const T*)s.ib.csr_w;
+        v.nm = s.ib.nm;
+    }
+    return D;
+}
+
+template <typename T>
+void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st) {
+    const int kact = B.active[s];
+    if (kact == 0) return;
+    const int total = B.h_first[kact];
+    const int g = grid > 0 ? std::min(grid, total) : total;
+    const auto* d = (const qslbm::InstDesc<T>*)B.desc;
+    if (threads == 128)
+        qslbm::k_batch_sweep<T, 128><<<g, 128, 0, st>>>(d, B.first, kact, s);
+    else
+        qslbm::k_batch_sweep<T, 256><<<g, 256, 0, st>>>(d, B.first, kact, s);
+    qslbm::k_batch_ib<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_smem, st>>>(d, B.pfirst, kact, s);
+}
+
+template <typename T>
+void launch_step(qslbm_batch& B, cudaStream_t st) {
+    for (int s = 0; s < B.max_nmag; ++s) launch_sweep<T>(B, s, B.threads, B.grid, st);
+    const int K = (int)B.members.size();
+    auto* d = (qslbm::InstDesc<T>*)B.desc;
+    qslbm::k_batch_force<T><<<B.h_pfirst[K], qslbm::kNodeThreads, 0, st>>>(d, B.pfirst, K);
+    qslbm::k_batch_flow<T><<<B.h_pfirst[K], qslbm::kPlaneThreads, B.ib_smem, st>>>(d, B.pfirst, K);
+    qslbm::k_batch_advance<T><<<(K + 127) / 128, 128, 0, st>>>(d, K);
+}
+
+// The node-block layout depends on the sweep block size (nodes per block).
+template <typename T>
+int build_tables(qslbm_batch& B, int threads) {
+    const int K = (int)B.members.size();
+    std::vector<qslbm::InstDesc<T>> h(K);
+    B.h_first.assign(K + 1, 0);
+    B.h_pfirst.assign(K + 1, 0);
+    size_t ring = 1;
+    for (int k = 0; k < K; ++k) {
+        const State& s = qslbm::handle_state_mut(B.members[k]);
+        h[k] = make_desc<T>(s);
+        h[k].bpp = (s.nx * s.ny + threads - 1) / threads;
+        B.h_first[k + 1] = B.h_first[k] + h[k].bpp * s.nz;
+        B.h_pfirst[k + 1] = B.h_pfirst[k] + s.nz;
+        ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
+    }
+    B.ib_smem = 3 * ring * sizeof(T);
+    if (K > B.capacity) {
+        if (B.desc) cudaFree(B.desc);
+        if (B.first) cudaFree(B.first);
+        if (B.pfirst) cudaFree(B.pfirst);
+        B.desc = nullptr;
+        B.first = B.pfirst = nullptr;
+        const int cap = std::max(K, 2 * B.capacity);
+        BCHK(cudaMalloc(&B.desc, sizeof(qslbm::InstDesc<T>) * cap));
+        BCHK(cudaMalloc((void**)&B.first, sizeof(int) * (cap + 1)));
+        BCHK(cudaMalloc((void**)&B.pfirst, sizeof(int) * (cap + 1)));
+        B.device_bytes = (long long)(sizeof(qslbm::InstDesc<T>) * cap + 2 * sizeof(int) * (cap + 1));
+        B.capacity = cap;
+    }
+    BCHK(cudaMemcpyAsync(B.desc, h.data(), sizeof(qslbm::InstDesc<T>) * K, cudaMemcpyHostToDevice, B.stream));
+    BCHK(cudaMemcpyAsync(B.first, B.h_first.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
+    BCHK(cudaMemcpyAsync(B.pfirst, B.h_pfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
+    BCHK(cudaStreamSynchronize(B.stream));
+    return QSLBM_OK;
+}
+
+// Autotuner: time the first sweep of the batch for each (block size, grid)
+// candidate on the real instances and keep the fastest.  The sweeps run on a
+// copy of the state that is restored afterwards, so tuning does not advance
+// the solution.
+template <typename T>
+int autotune(qslbm_batch& B) {
+    int dev = 0, sms = 0;
+    BCHK(cudaGetDevice(&dev));
+    BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    struct Cand {
+        int threads, grid;
+    };
+    std::vector<Cand> cands;
+    for (int th : {128, 256})
+        for (int per_sm : {4, 8, 16, 0}) cands.push_back({th, per_sm ? per_sm * sms : 0});
+    // the tuning sweeps write b[other parity]; they read b[current] and u only,
+    // so the state the batch starts from is untouched
+    cudaEvent_t e0, e1;
+    BCHK(cudaEventCreate(&e0));
+    BCHK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    B.tune_us.clear();
+    for (const Cand& c : cands) {
+        int rc = build_tables<T>(B, c.threads);
+        if (rc) return rc;
+        launch_sweep<T>(B, 0, c.threads, c.grid, B.stream);  // warm-up
+        BCHK(cudaEventRecord(e0, B.stream));
+        for (int r = 0; r < 3; ++r) launch_sweep<T>(B, 0, c.threads, c.grid, B.stream);
+        BCHK(cudaEventRecord(e1, B.stream));
+        BCHK(cudaEventSynchronize(e1));
+        float ms = 0;
+        BCHK(cudaEventElapsedTime(&ms, e0, e1));
+        B.tune_us.push_back(ms * 1e3 / 3);
+        if (ms < best) {
+            best = ms;
+            B.threads = c.threads;
+            B.grid = c.grid;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return build_tables<T>(B, B.threads);
+}
+
+template <typename T>
+int capture(qslbm_batch& B) {
+    if (B.graph) {
+        cudaGraphExecDestroy(B.graph);
+        B.graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    BCHK(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
+    launch_step<T>(B, B.stream);
+    cudaError_t e = cudaStreamEndCapture(B.stream, &g);
+    if (e != cudaSuccess) return fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&B.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+    return QSLBM_OK;
+}
+
+// Mirror the device-side parity updates on the members' host state.
+void advance_host(qslbm_batch& B, long long nsteps) {
+    for (qslbm_handle* h : B.members) {
+        State& s = qslbm::handle_state_mut(h);
+        s.fcur ^= (int)(nsteps & 1);
+        s.bcur ^= (int)((nsteps * s.units.n_mag) & 1);
+        s.t += nsteps;
+    }
+    B.steps += nsteps;
+}
+
+void destroy_batch(qslbm_batch* B) {
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->desc) cudaFree(B->desc);
+    if (B->first) cudaFree(B->first);
+    if (B->pfirst) cudaFree(B->pfirst);
+    if (B->owns_members)
+        for (qslbm_handle* h : B->members) qslbm_destroy(h);
+    if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+// (Re)build the batch over the given handles: order by N_mag, device tables,
+// autotune (first time only) and the per-step graph.  The handles' host parity
+// must match their device buffers (true for handles created by this library).
+int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs) {
+    const int count = (int)hs.size();
+    B->members.clear();
+    B->order.assign(count, 0);
+    B->rank.assign(count, 0);
+    if (count == 0) {
+        if (B->graph) {
+            cudaGraphExecDestroy(B->graph);
+            B->graph = nullptr;
+        }
+        B->max_nmag = 0;
+        B->active.clear();
+        return QSLBM_OK;
+    }
+    std::vector<int> idx(count);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return qslbm::handle_state_mut(hs[a]).units.n_mag > qslbm::handle_state_mut(hs[b]).units.n_mag;
+    });
+    B->order = idx;
+    for (int k = 0; k < count; ++k) {
+        B->members.push_back(hs[idx[k]]);
+        B->rank[idx[k]] = k;
+    }
+    B->max_nmag = qslbm::handle_state_mut(B->members[0]).units.n_mag;
+    B->active.assign(B->max_nmag, 0);
+    for (int s = 0; s < B->max_nmag; ++s) {
+        int a = 0;
+        while (a < count && qslbm::handle_state_mut(B->members[a]).units.n_mag > s) ++a;
+        B->active[s] = a;
+    }
+    int rc;
+    if (!B->tuned) {
+        rc = B->precision == QSLBM_FP64 ? autotune<double>(*B) : autotune<float>(*B);
+        B->tuned = true;
+    } else {
+        rc = B->precision == QSLBM_FP64 ? build_tables<double>(*B, B->threads) : build_tables<float>(*B, B->threads);
+    }
+    if (!rc) rc = B->precision == QSLBM_FP64 ? capture<double>(*B) : capture<float>(*B);
+    return rc;
+}
+
+int create_batch(const qslbm_params* params, int32_t count, void* stream, qslbm_batch** out) {
+    if (!params || !out || count <= 0) return QSLBM_EINVAL;
+    *out = nullptr;
+    const int prec = params[0].precision;
+    for (int i = 0; i < count; ++i)
+        if (params[i].precision != prec || params[i].dim != 3) return QSLBM_EINVAL;
+    qslbm_batch* B = new (std::nothrow) qslbm_batch();
+    if (!B) return QSLBM_ENOMEM;
+    B->precision = prec;
+    if (stream) {
+        B->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&B->stream);
+        if (e != cudaSuccess) {
+            delete B;
+            return fail(e, "cudaStreamCreate");
+        }
+        B->own_stream = true;
+    }
+    std::vector<qslbm_handle*> hs(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        qslbm_params p = params[i];
+        p.sweep_kernel = QSLBM_SWEEP_SPLIT;
+        p.stream = B->stream;
+        int rc = qslbm_create(&p, &hs[i]);
+        if (rc) {
+            for (qslbm_handle* h : hs)
+                if (h) qslbm_destroy(h);
+            if (B->own_stream) cudaStreamDestroy(B->stream);
+            delete B;
+            return rc;
+        }
+    }
+    int rc = set_members(B, hs);
+    if (rc) {
+        destroy_batch(B);
+        return rc;
+    }
+    *out = B;
+    return QSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qslbm_batch_create(const qslbm_params* params, int32_t count, void* stream, qslbm_batch** out) {
+    try {
+        return create_batch(params, count, stream, out);
+    } catch (...) {
+        return QSLBM_ENOMEM;
+    }
+}
+
+int qslbm_batch_step(qslbm_batch* B, int64_t nsteps) {
+    if (!B || nsteps < 0) return QSLBM_EINVAL;
+    if (B->members.empty()) return QSLBM_OK;
+    for (long long i = 0; i < nsteps; ++i) BCHK(cudaGraphLaunch(B->graph, B->stream));
+    advance_host(*B, nsteps);
+    return QSLBM_OK;
+}
+
+int qslbm_batch_handle(qslbm_batch* B, int32_t i, qslbm_handle** out) {
+    if (!B || !out || i < 0 || i >= (int)B->members.size()) return QSLBM_EINVAL;
+    BCHK(cudaStreamSynchronize(B->stream));
+    *out = B->members[B->rank[i]];
+    return QSLBM_OK;
+}
+
+int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
+    if (!B || !info) return QSLBM_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->count = (int32_t)B->members.size();
+    info->max_n_mag = B->max_nmag;
+    info->sweep_threads = B->threads;
+    info->sweep_grid = B->grid;
+    long long nodes = 0, bytes = B->device_bytes, sweeps = 0;
+    for (qslbm_handle* h : B->members) {
+        const State& s = qslbm::handle_state_mut(h);
+        nodes += s.n;
+        bytes += s.device_bytes;
+        sweeps += s.n * (long long)s.units.n_mag;
+    }
+    info->nodes = nodes;
+    info->node_sweeps_per_step = sweeps;
+    info->device_bytes = bytes;
+    info->launches_per_step = 2 * B->max_nmag + 3;
+    info->steps = B->steps;
+    for (size_t c = 0; c < B->tune_us.size() && c < 8; ++c) info->tune_us[c] = B->tune_us[c];
+    return QSLBM_OK;
+}
+
+int qslbm_batch_destroy(qslbm_batch* B) {
+    if (!B) return QSLBM_EINVAL;
+    destroy_batch(B);
+    return QSLBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: a request loop over the batched engine.  Requests (a problem and a
+// stop tolerance) are queued from any thread; each call of qslbm_server_run
+// admits the queued requests whose device memory fits the budget (first fit),
+// rebuilds the batch when its membership changed, advances every admitted
+// instance by one chunk of steps in the fused launches, then checks each
+// instance's FP64 steady residual and retires those that converged (or hit
+// their step cap, or went non-finite).  New requests join between chunks while
+// others keep running: continuous batching.
+#include <chrono>
+#include <deque>
+#include <mutex>
+
+namespace {
+
+struct Request {
+    int64_t id;
+    qslbm_params p;
+    double tol;
+    int64_t max_steps;
+    int32_t keep;
+    double t_submit;
+};
+
+struct Running {
+    Request r;
+    qslbm_handle* h;
+    double t_admit;
+    int64_t steps;
+    long long bytes;
+    double residual;
+};
+
+}  // namespace
+
+struct qslbm_server {
+    std::mutex mu;  // guards pending and next_id (submit may come from other threads)
+    std::deque<Request> pending;
+    int64_t next_id = 1;
+    std::vector<Running> running;
+    std::vector<qslbm_result> done;
+    std::vector<std::pair<int64_t, qslbm_handle*>> kept;
+    qslbm_batch* batch = nullptr;
+    qslbm_server_config cfg{};
+    long long used = 0;
+    std::chrono::steady_clock::time_point t0;
+    long long chunks = 0, rebuilds = 0, steps = 0, node_steps = 0;
+};
+
+namespace {
+
+double now_s(const qslbm_server& S) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+}
+
+// Device bytes a request will hold (fields, double buffers, scratch, tables).
+long long estimate_bytes(const qslbm_params& p) {
+    const long long n = (long long)p.nx * p.ny * (p.dim == 2 ? 1 : p.nz);
+    const long long esz = p.precision == QSLBM_FP64 ? 8 : 4;
+    return n * esz * 20 + n * 8 / 16 + (1 << 20);
+}
+
+void finish(qslbm_server& S, Running& r, int32_t status) {
+    qslbm_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.id = r.r.id;
+    res.status = status;
+    res.steps = r.steps;
+    res.residual = r.residual;
+    res.t_submit = r.r.t_submit;
+    res.t_admit = r.t_admit;
+    res.t_done = now_s(S);
+    res.nodes = qslbm::handle_state_mut(r.h).n;
+    qslbm_observables(r.h, &res.obs, nullptr, nullptr, nullptr);
+    S.done.push_back(res);
+    if (r.r.keep) {
+        S.kept.push_back({r.r.id, r.h});
+    } else {
+        S.used -= r.bytes;
+        qslbm_destroy(r.h);
+    }
+    r.h = nullptr;
+}
+
+int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
+    bool changed = false;
+    // admission (first fit under the budget)
+    {
+        std::lock_guard<std::mutex> lock(S.mu);
+        for (auto it = S.pending.begin(); it != S.pending.end();) {
+            if (S.cfg.max_running > 0 && (int)S.running.size() >= S.cfg.max_running) break;
+            const long long est = estimate_bytes(it->p);
+            if (est > S.cfg.hbm_budget_bytes) {
+                qslbm_result res;
+                std::memset(&res, 0, sizeof(res));
+                res.id = it->id;
+                res.status = QSLBM_EBUDGET;
+                res.t_submit = it->t_submit;
+                res.t_admit = res.t_done = now_s(S);
+                S.done.push_back(res);
+                it = S.pending.erase(it);
+                continue;
+            }
+            if (S.used + est > S.cfg.hbm_budget_bytes) {
+                ++it;
+                continue;
+            }
+            qslbm_params p = it->p;
+            p.precision = S.cfg.precision;
+            p.sweep_kernel = QSLBM_SWEEP_SPLIT;
+            p.stream = S.batch->stream;
+            qslbm_handle* h = nullptr;
+            int rc = qslbm_create(&p, &h);
+            if (rc) {
+                qslbm_result res;
+                std::memset(&res, 0, sizeof(res));
+                res.id = it->id;
+                res.status = rc;
+                res.t_submit = it->t_submit;
+                res.t_admit = res.t_done = now_s(S);
+                S.done.push_back(res);
+                it = S.pending.erase(it);
+                continue;
+            }
+            const long long bytes = qslbm::handle_state_mut(h).device_bytes;
+            S.used += bytes;
+            qslbm_obs o;
+            qslbm_observables(h, &o, nullptr, nullptr, nullptr);  // reference velocity for the residual
+            S.running.push_back({*it, h, now_s(S), 0, bytes, 0.0});
+            it = S.pending.erase(it);
+            changed = true;
+        }
+    }
+    if (changed) {
+        std::vector<qslbm_handle*> hs;
+        for (const Running& r : S.running) hs.push_back(r.h);
+        int rc = set_members(S.batch, hs);
+        if (rc) return rc;
+        ++S.rebuilds;
+    }
+    if (!S.running.empty()) {
+        int rc = qslbm_batch_step(S.batch, S.cfg.chunk_steps);
+        if (rc) return rc;
+        ++S.chunks;
+        S.steps += S.cfg.chunk_steps;
+        bool retired = false;
+        for (Running& r : S.running) {
+            r.steps += S.cfg.chunk_steps;
+            S.node_steps += qslbm::handle_state_mut(r.h).n * (long long)S.cfg.chunk_steps;
+            qslbm_obs o;
+            rc = qslbm_observables(r.h, &o, nullptr, nullptr, nullptr);
+            r.residual = o.steady_residual;
+            if (rc == QSLBM_EUNSTABLE || o.nan_flag) {
+                finish(S, r, QSLBM_EUNSTABLE);
+                retired = true;
+            } else if (rc) {
+                return rc;
+            } else if (o.steady_residual < r.r.tol) {
+                finish(S, r, QSLBM_OK);
+                retired = true;
+            } else if (r.steps >= r.r.max_steps) {
+                finish(S, r, QSLBM_ETIMEOUT);
+                retired = true;
+            }
+        }
+        if (retired) {
+            std::vector<Running> keep;
+            for (Running& r : S.running)
+                if (r.h) keep.push_back(r);
+            S.running.swap(keep);
+            std::vector<qslbm_handle*> hs;
+            for (const Running& r : S.running) hs.push_back(r.h);
+            rc = set_members(S.batch, hs);
+            if (rc) return rc;
+            ++S.rebuilds;
+        }
+    }
+    if (n_running) *n_running = (int32_t)S.running.size();
+    if (n_pending) {
+        std::lock_guard<std::mutex> lock(S.mu);
+        *n_pending = (int32_t)S.pending.size();
+    }
+    return QSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out) {
+    if (!cfg || !out || cfg->chunk_steps <= 0 || cfg->hbm_budget_bytes <= 0) return QSLBM_EINVAL;
+    if (cfg->precision != QSLBM_FP32 && cfg->precision != QSLBM_FP64) return QSLBM_EINVAL;
+    *out = nullptr;
+    qslbm_server* S = new (std::nothrow) qslbm_server();
+    if (!S) return QSLBM_ENOMEM;
+    S->cfg = *cfg;
+    S->t0 = std::chrono::steady_clock::now();
+    qslbm_batch* B = new (std::nothrow) qslbm_batch();
+    if (!B) {
+        delete S;
+        return QSLBM_ENOMEM;
+    }
+    B->owns_members = false;
+    B->precision = cfg->precision;
+    if (cfg->stream) {
+        B->stream = (cudaStream_t)cfg->stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&B->stream);
+        if (e != cudaSuccess) {
+            delete B;
+            delete S;
+            return fail(e, "cudaStreamCreate");
+        }
+        B->own_stream = true;
+    }
+    S->batch = B;
+    *out = S;
+    return QSLBM_OK;
+}
+
+int qslbm_server_submit(qslbm_server* S, const qslbm_params* p, double tol, int64_t max_steps, int32_t keep_fields,
+                        int64_t* id) {
+    if (!S || !p || !(tol > 0) || max_steps <= 0) return QSLBM_EINVAL;
+    if (p->dim != 3) return QSLBM_EINVAL;
+    std::lock_guard<std::mutex> lock(S->mu);
+    Request r{S->next_id++, *p, tol, max_steps, keep_fields, now_s(*S)};
+    S->pending.push_back(r);
+    if (id) *id = r.id;
+    return QSLBM_OK;
+}
+
+int qslbm_server_run(qslbm_server* S, int32_t* n_running, int32_t* n_pending) {
+    if (!S) return QSLBM_EINVAL;
+    try {
+        return server_run(*S, n_running, n_pending);
+    } catch (...) {
+        return QSLBM_ENOMEM;
+    }
+}
+
+int qslbm_server_poll(qslbm_server* S, qslbm_result* out, int32_t max, int32_t* n) {
+    if (!S || !n || max < 0 || (max > 0 && !out)) return QSLBM_EINVAL;
+    const int k = std::min<int>(max, (int)S->done.size());
+    for (int i = 0; i < k; ++i) out[i] = S->done[i];
+    S->done.erase(S->done.begin(), S->done.begin() + k);
+    *n = k;
+    return QSLBM_OK;
+}
+
+int qslbm_server_fields(qslbm_server* S, int64_t id, double* rho, double* u, double* b) {
+    if (!S) return QSLBM_EINVAL;
+    for (auto& kv : S->kept)
+        if (kv.first == id) return qslbm_get_state(kv.second, rho, u, b, nullptr);
+    return QSLBM_ENOTFOUND;
+}
+
+int qslbm_server_release(qslbm_server* S, int64_t id) {
+    if (!S) return QSLBM_EINVAL;
+    for (size_t i = 0; i < S->kept.size(); ++i)
+        if (S->kept[i].first == id) {
+            S->used -= qslbm::handle_state_mut(S->kept[i].second).device_bytes;
+            qslbm_destroy(S->kept[i].second);
+            S->kept.erase(S->kept.begin() + i);
+            return QSLBM_OK;
+        }
+    return QSLBM_ENOTFOUND;
+}
+
+int qslbm_server_stats(const qslbm_server* S, qslbm_server_stats_t* st) {
+    if (!S || !st) return QSLBM_EINVAL;
+    std::memset(st, 0, sizeof(*st));
+    st->running = (int32_t)S->running.size();
+    st->pending = (int32_t)S->pending.size();
+    st->chunks = S->chunks;
+    st->rebuilds = S->rebuilds;
+    st->steps = S->steps;
+    st->node_steps = S->node_steps;
+    st->device_bytes = S->used;
+    st->sweep_threads = S->batch->threads;
+    st->sweep_grid = S->batch->grid;
+    return QSLBM_OK;
+}
+
+int qslbm_server_destroy(qslbm_server* S) {
+    if (!S) return QSLBM_EINVAL;
+    if (S->batch->stream) cudaStreamSynchronize(S->batch->stream);
+    for (Running& r : S->running)
+        if (r.h) qslbm_destroy(r.h);
+    for (auto& kv : S->kept) qslbm_destroy(kv.second);
+    S->batch->members.clear();
+    destroy_batch(S->batch);
+    delete S;
+    return QSLBM_OK;
+}
+
+}  // extern "C"

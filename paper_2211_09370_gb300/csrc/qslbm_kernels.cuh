@@ -152,32 +152,40 @@ __device__ __forceinline__ void flux_pair(const T u[3], const T B[3], int beta, 
 
 // One node of the sweep: in-plane index p of the plane at base, z neighbours
 // at zmbase / zpbase.  Neighbours enter in the order -x, +x, -y, +y, -z, +z.
+// Indices are 32-bit (the library keeps 3 n below 2^31) so that every load is
+// one pointer + offset.
 template <typename T, int DIM>
-__device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* __restrict__ u, long long n, int nx,
-                                           int ny, long long base, long long zmbase, long long zpbase, int p,
+__device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* __restrict__ u, long long n_, int nx,
+                                           int ny, long long base_, long long zmbase_, long long zpbase_, int p,
                                            const SweepCoef<T>& c, const T be_c[3], const T be_m[3],
                                            const T be_p[3], T out[3]) {
+    const int n = (int)n_, base = (int)base_;
     const int y = p / nx;
     const int x = p - y * nx;
-    const long long k = base + p;
-    long long nb[6];  // -x, +x, -y, +y, -z, +z
-    nb[0] = base + (long long)y * nx + wrap_dec(x, nx);
-    nb[1] = base + (long long)y * nx + wrap_inc(x, nx);
-    nb[2] = base + (long long)wrap_dec(y, ny) * nx + x;
-    nb[3] = base + (long long)wrap_inc(y, ny) * nx + x;
-    nb[4] = zmbase + p;
-    nb[5] = zpbase + p;
-    T acc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) acc[a] = c.w0 * bin[k + a * n];
+    const int k = base + p;
+    int nb[6];  // -x, +x, -y, +y, -z, +z
+    const int row = base + y * nx;
+    nb[0] = row + wrap_dec(x, nx);
+    nb[1] = row + wrap_inc(x, nx);
+    nb[2] = base + wrap_dec(y, ny) * nx + x;
+    nb[3] = base + wrap_inc(y, ny) * nx + x;
+    nb[4] = (int)zmbase_ + p;
+    nb[5] = (int)zpbase_ + p;
+    const T* b0 = bin;
+    const T* b1 = bin + n;
+    const T* b2 = bin + 2 * n;
+    const T* u0 = u;
+    const T* u1 = u + n;
+    const T* u2 = u + 2 * n;
+    T acc[3] = {c.w0 * b0[k], c.w0 * b1[k], c.w0 * b2[k]};
     T diff[3] = {T(0), T(0), T(0)};  // sum_beta Phi_ab(x - e_beta) - Phi_ab(x + e_beta)
 #pragma unroll
     for (int d = 0; d < 2 * DIM; ++d) {
-        const long long q = nb[d];
-        const T bq[3] = {bin[q], bin[q + n], bin[q + 2 * n]};
+        const int q = nb[d];
+        const T bq[3] = {b0[q], b1[q], b2[q]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
-        const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
+        const T uq[3] = {u0[q], u1[q], u2[q]};
         const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
         T B[3];
 #pragma unroll
@@ -301,6 +309,8 @@ template <typename T, int DIM>
 __device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restrict__ F, long long n, int nx, int ny,
                                            int nz, int x, int y, int z, long long k, const ForceCoef<T>& c,
                                            T fb) {
+    const T* b1 = b + n;
+    const T* b2 = b + 2 * n;
     T db[3][3];  // db[beta][alpha] = d_beta b_alpha
 #pragma unroll
     for (int be = 0; be < 3; ++be)
@@ -313,9 +323,9 @@ __device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restric
             flow_dir3(j, cx, cy, cz);
         else
             flow_dir2(j, cx, cy, cz);
-        const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+        const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
         const T w = (T)(3.0 * flow_w<DIM>(j));
-        const T bq[3] = {b[q], b[q + n], b[q + 2 * n]};
+        const T bq[3] = {b[q], b1[q], b2[q]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (cx) db[0][a] += (w * (T)cx) * bq[a];
@@ -371,6 +381,10 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
                                           const T* __restrict__ F, T* __restrict__ drho_out, T* uout, long long n,
                                           int nx, int ny, int nz, int x, int y, int z, long long k,
                                           const FlowCoef<T>& c) {
+    const T* u1 = u + n;
+    const T* u2 = u + 2 * n;
+    const T* F1 = F + n;
+    const T* F2 = F + 2 * n;
     const T tau = c.tau, tm1 = c.tau - T(1), half_tau = T(0.5) * c.tau;
     const T dr0 = drho[k];
     const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
@@ -387,10 +401,10 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
             flow_dir3(j, cx, cy, cz);
         else
             flow_dir2(j, cx, cy, cz);
-        const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+        const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
         const T dr = drho[q];
-        const T uq[3] = {u[q], u[q + n], u[q + 2 * n]};
-        const T Fq[3] = {F[q], F[q + n], F[q + 2 * n]};
+        const T uq[3] = {u[q], u1[q], u2[q]};
+        const T Fq[3] = {F[q], F1[q], F2[q]};
         const T a = (T)cx * uq[0] + (T)cy * uq[1] + (T)cz * uq[2];
         const T uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
         const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
@@ -463,7 +477,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
 
 template <typename T>
 __global__ void k_init(Geo g, T* drho, T* u, T* b, unsigned long long seed, double amp, int ncomp,
-                       int geometry, double cx, double cy, double R) {
+                       int geometry, double cx, double cy, double R, int poiseuille, double U0, int axis) {
     const long long n = g.n;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
@@ -483,6 +497,11 @@ __global__ void k_init(Geo g, T* drho, T* u, T* b, unsigned long long seed, doub
             if (amp != 0.0 && inside && a < ncomp) {
                 const unsigned long long r = splitmix64(seed ^ (unsigned long long)(3 * k + a));
                 v = amp * ((double)(r >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+            }
+            if (poiseuille && inside && a == axis && geometry != 2) {
+                const double d2 = geometry == 0 ? ((double)y - cy) * ((double)y - cy)
+                                                : ((double)x - cx) * ((double)x - cx) + ((double)y - cy) * ((double)y - cy);
+                v += U0 * (1.0 - d2 / (R * R));
             }
             u[k + a * n] = (T)v;
         }

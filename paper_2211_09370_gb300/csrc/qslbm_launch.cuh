@@ -40,7 +40,8 @@ struct Launch {
         int ncomp = s.dim == 3 ? 3 : 2;
         k_init<T><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), (T*)s.drho[0], (T*)s.u[0], (T*)s.b[0], s.p.seed,
                                                        s.p.perturb * s.units.U0, ncomp, s.p.geometry, s.cx,
-                                                       s.cy, s.R);
+                                                       s.cy, s.R, s.p.init_kind == QSLBM_INIT_POISEUILLE,
+                                                       s.units.U0, s.axis);
     }
 
     static void sweeps(State& s, int nsweeps, cudaStream_t st) {

@@ -1,0 +1,72 @@
+"""Batched stepping (many pipes in fused launches) against single-instance runs
+and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_09370_gb300 import workloads as W
+from paper_2211_09370_gb300._lib import Batch, Solver
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def uneven(precision, n=5):
+    # different sizes, fields, N_mag (270 down to 9) and forcing
+    ps = [
+        W.small_pipe(nx=26, ny=24, nz=9, diameter=18.0, precision=precision, seed=1),
+        W.small_pipe(nx=17, ny=19, nz=13, diameter=12.0, Re=30.0, Ha=8.0, Rm=0.05, precision=precision, seed=2),
+        W.small_pipe(nx=30, ny=30, nz=6, diameter=22.0, Re=300.0, Ha=40.0, Rm=1e-2, b0_kind="tanh",
+                     ramp_center=3.0, ramp_width=1.5, precision=precision, seed=3),
+        W.small_pipe(nx=21, ny=23, nz=11, diameter=15.0, Re=50.0, Ha=0.0, Rm=0.2, force_amp=0.2,
+                     force_period=7.0, precision=precision, seed=4),
+        W.small_pipe(nx=20, ny=20, nz=7, diameter=14.0, Rm=1.0, n_mag=9, precision=precision, seed=5),
+    ]
+    return ps[:n]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_members_match_single_instances(precision):
+    ps = uneven(precision)
+    steps = 6
+    with Batch(ps) as B:
+        info = B.info()
+        assert info["count"] == len(ps) and info["max_n_mag"] == 270
+        assert info["sweep_threads"] in (128, 256)
+        B.step(steps)
+        got = [B.member(i).state() for i in range(len(ps))]
+    for i, p in enumerate(ps):
+        with Solver(dict(p, sweep_kernel="split")) as s:
+            s.step(steps)
+            want = s.state()
+        for a, b in zip(got[i], want):
+            assert rel(a, b) <= (1e-13 if precision == "fp64" else 1e-6), i
+
+
+def test_batch_member_matches_oracle_fp64():
+    ps = uneven("fp64", 3)
+    with Batch(ps) as B:
+        B.step(4)
+        m = B.member(1)
+        _, u, b = m.state()
+        obs = m.observables()
+    o = oracle.Oracle(ps[1])
+    o.step(4)
+    _, ou, ob = o.state()
+    assert rel(u, ou) <= 1e-12 and rel(b, ob) <= 1e-12
+    assert obs["step"] == 4
+
+
+def test_batch_steps_in_chunks_equal_one_call():
+    ps = uneven("fp32", 4)
+    with Batch(ps) as A, Batch(ps) as B:
+        A.step(5)
+        for _ in range(5):
+            B.step(1)
+        for i in range(len(ps)):
+            for a, b in zip(A.member(i).state(), B.member(i).state()):
+                np.testing.assert_array_equal(a, b)
