@@ -110,6 +110,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself without torch.distributed)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, nodes_per_rank: int, steps: int, slowest_ms: float) -> float:
+    """Whole-job MLUPS of independent replicas: every rank's node updates over
+    the slowest rank's time."""
+    return world * nodes_per_rank * steps / (slowest_ms / 1e3) / 1e6
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2211_09370_gb300", "csrc", "qslbm_kernels.cuh"), "rb") as f:
@@ -176,6 +192,120 @@ def cpu_baseline_sample():
             "sample": f"1 flow step (N_mag=270) of the full 64x64x128 pipe in {dt:.1f}s"}
 
 
+def run_batched(steps: int = 3, count: int = 64):
+    """The batched workload: `count` independent pipes of uneven size and
+    parameters (seed 4) advanced together; node updates per second over the
+    whole batch, timed with CUDA events on the batch's stream."""
+    import torch
+
+    from paper_2211_09370_gb300 import _lib
+
+    ps = W.batched_pipes(n=count)
+    stream = torch.cuda.Stream()
+    t_build = time.perf_counter()
+    B = _lib.Batch(ps, stream=stream.cuda_stream)
+    build_s = time.perf_counter() - t_build
+    info = B.info()
+    B.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    B.close()
+    return {"instances": count, "nodes": info["nodes"], "max_n_mag": info["max_n_mag"],
+            "node_sweeps_per_step": info["node_sweeps_per_step"], "ms_per_step": ms,
+            "MLUPS": info["nodes"] / ms / 1e3, "sweep_GLUPS": info["node_sweeps_per_step"] / ms / 1e6,
+            "tuned_sweep": {"threads": info["sweep_threads"], "grid": info["sweep_grid"],
+                            "candidates_us": [round(x, 1) for x in info["tune_us"]]},
+            "launches_per_step": info["launches_per_step"], "build_s": build_s, "steps": steps}
+
+
+def run_serving(count: int = 16, rate: float = 20.0, tol: float = 1e-6, max_steps: int = 3000, chunk: int = 100,
+                diameters=(16, 24, 32), time_cap_s: float = 120.0, baseline: int = 3):
+    """Serving: Poisson arrivals of steady-state pipe solves (seed 5; the
+    diameters restricted so that the run stays bounded), admitted under a
+    device-memory budget and advanced by continuous batching in FP32.  Reports
+    solves/s and p50/p99 latency (submit to result), and solves/s of the same
+    first `baseline` requests solved one at a time in FP64 with the same stop
+    rule, with the largest rel-L2 between the two answers."""
+    import threading as th
+
+    import numpy as np
+
+    from paper_2211_09370_gb300 import _lib
+
+    reqs = []
+    for r in W.serving_requests(n=4 * count, seed=5, rate=rate):
+        D = int(r["params"]["diameter"])
+        if D in diameters:
+            p = dict(r["params"], init_kind="poiseuille", nz=6 * D)
+            reqs.append((r["arrival_s"], p))
+        if len(reqs) == count:
+            break
+    t_first = reqs[0][0]
+    S = _lib.Server(hbm_budget_bytes=8 << 30, chunk_steps=chunk, precision="fp32")
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for k, (ta, p) in enumerate(reqs):
+            delay = (ta - t_first) - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = S.submit(p, tol=tol, max_steps=max_steps, keep_fields=k < baseline)
+
+    feed = th.Thread(target=feeder, daemon=True)
+    feed.start()
+    results = {}
+    while (len(results) < len(reqs) or feed.is_alive()) and time.perf_counter() - t0 < time_cap_s:
+        nr, npd = S.run()
+        for r in S.poll():
+            results[r["id"]] = r
+        if nr == 0 and npd == 0 and feed.is_alive():
+            time.sleep(0.002)
+    elapsed = time.perf_counter() - t0
+    feed.join(timeout=1)
+    lat = sorted(r["t_done"] - r["t_submit"] for r in results.values())
+    ok = [r for r in results.values() if r["status"] == 0]
+    stats = S.stats()
+    served_fields = {k: S.fields(ids[k]) for k in range(min(baseline, len(reqs))) if ids[k] in results}
+    S.close()
+    # one request at a time in FP64 (single-instance handles, same stop rule)
+    t1 = time.perf_counter()
+    worst = 0.0
+    done64 = 0
+    for k in range(min(baseline, len(reqs))):
+        p = dict(reqs[k][1], precision="fp64")
+        with _lib.Solver(p) as s:
+            s.observables()
+            steps = 0
+            while steps < max_steps:
+                s.step(chunk)
+                steps += chunk
+                if s.observables()["steady_residual"] < tol:
+                    done64 += 1
+                    break
+            if k in served_fields:
+                want = s.state()
+                got = served_fields[k]
+                for a, b in zip(got[1:], want[1:]):
+                    worst = max(worst, float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
+    t64 = time.perf_counter() - t1
+    pct = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None  # noqa: E731
+    return {"requests": len(reqs), "completed": len(results), "converged": len(ok),
+            "solves_per_s": len(ok) / elapsed, "p50_s": pct(0.5), "p99_s": pct(0.99), "elapsed_s": elapsed,
+            "arrival_rate_per_s": rate, "tol": tol, "chunk_steps": chunk, "max_steps": max_steps,
+            "diameters": list(diameters), "mean_steps": float(np.mean([r["steps"] for r in results.values()]))
+            if results else None, "statuses": sorted({r["status"] for r in results.values()}),
+            "rebuilds": stats["rebuilds"],
+            "fp64_one_at_a_time": {"requests": min(baseline, len(reqs)), "converged": done64,
+                                   "solves_per_s": done64 / t64 if t64 > 0 else None, "seconds": t64,
+                                   "max_rel_l2_vs_served_fp32": worst}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +313,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -229,6 +360,7 @@ def main():
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    dev = torch.device("cuda", local)
     # dominant kernel: the fused sweep + IB-on-b kernel, timed over back-to-back launches
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,11 +370,8 @@ def main():
     barrier()
     sweep_ms = e0.elapsed_time(e1) / n_mag
     clk = clocks.stop()
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = ws * n * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(total_ms, dev)
+    value = replica_throughput(ws, n, args.steps, total_ms)
 
     # end to end through the public call with host buffers (pinned), per step
     o = solver.observables()
@@ -265,11 +394,8 @@ def main():
         h_b, o_b = o_b, h_b
         t_state += 1
     barrier()
-    e2e_s = time.perf_counter() - t0
-    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_e2e, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = ws * n * e2e_steps / float(t_e2e.item()) / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = replica_throughput(ws, n, e2e_steps, e2e_s * 1e3)
     state_bytes = 7 * n * 8
     obs_bytes = C.sizeof(_lib.qslbm_obs)
 
@@ -305,6 +431,9 @@ def main():
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_extras:
+        result["batched"] = run_batched()
+        result["serving"] = run_serving()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample()
     solver.close()
