@@ -133,8 +133,9 @@ typedef struct qslbm_obs {
     double visc;            /* -nu <u . lap u>                                    */
     double joule;           /* -<u . (J x B)>                                     */
     double qs_residual;     /* RMS of eta lap b - div(u B - B u)                  */
-    double steady_residual; /* |u - u_prev| / ((t - t_prev) |u|), u_prev from the
-                               previous qslbm_observables call                    */
+    double steady_residual; /* |u - u_prev| / ((t - t_prev) |u|) over the averaging
+                               region, u_prev from the previous qslbm_observables
+                               call                                               */
     int32_t nan_flag;       /* 1 if any field value is not finite                 */
 } qslbm_obs;
 

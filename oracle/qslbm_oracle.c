@@ -736,8 +736,10 @@ void orc_ib_apply_field(orc* o, double* f, int magnetic) {
  * over the same region of eta lap_m b - div_m(u B - B u), with the field
  * lattice's own second difference and central first difference (the operators
  * whose solution the sweep converges to).  The steady residual is
- * |u - u_snap|_2 / ((t - t_snap) |u|_2) against the state at the previous call,
- * which then becomes the new snapshot. */
+ * |u - u_snap|_2 / ((t - t_snap) |u|_2) over the same region against the state
+ * at the previous call, which then becomes the new snapshot (nodes outside the
+ * wall are not part of the pipe flow and would converge on their own, slower
+ * time scale). */
 void orc_observables(orc* o, double* out) {
     long n = o->n;
     double mass = 0.0, ek = 0.0, em = 0.0, pump = 0.0, visc = 0.0, joule = 0.0, qs = 0.0;
@@ -751,17 +753,17 @@ void orc_observables(orc* o, double* out) {
         if (!isfinite(o->rho[k])) nan = 1;
         for (int a = 0; a < 3; ++a)
             if (!isfinite(o->u[a][k]) || !isfinite(o->b[a][k])) nan = 1;
-        for (int a = 0; a < 3; ++a) {
-            double dd = o->u[a][k] - o->usnap[a][k];
-            du2 += dd * dd;
-            u2 += o->u[a][k] * o->u[a][k];
-        }
     }
     for (long k = 0; k < n; ++k) {
         int x, y, z;
         coords(o, k, &x, &y, &z);
         if (!in_fluid(o, x, y, 2.0)) continue;
         ++cnt;
+        for (int a = 0; a < 3; ++a) {
+            double dd = o->u[a][k] - o->usnap[a][k];
+            du2 += dd * dd;
+            u2 += o->u[a][k] * o->u[a][k];
+        }
         double Be[3], B[3], J[3];
         bext(o, x, y, z, Be);
         for (int a = 0; a < 3; ++a) B[a] = Be[a] + o->b[a][k];

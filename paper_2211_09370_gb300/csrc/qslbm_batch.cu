@@ -59,34 +59,25 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, i
     return lo;
 }
 
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch_sweep(const InstDesc<T>* __restrict__ d,
-                                                         const int* __restrict__ first, int kact, int s) {
+// Persistent z-marching sweep over every active instance's tiles: work item w
+// is (instance, tile x, tile y, z chunk) in the prefix table `first`.
+template <typename T>
+__global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
+                                                                    const int* __restrict__ first, int kact, int s) {
+    __shared__ T tile[6][kMarchTY + 2][kMarchTX + 2];
     const int total = first[kact];
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int i = find_inst(first, kact, w);
         const InstDesc<T>& D = d[i];
         const int local = w - first[i];
-        const int z = local / D.bpp;
-        const int p = (local - z * D.bpp) * THREADS + threadIdx.x;
-        const int nx = D.g.nx, ny = D.g.ny, nz = D.g.nz, P = nx * ny;
-        if (p >= P) continue;
+        const int tiles_x = (D.g.nx + kMarchTX - 1) / kMarchTX;
+        const int tiles_y = (D.g.ny + kMarchTY - 1) / kMarchTY;
+        const int bz = local / (tiles_x * tiles_y);
+        const int r = local - bz * tiles_x * tiles_y;
+        const int by = r / tiles_x, bx = r - by * tiles_x;
         const int par = (D.bpar + s) & 1;
-        const T* bin = D.b[par];
-        T* bout = D.b[par ^ 1];
-        const T* u = D.u[D.fpar];
-        const long long base = (long long)z * P;
-        const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
-        T be_c[3], be_m[3], be_p[3];
-        bext_at(D.sc.bext_z, D.sc.be, z, be_c);
-        bext_at(D.sc.bext_z, D.sc.be, zm, be_m);
-        bext_at(D.sc.bext_z, D.sc.be, zp, be_p);
-        T o[3];
-        sweep_node<T, 3>(bin, u, D.g.n, nx, ny, base, (long long)zm * P, (long long)zp * P, p, D.sc, be_c, be_m,
-                         be_p, o);
-        bout[base + p] = o[0];
-        bout[base + p + D.g.n] = o[1];
-        bout[base + p + 2 * D.g.n] = o[2];
+        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, tile);
+        __syncthreads();
     }
 }
 
@@ -246,10 +237,8 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int total = B.h_first[kact];
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
-    if (threads == 128)
-        qslbm::k_batch_sweep<T, 128><<<g, 128, 0, st>>>(d, B.first, kact, s);
-    else
-        qslbm::k_batch_sweep<T, 256><<<g, 256, 0, st>>>(d, B.first, kact, s);
+    (void)threads;
+    qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s);
     qslbm::k_batch_ib<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_smem, st>>>(d, B.pfirst, kact, s);
 }
 
@@ -274,8 +263,11 @@ int build_tables(qslbm_batch& B, int threads) {
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
-        h[k].bpp = (s.nx * s.ny + threads - 1) / threads;
-        B.h_first[k + 1] = B.h_first[k] + h[k].bpp * s.nz;
+        const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
+                          ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
+                          ((s.nz + qslbm::kMarchChunk - 1) / qslbm::kMarchChunk);
+        h[k].bpp = tiles;
+        B.h_first[k + 1] = B.h_first[k] + tiles;
         B.h_pfirst[k + 1] = B.h_pfirst[k] + s.nz;
         ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
     }
@@ -313,8 +305,7 @@ int autotune(qslbm_batch& B) {
         int threads, grid;
     };
     std::vector<Cand> cands;
-    for (int th : {128, 256})
-        for (int per_sm : {4, 8, 16, 0}) cands.push_back({th, per_sm ? per_sm * sms : 0});
+    for (int per_sm : {1, 2, 4, 8, 0}) cands.push_back({qslbm::kMarchTX * qslbm::kMarchTY, per_sm ? per_sm * sms : 0});
     // the tuning sweeps write b[other parity]; they read b[current] and u only,
     // so the state the batch starts from is untouched
     cudaEvent_t e0, e1;

@@ -254,6 +254,128 @@ __global__ void __launch_bounds__(kNodeThreads) k_sweep_nodes(Geo g, const T* __
     bout[base + p + 2 * n] = o[2];
 }
 
+// z-marching sweep without the IB (3-D): a CTA owns an (x, y) tile of
+// kMarchTX x kMarchTY columns and walks a chunk of z planes.  Each thread keeps
+// b and u of its column at z - 1, z, z + 1 in registers, so a node costs one
+// new load of (b, u) from HBM plus the tile's halo; the in-plane neighbours come
+// from the tile of plane z staged in shared memory.  Same expressions and
+// neighbour order as sweep_node.
+constexpr int kMarchTX = 32, kMarchTY = 8, kMarchChunk = 16;
+
+template <typename T>
+__device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
+                                           const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
+                                           T (*tile)[kMarchTY + 2][kMarchTX + 2]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int n = (int)g.n, P = nx * ny;
+    const int tx = threadIdx.x % kMarchTX, ty = threadIdx.x / kMarchTX;
+    const int x0 = bx * kMarchTX, y0 = by * kMarchTY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < nx && y < ny;
+    // columns past the domain edge stage the periodic images their neighbours need
+    const int xc = x % nx, yc = y % ny;
+    const int p = yc * nx + xc;
+    const int z0 = bz * kMarchChunk;
+    const int z1 = min(z0 + kMarchChunk, nz);
+    const T* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
+    // halo cells of the tile: ring of (kMarchTX + 2) x (kMarchTY + 2) minus the interior
+    constexpr int W = kMarchTX + 2, H = kMarchTY + 2, NH = 2 * W + 2 * kMarchTY;
+    int hx = 0, hy = 0;
+    const int hid = threadIdx.x;
+    if (hid < NH) {
+        if (hid < W) {
+            hx = hid;
+            hy = 0;
+        } else if (hid < 2 * W) {
+            hx = hid - W;
+            hy = H - 1;
+        } else {
+            const int r = hid - 2 * W;
+            hx = (r & 1) ? W - 1 : 0;
+            hy = 1 + (r >> 1);
+        }
+    }
+    const int gx = (x0 + hx - 1 + nx) % nx, gy = (y0 + hy - 1 + ny) % ny;
+    const int hp = hid < NH ? gy * nx + gx : -1;
+    T prv[6], cur[6], nxt[6];
+    {
+        const int zm = wrap_dec(z0, nz);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            prv[v] = src[v][zm * P + p];
+            cur[v] = src[v][z0 * P + p];
+        }
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int zn = wrap_inc(z, nz);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) nxt[v] = src[v][zn * P + p];
+        // stage plane z (interior from registers, halo from global)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) tile[v][ty + 1][tx + 1] = cur[v];
+        if (hp >= 0) {
+#pragma unroll
+            for (int v = 0; v < 6; ++v) tile[v][hy][hx] = src[v][z * P + hp];
+        }
+        __syncthreads();
+        if (active) {
+            T be_c[3], be_m[3], be_p[3];
+            bext_at(c.bext_z, c.be, z, be_c);
+            bext_at(c.bext_z, c.be, wrap_dec(z, nz), be_m);
+            bext_at(c.bext_z, c.be, zn, be_p);
+            T acc[3] = {c.w0 * cur[0], c.w0 * cur[1], c.w0 * cur[2]};
+            T diff[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                T bq[3], uq[3];
+                if (d < 4) {
+                    const int ix = tx + 1 + (d == 0 ? -1 : d == 1 ? 1 : 0);
+                    const int iy = ty + 1 + (d == 2 ? -1 : d == 3 ? 1 : 0);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        bq[a] = tile[a][iy][ix];
+                        uq[a] = tile[3 + a][iy][ix];
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        bq[a] = d == 4 ? prv[a] : nxt[a];
+                        uq[a] = d == 4 ? prv[3 + a] : nxt[3 + a];
+                    }
+                }
+                const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
+                T B[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+                T phi[3];
+                flux_pair(uq, B, d >> 1, phi);
+                const T sgn = (d & 1) ? T(-1) : T(1);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+            }
+            const int k = z * P + p;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bout[k + a * n] = acc[a] + c.w1 * c.kappa * diff[a];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            prv[v] = cur[v];
+            cur[v] = nxt[v];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMarchTX* kMarchTY) k_sweep_march(Geo g, const T* __restrict__ bin,
+                                                                    T* __restrict__ bout, const T* __restrict__ u,
+                                                                    SweepCoef<T> c) {
+    __shared__ T tile[6][kMarchTY + 2][kMarchTX + 2];  // b0 b1 b2 u0 u1 u2 of plane z with halo
+    march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+}
+
 // IB corrector alone, one CTA per z plane (after k_sweep_nodes).
 template <typename T>
 __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<T> ib) {
@@ -568,12 +690,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         const double bk[3] = {(double)b[k], (double)b[k + n], (double)b[k + 2 * n]};
         acc[0] += rho;
         bool bad = !isfinite(rho);
-        for (int a = 0; a < 3; ++a) {
-            bad = bad || !isfinite(uk[a]) || !isfinite(bk[a]);
-            const double du = uk[a] - (double)usnap[k + a * n];
-            acc[7] += du * du;
-            acc[8] += uk[a] * uk[a];
-        }
+        for (int a = 0; a < 3; ++a) bad = bad || !isfinite(uk[a]) || !isfinite(bk[a]);
         if (bad) acc[10] += 1.0;
         bool inside;
         if (c.geometry == 2)
@@ -584,6 +701,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
             inside = sqrt(((double)x - c.cx) * ((double)x - c.cx) + ((double)y - c.cy) * ((double)y - c.cy)) <= c.rin;
         if (!inside) continue;
         acc[9] += 1.0;
+        for (int a = 0; a < 3; ++a) {
+            const double du = uk[a] - (double)usnap[k + a * n];
+            acc[7] += du * du;
+            acc[8] += uk[a] * uk[a];
+        }
         T Be_t[3];
         bext_at(c.bext_z, c.be, z, Be_t);
         const double Be[3] = {(double)Be_t[0], (double)Be_t[1], (double)Be_t[2]};

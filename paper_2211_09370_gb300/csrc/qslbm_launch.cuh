@@ -62,12 +62,14 @@ struct Launch {
         if (s.p.sweep_kernel == QSLBM_SWEEP_SPLIT) {
             const int P = s.nx * s.ny;
             const dim3 grid((unsigned)((P + kNodeThreads - 1) / kNodeThreads), (unsigned)s.nz);
+            const dim3 mgrid((unsigned)((s.nx + kMarchTX - 1) / kMarchTX), (unsigned)((s.ny + kMarchTY - 1) / kMarchTY),
+                             (unsigned)((s.nz + kMarchChunk - 1) / kMarchChunk));
             for (int i = 0; i < nsweeps; ++i) {
                 const T* bin = (const T*)s.b[s.bcur];
                 T* bout = (T*)s.b[1 - s.bcur];
                 const T* u = (const T*)s.u[s.fcur];
                 if (s.dim == 3)
-                    k_sweep_nodes<T, 3><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
+                    k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c);
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
                 if (s.ib.nm > 0) k_ib_planes<T><<<s.nz, kNodeThreads, smem, st>>>(geo(s), bout, v);
