@@ -37,6 +37,13 @@ from paper_2211_09370_gb300 import workloads as W  # noqa: E402
 METRIC = "MLUPS"
 UNIT = "MLUPS"
 WORKLOAD = "pipe_64x64x128 D3Q19+D3Q7 D=56 Re=100 Ha=20 Rm=1e-3 N_mag=270 (10k-step workload, per step)"
+WORKLOADS = {
+    "pipe64": (WORKLOAD, lambda rank: W.pipe_64x64x128(seed=2211 + rank)),
+    # the non-uniform-field pipe (above L2): measurement of the HBM-bound path
+    "ramp96": ("pipe_ramp_96x96x512 D3Q19+D3Q7 D=88 tanh-ramped B0 Ha_max=50 Re=500 Rm=1e-2 N_mag=270 "
+               "pulsating force (20k-step workload, per step)",
+               lambda rank: W.pipe_ramp_96x96x512(Rm=1e-2, perturb=0.01, seed=7 + rank)),
+}
 
 
 def peaks():
@@ -313,6 +320,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--workload", default="pipe64", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -333,7 +341,8 @@ def main():
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    p = W.pipe_64x64x128(seed=2211 + rank)
+    workload_name, make = WORKLOADS[args.workload]
+    p = make(rank)
     solver = _lib.Solver(p, stream=stream.cuda_stream)
     n = solver.n
     n_mag = solver.units["n_mag"]
@@ -403,6 +412,10 @@ def main():
         kernel_name = "k_sweeps_resident<float,3> (all sweeps + IB on b, planes held in shared memory)"
         launches_per_step = 2 + 1
         per_launch_units = n_mag  # one launch runs every sweep of the step
+    elif solver.units["sweep_kernel"] == "split":
+        kernel_name = "k_sweep_march<float> + k_ib_planes<float> (one sweep: z-marching stencil, then IB on b)"
+        launches_per_step = 2 * n_mag + 2
+        per_launch_units = 1
     else:
         kernel_name = "k_sweep_ib<float,3> (one sweep + IB on b, one z plane per CTA)"
         launches_per_step = n_mag + 2
@@ -415,7 +428,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": n, "n_mag": n_mag, "precision": "fp32",
+        "config": {"workload": workload_name, "nodes": n, "n_mag": n_mag, "precision": "fp32",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                    "l2": "flushed before every timed step (256 MB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
