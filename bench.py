@@ -231,7 +231,7 @@ def run_batched(steps: int = 3, count: int = 64):
 
 
 def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_steps: int = 20000, chunk: int = 100,
-                diameters=(16, 24), time_cap_s: float = 150.0, baseline: int = 2, baseline_cap_s: float = 90.0):
+                diameters=(16, 24), time_cap_s: float = 150.0, baseline: int = 4):
     """Serving: Poisson arrivals of steady-state pipe solves (seed 5; diameters
     restricted so that the run stays bounded), admitted under a device-memory
     budget and advanced by continuous batching in FP32.  Reports solves/s and
@@ -261,7 +261,7 @@ def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_step
             delay = (ta - t_first) - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            ids[k] = S.submit(p, tol=tol, max_steps=max_steps, keep_fields=k < baseline)
+            ids[k] = S.submit(p, tol=tol, max_steps=max_steps)
 
     feed = th.Thread(target=feeder, daemon=True)
     feed.start()
@@ -278,28 +278,32 @@ def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_step
     lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
     stats = S.stats()
     by_k = {k: results.get(ids[k]) for k in range(len(reqs))}
-    served = {k: S.fields(ids[k]) for k in range(min(baseline, len(reqs)))
-              if by_k.get(k) and by_k[k]["status"] == 0}
     S.close()
-    # the same first requests, one at a time, FP64 single-instance handles
-    t1 = time.perf_counter()
-    worst, done64, steps64 = 0.0, 0, []
+    # The same first requests one at a time in FP64 (single-instance handles).
+    # A full FP64 solve of a request that needs ~10^4 steps takes minutes, so
+    # the FP64 step time is measured over `fp64_probe` steps and multiplied by
+    # the steps the served solve needed; accuracy is compared at equal steps.
+    fp64_probe = 200
+    t64_total, worst, solve_s = 0.0, 0.0, []
     for k in range(min(baseline, len(reqs))):
-        with _lib.Solver(dict(reqs[k][1], precision="fp64")) as s:
-            s.observables()
-            steps = 0
-            while steps < max_steps and time.perf_counter() - t1 < baseline_cap_s:
-                s.step(chunk)
-                steps += chunk
-                if s.observables()["steady_residual"] < tol:
-                    done64 += 1
-                    steps64.append(steps)
-                    if k in served:
-                        want = s.state()
-                        for a, b in zip(served[k][1:], want[1:]):
-                            worst = max(worst, float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
-                    break
-    t64 = time.perf_counter() - t1
+        r = by_k.get(k)
+        if not r or r["status"] != 0:
+            continue
+        with _lib.Solver(dict(reqs[k][1], precision="fp64")) as s64, \
+                _lib.Solver(dict(reqs[k][1], precision="fp32", sweep_kernel="split")) as s32:
+            s64.step(2)
+            s64.sync()
+            t1 = time.perf_counter()
+            s64.step(fp64_probe)
+            s64.sync()
+            dt = time.perf_counter() - t1
+            t64_total += dt
+            solve_s.append(dt / fp64_probe * r["steps"])
+            s32.step(fp64_probe + 2)
+            a = s32.state()
+            b = s64.state()
+            for x, y in zip(a[1:], b[1:]):
+                worst = max(worst, float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)))
     pct = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None  # noqa: E731
     return {"requests": len(reqs), "completed": len(results), "converged": len(ok),
             "solves_per_s": len(ok) / elapsed, "p50_s": pct(0.5), "p99_s": pct(0.99), "elapsed_s": elapsed,
@@ -307,9 +311,11 @@ def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_step
             "diameters": list(diameters),
             "mean_steps_converged": float(np.mean([r["steps"] for r in ok])) if ok else None,
             "statuses": sorted({r["status"] for r in results.values()}), "rebuilds": stats["rebuilds"],
-            "fp64_one_at_a_time": {"requests": min(baseline, len(reqs)), "converged": done64, "steps": steps64,
-                                   "solves_per_s": done64 / t64 if t64 > 0 else None, "seconds": t64,
-                                   "max_rel_l2_vs_served_fp32": worst}}
+            "fp64_one_at_a_time": {"requests": len(solve_s),
+                                   "seconds_per_solve": float(np.mean(solve_s)) if solve_s else None,
+                                   "solves_per_s": len(solve_s) / float(np.sum(solve_s)) if solve_s else None,
+                                   "method": f"FP64 step time over {fp64_probe} steps x steps the served solve took",
+                                   "fp32_vs_fp64_rel_l2_at_equal_steps": worst}}
 
 
 def main():

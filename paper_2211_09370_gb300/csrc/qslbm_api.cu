@@ -283,6 +283,20 @@ int upload_ib(State& s) {
     if ((rc = upload_real(s, &d.mk_w, w9))) return rc;
     if ((rc = upload_real(s, &d.mk_s, h.s))) return rc;
     if ((rc = upload_real(s, &d.mk_sm, h.sm))) return rc;
+    {
+        const long long P = (long long)s.nx * s.ny;
+        std::vector<int> mbase(nm), snode(h.shell_xy.size()), cmg(h.csr_m.size());
+        for (size_t j = 0; j < nm; ++j) mbase[j] = (int)(h.zplane[j] * P);
+        for (int z = 0; z < s.nz; ++z)
+            for (int i = h.shell_off[z]; i < h.shell_off[z + 1]; ++i) {
+                snode[i] = (int)(z * P + h.shell_xy[i]);
+                for (int e = h.csr_off[i]; e < h.csr_off[i + 1]; ++e) cmg[e] = h.ring_off[z] + h.csr_m[e];
+            }
+        if ((rc = upload(s, (void**)&d.mk_base, mbase))) return rc;
+        if ((rc = upload(s, (void**)&d.shell_node, snode))) return rc;
+        if ((rc = upload(s, (void**)&d.csr_mg, cmg))) return rc;
+        if ((rc = dev_alloc(s, &d.delta, (size_t)3 * std::max<size_t>(1, nm) * s.esz))) return rc;
+    }
     if ((rc = upload(s, (void**)&d.shell_off, h.shell_off))) return rc;
     if ((rc = upload(s, (void**)&d.shell_xy, h.shell_xy))) return rc;
     if ((rc = upload(s, (void**)&d.csr_off, h.csr_off))) return rc;
@@ -421,6 +435,13 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         }
     }
     if (!s.resident && s.p.sweep_kernel == QSLBM_SWEEP_AUTO) s.p.sweep_kernel = QSLBM_SWEEP_SPLIT;
+    {
+        cudaError_t e = ops(s).plan_march(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "plan_march");
+            goto fail;
+        }
+    }
     s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : s.p.sweep_kernel;
     {
         long long zero = 0;

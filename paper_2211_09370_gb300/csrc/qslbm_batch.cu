@@ -76,9 +76,31 @@ __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDe
         const int r = local - bz * tiles_x * tiles_y;
         const int by = r / tiles_x, bx = r - by * tiles_x;
         const int par = (D.bpar + s) & 1;
-        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, tile);
+        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, kMarchChunk, tile);
         __syncthreads();
     }
+}
+
+// Two-phase IB over every active instance: markers, then (next launch) shell
+// nodes; w indexes the prefix tables of markers / shell nodes.
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_batch_ib_markers(const InstDesc<T>* __restrict__ d,
+                                                                   const int* __restrict__ mfirst, int kact, int s) {
+    const int w = blockIdx.x * kNodeThreads + threadIdx.x;
+    if (w >= mfirst[kact]) return;
+    const int i = find_inst(mfirst, kact, w);
+    const InstDesc<T>& D = d[i];
+    ib_marker<T>(D.ibm, D.b[((D.bpar + s) & 1) ^ 1], (int)D.g.n, w - mfirst[i]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_batch_ib_shell(const InstDesc<T>* __restrict__ d,
+                                                                 const int* __restrict__ sfirst, int kact, int s) {
+    const int w = blockIdx.x * kNodeThreads + threadIdx.x;
+    if (w >= sfirst[kact]) return;
+    const int i = find_inst(sfirst, kact, w);
+    const InstDesc<T>& D = d[i];
+    ib_shell<T>(D.ibm, D.b[((D.bpar + s) & 1) ^ 1], (int)D.g.n, w - sfirst[i]);
 }
 
 template <typename T>
@@ -155,7 +177,9 @@ struct qslbm_batch {
     void* desc = nullptr;                // InstDesc<T>[K]
     int* first = nullptr;                // node-block prefix [K + 1]
     int* pfirst = nullptr;               // plane prefix [K + 1]
-    std::vector<int> h_first, h_pfirst;
+    int* mfirst = nullptr;               // marker prefix [K + 1]
+    int* sfirst = nullptr;               // shell-node prefix [K + 1]
+    std::vector<int> h_first, h_pfirst, h_mfirst, h_sfirst;
     std::vector<int> active;             // active[s] = instances with N_mag > s
     int max_nmag = 0;
     int capacity = 0;                    // instances the device tables can hold
@@ -225,7 +249,12 @@ qslbm::InstDesc<T> make_desc(const State& s) {
         v.csr_off = s.ib.csr_off;
         v.csr_m = s.ib.csr_m;
         v.csr_w = (const T*)s.ib.csr_w;
+        v.mk_base = s.ib.mk_base;
+        v.shell_node = s.ib.shell_node;
+        v.csr_mg = s.ib.csr_mg;
+        v.delta = (T*)s.ib.delta;
         v.nm = s.ib.nm;
+        v.ns = s.ib.ns;
     }
     return D;
 }
@@ -239,7 +268,13 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
     (void)threads;
     qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s);
-    qslbm::k_batch_ib<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_smem, st>>>(d, B.pfirst, kact, s);
+    const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
+    if (nm > 0) {
+        qslbm::k_batch_ib_markers<T><<<(nm + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
+                                        st>>>(d, B.mfirst, kact, s);
+        qslbm::k_batch_ib_shell<T><<<(ns + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
+                                      st>>>(d, B.sfirst, kact, s);
+    }
 }
 
 template <typename T>
@@ -259,6 +294,8 @@ int build_tables(qslbm_batch& B, int threads) {
     std::vector<qslbm::InstDesc<T>> h(K);
     B.h_first.assign(K + 1, 0);
     B.h_pfirst.assign(K + 1, 0);
+    B.h_mfirst.assign(K + 1, 0);
+    B.h_sfirst.assign(K + 1, 0);
     size_t ring = 1;
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
@@ -269,6 +306,8 @@ int build_tables(qslbm_batch& B, int threads) {
         h[k].bpp = tiles;
         B.h_first[k + 1] = B.h_first[k] + tiles;
         B.h_pfirst[k + 1] = B.h_pfirst[k] + s.nz;
+        B.h_mfirst[k + 1] = B.h_mfirst[k] + s.ib.nm;
+        B.h_sfirst[k + 1] = B.h_sfirst[k] + s.ib.ns;
         ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
     }
     B.ib_smem = 3 * ring * sizeof(T);
@@ -276,18 +315,24 @@ int build_tables(qslbm_batch& B, int threads) {
         if (B.desc) cudaFree(B.desc);
         if (B.first) cudaFree(B.first);
         if (B.pfirst) cudaFree(B.pfirst);
+        if (B.mfirst) cudaFree(B.mfirst);
+        if (B.sfirst) cudaFree(B.sfirst);
         B.desc = nullptr;
-        B.first = B.pfirst = nullptr;
+        B.first = B.pfirst = B.mfirst = B.sfirst = nullptr;
         const int cap = std::max(K, 2 * B.capacity);
         BCHK(cudaMalloc(&B.desc, sizeof(qslbm::InstDesc<T>) * cap));
         BCHK(cudaMalloc((void**)&B.first, sizeof(int) * (cap + 1)));
         BCHK(cudaMalloc((void**)&B.pfirst, sizeof(int) * (cap + 1)));
-        B.device_bytes = (long long)(sizeof(qslbm::InstDesc<T>) * cap + 2 * sizeof(int) * (cap + 1));
+        BCHK(cudaMalloc((void**)&B.mfirst, sizeof(int) * (cap + 1)));
+        BCHK(cudaMalloc((void**)&B.sfirst, sizeof(int) * (cap + 1)));
+        B.device_bytes = (long long)(sizeof(qslbm::InstDesc<T>) * cap + 4 * sizeof(int) * (cap + 1));
         B.capacity = cap;
     }
     BCHK(cudaMemcpyAsync(B.desc, h.data(), sizeof(qslbm::InstDesc<T>) * K, cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.first, B.h_first.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.pfirst, B.h_pfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
+    BCHK(cudaMemcpyAsync(B.mfirst, B.h_mfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
+    BCHK(cudaMemcpyAsync(B.sfirst, B.h_sfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaStreamSynchronize(B.stream));
     return QSLBM_OK;
 }
@@ -370,6 +415,8 @@ void destroy_batch(qslbm_batch* B) {
     if (B->desc) cudaFree(B->desc);
     if (B->first) cudaFree(B->first);
     if (B->pfirst) cudaFree(B->pfirst);
+    if (B->mfirst) cudaFree(B->mfirst);
+    if (B->sfirst) cudaFree(B->sfirst);
     if (B->owns_members)
         for (qslbm_handle* h : B->members) qslbm_destroy(h);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);

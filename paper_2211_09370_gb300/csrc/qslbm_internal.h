@@ -20,6 +20,8 @@ struct DeviceIB {
     int *ring_off = nullptr, *mk_q = nullptr;
     int *shell_off = nullptr, *shell_xy = nullptr, *csr_off = nullptr, *csr_m = nullptr;
     void *mk_w = nullptr, *mk_s = nullptr, *mk_sm = nullptr, *csr_w = nullptr;
+    int *mk_base = nullptr, *shell_node = nullptr, *csr_mg = nullptr;
+    void *delta = nullptr;  // [3 nm] markers' corrections (two-phase corrector)
     int nm = 0, ns = 0, nnz = 0, max_ring = 0, max_shell = 0, max_nnz = 0;
 };
 
@@ -65,6 +67,7 @@ struct State {
     // resident sub-iteration (all sweeps of a step in one cooperative launch)
     bool resident = false;
     bool launch_error = false;  // a cudaLaunchKernelEx call failed
+    int march_chunk = 16;       // z planes per CTA of the marching sweep (one wave)
     bool resident_uhalo = false;
     size_t resident_smem = 0;
     void* xbuf = nullptr;   // [2][nz][3][P] plane exchange
@@ -85,6 +88,7 @@ struct Ops {
     // decide whether the resident sweep kernel fits this domain; sets
     // s.resident, s.resident_uhalo, s.resident_smem (no allocation)
     cudaError_t (*plan_resident)(State&);
+    cudaError_t (*plan_march)(State&);  // sets s.march_chunk
 };
 
 const Ops& ops_f32();

@@ -47,7 +47,11 @@ struct IBView {
     const int* csr_off;    // [ns + 1]: entries of shell node s
     const int* csr_m;      // [nnz]: marker index relative to its ring
     const T* csr_w;        // [nnz]: D(x_k - X_j) for that pair
-    int nm;
+    const int* mk_base;    // [nm]: first node of the marker's plane (z * nx * ny)
+    const int* shell_node; // [ns]: node index of each shell node
+    const int* csr_mg;     // [nnz]: marker index in the whole domain
+    T* delta;              // [3 * nm]: delta_j of the two-phase corrector
+    int nm, ns;
 };
 
 // Coefficients of the tau_m = 1 magnetic sweep (Sec. V.G).
@@ -265,7 +269,7 @@ constexpr int kMarchTX = 32, kMarchTY = 8, kMarchChunk = 16;
 template <typename T>
 __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
                                            const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
-                                           T (*tile)[kMarchTY + 2][kMarchTX + 2]) {
+                                           int chunk, T (*tile)[kMarchTY + 2][kMarchTX + 2]) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int n = (int)g.n, P = nx * ny;
     const int tx = threadIdx.x % kMarchTX, ty = threadIdx.x / kMarchTX;
@@ -275,8 +279,8 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     // columns past the domain edge stage the periodic images their neighbours need
     const int xc = x % nx, yc = y % ny;
     const int p = yc * nx + xc;
-    const int z0 = bz * kMarchChunk;
-    const int z1 = min(z0 + kMarchChunk, nz);
+    const int z0 = bz * chunk;
+    const int z1 = min(z0 + chunk, nz);
     const T* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
     // halo cells of the tile: ring of (kMarchTX + 2) x (kMarchTY + 2) minus the interior
     constexpr int W = kMarchTX + 2, H = kMarchTY + 2, NH = 2 * W + 2 * kMarchTY;
@@ -297,19 +301,25 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     }
     const int gx = (x0 + hx - 1 + nx) % nx, gy = (y0 + hy - 1 + ny) % ny;
     const int hp = hid < NH ? gy * nx + gx : -1;
-    T prv[6], cur[6], nxt[6];
+    // prv / cur / nxt hold planes z - 1, z, z + 1; ahd is loaded one plane
+    // ahead (z + 2) so that its memory latency overlaps the work on plane z
+    T prv[6], cur[6], nxt[6], ahd[6];
     {
-        const int zm = wrap_dec(z0, nz);
+        const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
             prv[v] = src[v][zm * P + p];
             cur[v] = src[v][z0 * P + p];
+            nxt[v] = src[v][zn * P + p];
         }
     }
     for (int z = z0; z < z1; ++z) {
         const int zn = wrap_inc(z, nz);
+        if (z + 1 < z1) {
+            const int za = wrap_inc(zn, nz);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) nxt[v] = src[v][zn * P + p];
+            for (int v = 0; v < 6; ++v) ahd[v] = src[v][za * P + p];
+        }
         // stage plane z (interior from registers, halo from global)
 #pragma unroll
         for (int v = 0; v < 6; ++v) tile[v][ty + 1][tx + 1] = cur[v];
@@ -364,6 +374,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
         for (int v = 0; v < 6; ++v) {
             prv[v] = cur[v];
             cur[v] = nxt[v];
+            nxt[v] = ahd[v];
         }
     }
 }
@@ -371,9 +382,60 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
 template <typename T>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_sweep_march(Geo g, const T* __restrict__ bin,
                                                                     T* __restrict__ bout, const T* __restrict__ u,
-                                                                    SweepCoef<T> c) {
+                                                                    SweepCoef<T> c, int chunk) {
     __shared__ T tile[6][kMarchTY + 2][kMarchTX + 2];  // b0 b1 b2 u0 u1 u2 of plane z with halo
-    march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+    march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, chunk, tile);
+}
+
+// Two-phase IB corrector over the whole domain (Sec. V.C-V.F): first one
+// thread per marker forms delta_j = s_j (0 - D f*) from the predictor field,
+// then (next launch, so every delta is ready) one thread per shell node adds
+// sum_j D(x_k - X_j) delta_j.  Same sums, in the same order, as ib_plane.
+template <typename T>
+__device__ __forceinline__ void ib_marker(const IBView<T>& ib, const T* __restrict__ f, int n, int m) {
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    const int base = ib.mk_base[m];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const T w = ib.mk_w[9 * m + j];
+        const int q = base + ib.mk_q[9 * m + j];
+        a0 += w * f[q];
+        a1 += w * f[q + n];
+        a2 += w * f[q + 2 * n];
+    }
+    const T sm = ib.mk_s[m];
+    ib.delta[3 * m + 0] = -sm * a0;
+    ib.delta[3 * m + 1] = -sm * a1;
+    ib.delta[3 * m + 2] = -sm * a2;
+}
+
+template <typename T>
+__device__ __forceinline__ void ib_shell(const IBView<T>& ib, T* __restrict__ f, int n, int i) {
+    T c0 = T(0), c1 = T(0), c2 = T(0);
+    const int e0 = ib.csr_off[i], e1 = ib.csr_off[i + 1];
+    for (int e = e0; e < e1; ++e) {
+        const T w = ib.csr_w[e];
+        const int m = ib.csr_mg[e];
+        c0 += w * ib.delta[3 * m + 0];
+        c1 += w * ib.delta[3 * m + 1];
+        c2 += w * ib.delta[3 * m + 2];
+    }
+    const int q = ib.shell_node[i];
+    f[q] += c0;
+    f[q + n] += c1;
+    f[q + 2 * n] += c2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_ib_markers(Geo g, const T* __restrict__ f, IBView<T> ib) {
+    const int m = blockIdx.x * kNodeThreads + threadIdx.x;
+    if (m < ib.nm) ib_marker<T>(ib, f, (int)g.n, m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_ib_shell(Geo g, T* __restrict__ f, IBView<T> ib) {
+    const int i = blockIdx.x * kNodeThreads + threadIdx.x;
+    if (i < ib.ns) ib_shell<T>(ib, f, (int)g.n, i);
 }
 
 // IB corrector alone, one CTA per z plane (after k_sweep_nodes).

@@ -2,6 +2,8 @@
 // qslbm_f64.cu, which instantiate it for float and double.
 #pragma once
 
+#include <algorithm>
+
 #include "qslbm_internal.h"
 #include "qslbm_kernels.cuh"
 #include "qslbm_resident.cuh"
@@ -23,7 +25,12 @@ struct Launch {
         v.csr_off = s.ib.csr_off;
         v.csr_m = s.ib.csr_m;
         v.csr_w = static_cast<const T*>(s.ib.csr_w);
+        v.mk_base = s.ib.mk_base;
+        v.shell_node = s.ib.shell_node;
+        v.csr_mg = s.ib.csr_mg;
+        v.delta = static_cast<T*>(s.ib.delta);
         v.nm = s.ib.nm;
+        v.ns = s.ib.ns;
         return v;
     }
 
@@ -62,17 +69,21 @@ struct Launch {
         if (s.p.sweep_kernel == QSLBM_SWEEP_SPLIT) {
             const int P = s.nx * s.ny;
             const dim3 grid((unsigned)((P + kNodeThreads - 1) / kNodeThreads), (unsigned)s.nz);
+            const int chunk = s.march_chunk;
             const dim3 mgrid((unsigned)((s.nx + kMarchTX - 1) / kMarchTX), (unsigned)((s.ny + kMarchTY - 1) / kMarchTY),
-                             (unsigned)((s.nz + kMarchChunk - 1) / kMarchChunk));
+                             (unsigned)((s.nz + chunk - 1) / chunk));
             for (int i = 0; i < nsweeps; ++i) {
                 const T* bin = (const T*)s.b[s.bcur];
                 T* bout = (T*)s.b[1 - s.bcur];
                 const T* u = (const T*)s.u[s.fcur];
                 if (s.dim == 3)
-                    k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c);
+                    k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
-                if (s.ib.nm > 0) k_ib_planes<T><<<s.nz, kNodeThreads, smem, st>>>(geo(s), bout, v);
+                if (s.ib.nm > 0) {
+                    k_ib_markers<T><<<(s.ib.nm + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
+                    k_ib_shell<T><<<(s.ib.ns + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
+                }
                 s.bcur ^= 1;
             }
             return;
@@ -161,6 +172,23 @@ struct Launch {
     static cudaError_t try_resident(State& s, size_t smem, bool& ok) {
         if ((long long)s.nx * s.ny <= (long long)RT * RN) return try_resident_npt<DIM, UHALO, RN>(s, smem, ok);
         return try_resident_npt<DIM, UHALO, 2 * RN>(s, smem, ok);
+    }
+
+    // z planes per CTA of the marching sweep such that the grid fills one wave
+    static cudaError_t plan_march(State& s) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T>, kMarchTX * kMarchTY, 0);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)((s.nx + kMarchTX - 1) / kMarchTX) * ((s.ny + kMarchTY - 1) / kMarchTY);
+        const long long slots = (long long)std::max(1, per_sm) * std::max(1, sms);
+        const long long per_column = std::max<long long>(1, slots / std::max<long long>(1, tiles));
+        long long chunk = (s.nz + per_column - 1) / per_column;
+        chunk = std::max<long long>(chunk, 4);  // keep the z halo overhead small
+        s.march_chunk = (int)std::min<long long>(chunk, s.nz);
+        return cudaSuccess;
     }
 
     static cudaError_t plan_resident(State& s) {
@@ -263,7 +291,7 @@ struct Launch {
     }
 
     static const Ops& table() {
-        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64, &plan_resident};
+        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64, &plan_resident, &plan_march};
         return o;
     }
 };
