@@ -230,6 +230,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     for (int a = 0; a < 3; ++a) D.sc.be[a] = (T)s.be[a];
     D.sc.bext_z = (const T*)s.bext_z;
     D.sc.strict_qs = s.p.strict_qs;
+    D.sc.sq = s.p.strict_qs ? T(0) : T(1);
     D.fc.F0 = s.units.F0;
     D.fc.amp = s.p.force_amp;
     D.fc.omega = s.omega;

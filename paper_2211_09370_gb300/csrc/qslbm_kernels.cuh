@@ -62,6 +62,7 @@ struct SweepCoef {
     T be[3];       // uniform B^ext (used when bext_z == nullptr)
     const T* bext_z;  // [3 * nz] B^ext per plane for the ramp, or nullptr
     int strict_qs;
+    T sq;          // weight of b in the flux's B: 1, or 0 for the strict QS flux
 };
 
 // Coefficients of the flow update (Sec. III.E, V.A).
@@ -147,11 +148,14 @@ __device__ __forceinline__ void ib_plane(const IBView<T>& ib, T* f0, T* f1, T* f
 //               + kappa (Phi_ab(x - e_beta) - Phi_ab(x + e_beta)) ],
 // Phi_ab = u_beta B_alpha - u_alpha B_beta, B = B^ext + b (B^ext only if
 // strict_qs).  This is sum_i g^eq_i(x - e_i) of Sec. V.G written per axis.
+// diff[alpha] += sgn Phi_{alpha beta}, Phi_{alpha beta} = u_beta B_alpha - u_alpha B_beta,
+// for alpha != beta (Phi_{beta beta} is zero).  beta is a constant after the
+// callers' loops are unrolled, so the skipped component costs nothing.
 template <typename T>
-__device__ __forceinline__ void flux_pair(const T u[3], const T B[3], int beta, T phi[3]) {
-    // phi[alpha] = u_beta B_alpha - u_alpha B_beta
+__device__ __forceinline__ void flux_acc(const T u[3], const T B[3], int beta, T sgn, T diff[3]) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) phi[a] = u[beta] * B[a] - u[a] * B[beta];
+    for (int a = 0; a < 3; ++a)
+        if (a != beta) diff[a] += sgn * (u[beta] * B[a] - u[a] * B[beta]);
 }
 
 // One node of the sweep: in-plane index p of the plane at base, z neighbours
@@ -193,12 +197,9 @@ __device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* _
         const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
         T B[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
-        T phi[3];
-        flux_pair(uq, B, d >> 1, phi);
-        const T sgn = (d & 1) ? T(-1) : T(1);  // x - e_beta enters with +, x + e_beta with -
-#pragma unroll
-        for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+        for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
+        // x - e_beta enters with +, x + e_beta with -
+        flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) out[a] = acc[a] + c.w1 * c.kappa * diff[a];
@@ -358,12 +359,8 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                 for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
                 T B[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
-                T phi[3];
-                flux_pair(uq, B, d >> 1, phi);
-                const T sgn = (d & 1) ? T(-1) : T(1);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) diff[a] += sgn * phi[a];
+                for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
+                flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
             }
             const int k = z * P + p;
 #pragma unroll
@@ -752,6 +749,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         const double bk[3] = {(double)b[k], (double)b[k + n], (double)b[k + 2 * n]};
         acc[0] += rho;
         bool bad = !isfinite(rho);
+#pragma unroll
         for (int a = 0; a < 3; ++a) bad = bad || !isfinite(uk[a]) || !isfinite(bk[a]);
         if (bad) acc[10] += 1.0;
         bool inside;
@@ -763,6 +761,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
             inside = sqrt(((double)x - c.cx) * ((double)x - c.cx) + ((double)y - c.cy) * ((double)y - c.cy)) <= c.rin;
         if (!inside) continue;
         acc[9] += 1.0;
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double du = uk[a] - (double)usnap[k + a * n];
             acc[7] += du * du;
@@ -778,6 +777,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         // flow-lattice Laplacian of u and isotropic gradient of b
         double lap[3] = {0.0, 0.0, 0.0};
         double db[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+#pragma unroll
         for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
             int cx, cy, cz;
             if (DIM == 3)
@@ -786,6 +786,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
                 flow_dir2(j, cx, cy, cz);
             const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
             const double w = flow_w<DIM>(j);
+#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 lap[a] += w * ((double)u[q + a * n] - uk[a]);
                 const double bq = (double)b[q + a * n];
@@ -795,14 +796,17 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
             }
         }
         double ulap = 0.0;
+#pragma unroll
         for (int a = 0; a < 3; ++a) ulap += uk[a] * 6.0 * lap[a];
         acc[4] += ulap;
         const double J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
         const double L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
         acc[5] += -(uk[0] * L[0] + uk[1] * L[1] + uk[2] * L[2]);
         // QS residual with the field lattice's operators
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             double lapb = 0.0, div = 0.0;
+#pragma unroll
             for (int be = 0; be < DIM; ++be) {
                 const int ex = be == 0, ey = be == 1, ez = be == 2;
                 const int zpp = wrapi(z + ez, nz), zmm = wrapi(z - ez, nz);
@@ -813,6 +817,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
                 bext_at(c.bext_z, c.be, zpp, Bep_t);
                 bext_at(c.bext_z, c.be, zmm, Bem_t);
                 double Bp[3], Bm[3];
+#pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
                     Bp[cc] = (double)Bep_t[cc] + (c.strict_qs ? 0.0 : (double)b[kp + cc * n]);
                     Bm[cc] = (double)Bem_t[cc] + (c.strict_qs ? 0.0 : (double)b[km + cc * n]);

@@ -59,6 +59,7 @@ struct Launch {
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
         c.bext_z = static_cast<const T*>(s.bext_z);
         c.strict_qs = s.p.strict_qs;
+        c.sq = s.p.strict_qs ? T(0) : T(1);
         const IBView<T> v = view(s, true);
         const size_t smem = ib_smem(s);
         if (s.resident && nsweeps > 0) {
@@ -119,11 +120,17 @@ struct Launch {
         const T* bin = (const T*)s.b[s.bcur];
         T* bout = (T*)s.b[1 - s.bcur];
         const T* u = (const T*)s.u[s.fcur];
-        // a failed launch is recorded for cudaGetLastError, which the caller checks
-        if (cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO, RT, NPT>, geo(s), bin, bout, u, c, v,
-                               (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps, s.ib.max_ring, s.ib.max_shell,
-                               s.ib.max_nnz) != cudaSuccess)
-            s.launch_error = true;
+        cudaError_t e;
+        if (s.nx % 2 == 0)
+            e = cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO, RT, NPT, true>, geo(s), bin, bout, u, c, v,
+                                   (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps, s.ib.max_ring, s.ib.max_shell,
+                                   s.ib.max_nnz);
+        else
+            e = cudaLaunchKernelEx(&cfg, k_sweeps_resident<T, DIM, UHALO, RT, NPT, false>, geo(s), bin, bout, u, c,
+                                   v, (T*)s.xbuf, (ResidentSync*)s.rsync, nsweeps, s.ib.max_ring, s.ib.max_shell,
+                                   s.ib.max_nnz);
+        // a failed launch is recorded for the caller
+        if (e != cudaSuccess) s.launch_error = true;
     }
 
     static void launch_resident(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
@@ -152,8 +159,10 @@ struct Launch {
     template <int DIM, bool UHALO, int NPT>
     static cudaError_t try_resident_npt(State& s, size_t smem, bool& ok) {
         ok = false;
-        auto kern = k_sweeps_resident<T, DIM, UHALO, RT, NPT>;
+        auto kern = k_sweeps_resident<T, DIM, UHALO, RT, NPT, false>;
+        auto kern2 = k_sweeps_resident<T, DIM, UHALO, RT, NPT, true>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return cudaSuccess;  // too much shared memory: not resident

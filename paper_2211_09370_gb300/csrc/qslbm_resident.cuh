@@ -57,6 +57,40 @@ __device__ __forceinline__ T ldcg(const T* p) {
     return __ldcg(p);
 }
 
+// Two adjacent values (8-byte float2 or 16-byte double2 accesses).
+template <typename T>
+struct Two;
+template <>
+struct Two<float> {
+    using V = float2;
+};
+template <>
+struct Two<double> {
+    using V = double2;
+};
+template <typename T>
+__device__ __forceinline__ typename Two<T>::V ld2(const T* p) {
+    return *reinterpret_cast<const typename Two<T>::V*>(p);
+}
+template <typename T>
+__device__ __forceinline__ typename Two<T>::V ldcg2(const T* p) {
+    return __ldcg(reinterpret_cast<const typename Two<T>::V*>(p));
+}
+template <typename T>
+__device__ __forceinline__ void st2(T* p, T a, T b) {
+    typename Two<T>::V v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<typename Two<T>::V*>(p) = v;
+}
+template <typename T>
+__device__ __forceinline__ void stcg2(T* p, T a, T b) {
+    typename Two<T>::V v;
+    v.x = a;
+    v.y = b;
+    __stcg(reinterpret_cast<typename Two<T>::V*>(p), v);
+}
+
 // Shared-memory copy of one plane's IB tables (ring markers and shell CSR).
 template <typename T>
 struct LocalIB {
@@ -118,7 +152,9 @@ __host__ __device__ inline size_t resident_smem_bytes(int P, bool uhalo, int max
     return nT * sizeof(T) + nI * sizeof(int);
 }
 
-template <typename T, int DIM, bool UHALO, int kResidentThreads, int kResidentMaxNpt>
+// PAIR: each thread takes x-adjacent node pairs (nx even), so that own-row,
+// y-neighbour and z-neighbour values move two at a time.
+template <typename T, int DIM, bool UHALO, int kResidentThreads, int kResidentMaxNpt, bool PAIR>
 __global__ void __launch_bounds__(kResidentThreads, 1)
     k_sweeps_resident(Geo g, const T* __restrict__ b_in, T* __restrict__ b_out, const T* __restrict__ u,
                       SweepCoef<T> c, IBView<T> ib, T* xbuf, ResidentSync* sync, int nsweeps, int max_ring,
@@ -195,6 +231,128 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     const unsigned int epoch = s_epoch;
     const long long xplane = 3LL * P;
     for (int s = 0; s < nsweeps; ++s) {
+        const bool publish = DIM == 3 && s + 1 < nsweeps;
+        T* xout = xbuf + (long long)(s & 1) * nz * xplane + (long long)z * xplane;
+        if constexpr (PAIR) {
+        constexpr int NPAIR = kResidentMaxNpt / 2;
+        // (1) in-plane part, pairs (x, x + 1) with x even
+        T nv[NPAIR][2][3];
+#pragma unroll
+        for (int k = 0; k < NPAIR; ++k) {
+            const int p0 = 2 * (tid + k * kResidentThreads);
+            if (p0 < P) {
+                const int y = p0 / nx;
+                const int x0 = p0 - y * nx;
+                const int rc = y * nx, rm = wrap_dec(y, ny) * nx, rp = wrap_inc(y, ny) * nx;
+                const int xl = wrap_dec(x0, nx), xr = x0 + 2 == nx ? 0 : x0 + 2;
+                T bC[2][3], bN[2][4][3], uN[2][4][3];  // own b; neighbours -x, +x, -y, +y
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const auto cb = ld2(sb + a * P + rc + x0), cu = ld2(su + a * P + rc + x0);
+                    const auto mb = ld2(sb + a * P + rm + x0), mu = ld2(su + a * P + rm + x0);
+                    const auto pb = ld2(sb + a * P + rp + x0), pu = ld2(su + a * P + rp + x0);
+                    const T lb = sb[a * P + rc + xl], lu = su[a * P + rc + xl];
+                    const T rb = sb[a * P + rc + xr], ru = su[a * P + rc + xr];
+                    bC[0][a] = cb.x;
+                    bC[1][a] = cb.y;
+                    bN[0][0][a] = lb;   uN[0][0][a] = lu;
+                    bN[0][1][a] = cb.y; uN[0][1][a] = cu.y;
+                    bN[0][2][a] = mb.x; uN[0][2][a] = mu.x;
+                    bN[0][3][a] = pb.x; uN[0][3][a] = pu.x;
+                    bN[1][0][a] = cb.x; uN[1][0][a] = cu.x;
+                    bN[1][1][a] = rb;   uN[1][1][a] = ru;
+                    bN[1][2][a] = mb.y; uN[1][2][a] = mu.y;
+                    bN[1][3][a] = pb.y; uN[1][3][a] = pu.y;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    T acc[3], dif[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        acc[a] = c.w0 * bC[h][a];
+                        dif[a] = T(0);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        T B[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            acc[a] += c.w1 * bN[h][d][a];
+                            B[a] = be_c[a] + c.sq * bN[h][d][a];
+                        }
+                        flux_acc(uN[h][d], B, d >> 1, (d & 1) ? T(-1) : T(1), dif);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) nv[k][h][a] = acc[a] + c.w1 * c.kappa * dif[a];
+                }
+            }
+        }
+        // (2) neighbour planes of the previous sweep
+        if (DIM == 3 && s > 0) {
+            if (tid == 0) {
+                const unsigned int target = epoch + (unsigned int)s;
+                const unsigned long long t0 = globaltimer_ns();
+                while ((int)(ld_acquire_u32(&sync->flags[zm]) - target) < 0 ||
+                       (int)(ld_acquire_u32(&sync->flags[zp]) - target) < 0) {
+                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+                        atomicExch(&sync->err, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(16);
+                }
+            }
+            __syncthreads();
+            if (s_abort) return;
+        }
+        // (3) the z terms, two nodes at a time
+        const T* xin = xbuf + (long long)((s - 1) & 1) * nz * xplane;
+#pragma unroll
+        for (int k = 0; k < NPAIR; ++k) {
+            const int p0 = 2 * (tid + k * kResidentThreads);
+            if (DIM == 3 && p0 < P) {
+#pragma unroll
+                for (int d = 4; d < 6; ++d) {
+                    const int zn = d == 4 ? zm : zp;
+                    const T* bez = d == 4 ? be_m : be_p;
+                    T bq[2][3], uq[2][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const auto vb = s == 0 ? ld2(b_in + a * n + (long long)zn * P + p0)
+                                               : ldcg2(xin + (long long)zn * xplane + (long long)a * P + p0);
+                        const auto vu = UHALO ? ld2(suh + ((d == 4 ? 0 : 3) + a) * P + p0)
+                                              : ld2(u + a * n + (long long)zn * P + p0);
+                        bq[0][a] = vb.x;
+                        bq[1][a] = vb.y;
+                        uq[0][a] = vu.x;
+                        uq[1][a] = vu.y;
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        T B[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[h][a];
+                        T phz[3] = {T(0), T(0), T(0)};
+                        flux_acc(uq[h], B, 2, d == 5 ? -c.w1 * c.kappa : c.w1 * c.kappa, phz);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) nv[k][h][a] += c.w1 * bq[h][a] + phz[a];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every read of the old plane is done
+#pragma unroll
+        for (int k = 0; k < NPAIR; ++k) {
+            const int p0 = 2 * (tid + k * kResidentThreads);
+            if (p0 < P) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    st2(sb + a * P + p0, nv[k][0][a], nv[k][1][a]);
+                    if (publish) stcg2(xout + a * P + p0, nv[k][0][a], nv[k][1][a]);
+                }
+            }
+        }
+        } else {
         // (1) in-plane part of the sweep from this CTA's own plane; it overlaps
         // the neighbours' publication of the previous sweep
         T nv[kResidentMaxNpt][3];
@@ -215,18 +373,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
                     const int q = qn[d];
-                    T uq[3], B[3], phi[3];
+                    T uq[3], B[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const T bq = sb[a * P + q];
                         uq[a] = su[a * P + q];
                         acc[a] += c.w1 * bq;
-                        B[a] = c.strict_qs ? be_c[a] : be_c[a] + bq;
+                        B[a] = be_c[a] + c.sq * bq;
                     }
-                    flux_pair(uq, B, d >> 1, phi);
-                    const T sgn = (d & 1) ? T(-1) : T(1);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) dif[a] += sgn * phi[a];
+                    flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), dif);
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a) nv[k][a] = acc[a] + c.w1 * c.kappa * dif[a];
@@ -261,25 +416,23 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                     for (int d = 4; d < 6; ++d) {
                         const int zn = d == 4 ? zm : zp;
                         const T* bez = d == 4 ? be_m : be_p;
-                        T uq[3], B[3], phi[3], bq[3];
+                        T uq[3], B[3], bq[3];
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             bq[a] = s == 0 ? b_in[a * n + (long long)zn * P + p]
                                            : ldcg(xin + (long long)zn * xplane + (long long)a * P + p);
                             uq[a] = UHALO ? suh[((d == 4 ? 0 : 3) + a) * P + p] : u[a * n + (long long)zn * P + p];
-                            B[a] = c.strict_qs ? bez[a] : bez[a] + bq[a];
+                            B[a] = bez[a] + c.sq * bq[a];
                         }
-                        flux_pair(uq, B, 2, phi);
-                        const T sk = d == 5 ? -c.w1 * c.kappa : c.w1 * c.kappa;
+                        T phz[3] = {T(0), T(0), T(0)};
+                        flux_acc(uq, B, 2, d == 5 ? -c.w1 * c.kappa : c.w1 * c.kappa, phz);
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) nv[k][a] += c.w1 * bq[a] + sk * phi[a];
+                        for (int a = 0; a < 3; ++a) nv[k][a] += c.w1 * bq[a] + phz[a];
                     }
                 }
             }
         }
         __syncthreads();  // every read of the old plane is done
-        const bool publish = DIM == 3 && s + 1 < nsweeps;
-        T* xout = xbuf + (long long)(s & 1) * nz * xplane + (long long)z * xplane;
 #pragma unroll
         for (int k = 0; k < kResidentMaxNpt; ++k) {
             const int p = tid + k * kResidentThreads;
@@ -292,6 +445,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                     if (publish) __stcg(xout + a * P + p, nv[k][a]);
                 }
             }
+        }
         }
         ib_local<T, kResidentThreads>(lib, sb, sb + P, sb + 2 * P, sdelta);
         __syncthreads();
