@@ -133,19 +133,25 @@ def replica_throughput(world: int, nodes_per_rank: int, steps: int, slowest_ms: 
     return world * nodes_per_rank * steps / (slowest_ms / 1e3) / 1e6
 
 
+KERNEL_SOURCES = ("qslbm_kernels.cuh", "qslbm_resident.cuh", "qslbm_launch.cuh")
+
+
 def kernel_source_sha() -> str:
+    """Hash of the sources that define the timed kernels and their launches."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2211_09370_gb300", "csrc", "qslbm_kernels.cuh"), "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2211_09370_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the roofline kernel from the committed ncu
+    summary (profiles/traffic.json), or None when the kernel sources changed
+    since that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            d = json.load(f)
+            d = json.load(f)[workload]
         if d.get("kernel_source_sha") != kernel_source_sha():
             return None
         return float(d["dram_bytes_per_launch"])
@@ -419,7 +425,8 @@ def main():
         launches_per_step = 2 + 1
         per_launch_units = n_mag  # one launch runs every sweep of the step
     elif solver.units["sweep_kernel"] == "split":
-        kernel_name = "k_sweep_march<float> + k_ib_planes<float> (one sweep: z-marching stencil, then IB on b)"
+        kernel_name = ("k_sweep_march<float> + k_ib_planes<float> (one sweep: z-marching stencil, then the IB "
+                       "corrector on b, one CTA per plane)")
         launches_per_step = 2 * n_mag + 2
         per_launch_units = 1
     else:
@@ -438,7 +445,7 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                    "l2": "flushed before every timed step (256 MB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
                      "kernel": kernel_name,
                      "bytes_per_launch": alg_bytes, "ms_per_launch": launch_ms,
                      "sweeps_per_launch": per_launch_units, "us_per_sweep": sweep_ms * 1e3,

@@ -228,6 +228,20 @@ int qslbm_destroy(qslbm_handle* h);
 int qslbm_observables_static(const qslbm_handle* h, const void* drho, const void* u, const void* b,
                              const void* u_prev, double fb, int64_t steps_since_prev, double* out, void* stream);
 
+/* Self-check of the bounded wait (test support; the paper has no counterpart).
+ * The resident sweep kernel waits on its neighbour planes' counters with a
+ * routine that gives up after a limit instead of spinning for ever (the
+ * kernel then flags QSLBM_ETIMEOUT).  This call runs that routine in one warp
+ * on a counter in device memory: counter_set = 0 leaves the counter at 0, so
+ * the wait can never be satisfied and must give up after limit_s seconds;
+ * counter_set = 1 satisfies it at once.
+ *   limit_s    the wait's limit, 0 < limit_s <= 2 seconds
+ *   gave_up    out: 1 if the wait gave up, 0 if it was satisfied
+ *   waited_s   out: time spent in the wait, by the GPU's global timer
+ * Synchronous (default stream); allocates and frees 16 bytes of device memory.
+ * Errors: QSLBM_EINVAL (NULL output, limit out of range), QSLBM_ECUDA. */
+int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_up, double* waited_s);
+
 /* ------------------------------------------------------------------ batches
  * Many independent instances (3-D, one precision) advanced together: every
  * phase of a flow step is one fused launch over all instances' work (the

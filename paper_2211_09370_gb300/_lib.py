@@ -80,6 +80,7 @@ class qslbm_server_stats_t(C.Structure):
 EXPORTS = ("qslbm_params_init", "qslbm_create", "qslbm_get_units", "qslbm_step", "qslbm_mag_sweeps",
            "qslbm_observables", "qslbm_get_state", "qslbm_set_state", "qslbm_step_host", "qslbm_sync",
            "qslbm_destroy", "qslbm_strerror", "qslbm_last_error", "qslbm_observables_static",
+           "qslbm_check_bounded_wait",
            "qslbm_batch_create", "qslbm_batch_step", "qslbm_batch_handle", "qslbm_batch_info",
            "qslbm_batch_destroy", "qslbm_server_create", "qslbm_server_submit", "qslbm_server_run",
            "qslbm_server_poll", "qslbm_server_fields", "qslbm_server_release", "qslbm_server_stats",
@@ -114,6 +115,8 @@ def load(path: str | None = None):
     L.qslbm_observables_static.argtypes = [hp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                            C.c_int64, C.c_void_p, C.c_void_p]
     L.qslbm_observables_static.restype = C.c_int
+    L.qslbm_check_bounded_wait.argtypes = [C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    L.qslbm_check_bounded_wait.restype = C.c_int
     L.qslbm_batch_create.argtypes = [C.POINTER(qslbm_params), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
     L.qslbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
     L.qslbm_batch_handle.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]

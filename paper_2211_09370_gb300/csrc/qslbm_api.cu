@@ -264,6 +264,34 @@ int build_markers(State& s) {
     return QSLBM_OK;
 }
 
+// True when every z plane's ring and shell tables (in-plane indices, weights,
+// scalings, CSR) equal plane 0's, as for a straight pipe with a ring on every
+// plane; per-plane IB kernels then read one plane's tables for all planes.
+bool ib_tables_z_invariant(const State& s, const std::vector<int>& q9, const std::vector<double>& w9) {
+    const qslbm::HostIB& h = s.hib;
+    if (s.nz <= 1) return true;
+    const int R = h.ring_off[1] - h.ring_off[0];
+    const int S = h.shell_off[1] - h.shell_off[0];
+    for (int z = 1; z < s.nz; ++z) {
+        const int m0 = h.ring_off[z], s0 = h.shell_off[z];
+        if (h.ring_off[z + 1] - m0 != R || h.shell_off[z + 1] - s0 != S) return false;
+        for (int j = 0; j < R; ++j) {
+            if (h.s[m0 + j] != h.s[j] || h.sm[m0 + j] != h.sm[j]) return false;
+            for (int k = 0; k < 9; ++k)
+                if (q9[9 * (m0 + j) + k] != q9[9 * j + k] || w9[9 * (m0 + j) + k] != w9[9 * j + k]) return false;
+        }
+        for (int i = 0; i < S; ++i) {
+            if (h.shell_xy[s0 + i] != h.shell_xy[i]) return false;
+            const int e0 = h.csr_off[s0 + i], e1 = h.csr_off[s0 + i + 1];
+            if (e1 - e0 != h.csr_off[i + 1] - h.csr_off[i]) return false;
+            for (int e = 0; e < e1 - e0; ++e)
+                if (h.csr_m[e0 + e] != h.csr_m[h.csr_off[i] + e] || h.csr_w[e0 + e] != h.csr_w[h.csr_off[i] + e])
+                    return false;
+        }
+    }
+    return true;
+}
+
 int upload_ib(State& s) {
     qslbm::HostIB& h = s.hib;
     qslbm::DeviceIB& d = s.ib;
@@ -278,6 +306,23 @@ int upload_ib(State& s) {
                 q9[9 * j + 3 * b + a] = h.iy[3 * j + b] * s.nx + h.ix[3 * j + a];
                 w9[9 * j + 3 * b + a] = h.wx[3 * j + a] * h.wy[3 * j + b];
             }
+    {
+        // position of each support node in its plane's shell list (sorted by
+        // in-plane index); zero-weight support nodes point at entry 0
+        std::vector<int> slot(9 * nm, 0);
+        for (int z = 0; z < s.nz; ++z) {
+            const int* sb = h.shell_xy.data() + h.shell_off[z];
+            const int S = h.shell_off[z + 1] - h.shell_off[z];
+            for (int j = h.ring_off[z]; j < h.ring_off[z + 1]; ++j)
+                for (int k = 0; k < 9; ++k) {
+                    if (w9[9 * j + k] == 0.0) continue;
+                    const int* it = std::lower_bound(sb, sb + S, q9[9 * j + k]);
+                    if (it == sb + S || *it != q9[9 * j + k]) return QSLBM_EINVAL;  // not reachable
+                    slot[9 * j + k] = (int)(it - sb);
+                }
+        }
+        if ((rc = upload(s, (void**)&d.mk_slot, slot))) return rc;
+    }
     if ((rc = upload(s, (void**)&d.ring_off, h.ring_off))) return rc;
     if ((rc = upload(s, (void**)&d.mk_q, q9))) return rc;
     if ((rc = upload_real(s, &d.mk_w, w9))) return rc;
@@ -308,6 +353,7 @@ int upload_ib(State& s) {
     d.max_ring = h.max_ring;
     d.max_shell = h.max_shell;
     d.max_nnz = h.max_nnz;
+    d.zinv = ib_tables_z_invariant(s, q9, w9) ? 1 : 0;
     return QSLBM_OK;
 }
 

@@ -7,9 +7,9 @@
 // kernel is persistent (grid-stride over the work list) with its block size
 // and grid chosen by a timing autotuner when the batch is built.
 //
-// The per-node arithmetic is the single-instance code (sweep_node, ib_plane,
-// force_node, flow_node), so a batched instance follows the same expressions as
-// one stepped alone with the split sweep kernel.
+// The per-node arithmetic is the single-instance code (march_tile, the IB sums
+// of ib_plane, force_node, flow_node), so a batched instance follows the same
+// expressions as one stepped alone with the split sweep kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,7 +64,7 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, i
 template <typename T>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
                                                                     const int* __restrict__ first, int kact, int s) {
-    __shared__ T tile[6][kMarchTY + 2][kMarchTX + 2];
+    __shared__ MarchTile<T> tile;
     const int total = first[kact];
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int i = find_inst(first, kact, w);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_batch_ib(const InstDesc<T>* __
     const int z = blockIdx.x - pfirst[i];
     T* f = D.b[((D.bpar + s) & 1) ^ 1];
     const long long n = D.g.n;
-    ib_plane<T>(D.ibm, f, f + n, f + 2 * n, (long long)z * D.g.nx * D.g.ny, z, sdelta);
+    ib_plane<T>(D.ibm, f, f + n, f + 2 * n, (long long)z * D.g.nx * D.g.ny, D.ibm.zinv ? 0 : z, sdelta);
 }
 
 template <typename T>
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_batch_flow(InstDesc<T>* __res
         const int x = p - y * nx;
         flow_node<T, 3>(dr, u, D.F, dro, uo, n, nx, ny, nz, x, y, z, base + p, D.flc);
     }
-    ib_plane<T>(D.ibu, uo, uo + n, uo + 2 * n, base, z, sdelta);
+    ib_plane<T>(D.ibu, uo, uo + n, uo + 2 * n, base, D.ibu.zinv ? 0 : z, sdelta);
     if (z == 0 && threadIdx.x == 0) *D.tdev += 1;
 }
 
@@ -256,6 +256,8 @@ qslbm::InstDesc<T> make_desc(const State& s) {
         v.delta = (T*)s.ib.delta;
         v.nm = s.ib.nm;
         v.ns = s.ib.ns;
+        v.zinv = s.ib.zinv;
+        v.mk_slot = s.ib.mk_slot;
     }
     return D;
 }

@@ -23,6 +23,8 @@ struct DeviceIB {
     int *mk_base = nullptr, *shell_node = nullptr, *csr_mg = nullptr;
     void *delta = nullptr;  // [3 nm] markers' corrections (two-phase corrector)
     int nm = 0, ns = 0, nnz = 0, max_ring = 0, max_shell = 0, max_nnz = 0;
+    int zinv = 0;  // 1: every z plane carries plane 0's ring and shell tables
+    int* mk_slot = nullptr;  // [9 nm] shell-list position of each support node
 };
 
 // Host copy of the marker geometry and IB weights (binary64).
@@ -68,6 +70,7 @@ struct State {
     bool resident = false;
     bool launch_error = false;  // a cudaLaunchKernelEx call failed
     int march_chunk = 16;       // z planes per CTA of the marching sweep (one wave)
+    size_t ib_staged_smem = 0;  // shared memory of k_ib_staged, 0 when it does not fit
     bool resident_uhalo = false;
     size_t resident_smem = 0;
     void* xbuf = nullptr;   // [2][nz][3][P] plane exchange
@@ -88,7 +91,7 @@ struct Ops {
     // decide whether the resident sweep kernel fits this domain; sets
     // s.resident, s.resident_uhalo, s.resident_smem (no allocation)
     cudaError_t (*plan_resident)(State&);
-    cudaError_t (*plan_march)(State&);  // sets s.march_chunk
+    cudaError_t (*plan_march)(State&);  // sets s.march_chunk and s.ib_staged_smem
 };
 
 const Ops& ops_f32();

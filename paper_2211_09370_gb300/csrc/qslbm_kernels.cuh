@@ -51,7 +51,10 @@ struct IBView {
     const int* shell_node; // [ns]: node index of each shell node
     const int* csr_mg;     // [nnz]: marker index in the whole domain
     T* delta;              // [3 * nm]: delta_j of the two-phase corrector
+    const int* mk_slot;    // [9 * nm]: position of each support node in its plane's shell list
+                           //           (0 where the weight is zero)
     int nm, ns;
+    int zinv;              // 1: every plane has plane 0's ring and shell tables (straight pipe)
 };
 
 // Coefficients of the tau_m = 1 magnetic sweep (Sec. V.G).
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_sweep_ib(Geo g, const T* __re
         bout[base + p + n] = o[1];
         bout[base + p + 2 * n] = o[2];
     }
-    ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, z, sdelta);
+    ib_plane<T>(ib, bout, bout + n, bout + 2 * n, base, ib.zinv ? 0 : z, sdelta);
 }
 
 // Node-parallel sweep without the IB (grid: in-plane blocks x z planes); the
@@ -261,16 +264,73 @@ __global__ void __launch_bounds__(kNodeThreads) k_sweep_nodes(Geo g, const T* __
 
 // z-marching sweep without the IB (3-D): a CTA owns an (x, y) tile of
 // kMarchTX x kMarchTY columns and walks a chunk of z planes.  Each thread keeps
-// b and u of its column at z - 1, z, z + 1 in registers, so a node costs one
-// new load of (b, u) from HBM plus the tile's halo; the in-plane neighbours come
-// from the tile of plane z staged in shared memory.  Same expressions and
-// neighbour order as sweep_node.
+// its column's values at z - 1, z, z + 1 in registers, so a node costs one new
+// load of (b, u) from HBM plus the tile's halo; the in-plane neighbours come
+// from the tile of plane z staged in shared memory.
 constexpr int kMarchTX = 32, kMarchTY = 8, kMarchChunk = 16;
 
+// Halo cell of a march tile handled by thread hid: the ring of
+// (kMarchTX + 2) x (kMarchTY + 2) tile cells around the interior.  hp is the
+// in-plane index of the node it stages (periodic image), -1 for no cell.
+__device__ __forceinline__ void march_halo(int hid, int x0, int y0, int nx, int ny, int& hx, int& hy, int& hp) {
+    constexpr int W = kMarchTX + 2, H = kMarchTY + 2, NH = 2 * W + 2 * kMarchTY;
+    hx = 0;
+    hy = 0;
+    hp = -1;
+    if (hid >= NH) return;
+    if (hid < W) {
+        hx = hid;
+        hy = 0;
+    } else if (hid < 2 * W) {
+        hx = hid - W;
+        hy = H - 1;
+    } else {
+        const int r = hid - 2 * W;
+        hx = (r & 1) ? W - 1 : 0;
+        hy = 1 + (r >> 1);
+    }
+    const int gx = (x0 + hx - 1 + nx) % nx, gy = (y0 + hy - 1 + ny) % ny;
+    hp = gy * nx + gx;
+}
+
+// The flux Phi_{ab} = u_b B_a - u_a B_b is antisymmetric, so a node carries
+// three numbers of it: e1 = Phi_yx, e2 = Phi_zx, e3 = Phi_zy (B = B^ext + sq b).
+// Written over them, the neighbour sum of the sweep is
+//   b_a <- w0 b_a + w1 (sum_{6 nbrs} b_a + kappa D_a),
+//   D_x = e1(+y) - e1(-y) + e2(+z) - e2(-z),
+//   D_y = e1(-x) - e1(+x) + e3(+z) - e3(-z),
+//   D_z = e2(-x) - e2(+x) + e3(-y) - e3(+y),
+// where D_a = sum_b [Phi_ab(x - e_b) - Phi_ab(x + e_b)] as in sweep_node.
+// node_emf turns a node's (b, u) into (b, e) in place.
+template <typename T>
+__device__ __forceinline__ void node_emf(T r[6], const T be[3], T sq) {
+    const T B0 = be[0] + sq * r[0], B1 = be[1] + sq * r[1], B2 = be[2] + sq * r[2];
+    const T u0 = r[3], u1 = r[4], u2 = r[5];
+    r[3] = u0 * B1 - u1 * B0;
+    r[4] = u0 * B2 - u2 * B0;
+    r[5] = u1 * B2 - u2 * B1;
+}
+
+// Shared tile of one march plane: six fields of (kMarchTY + 2) x (kMarchTX + 2)
+// cells, double-buffered so that staging plane z + 1 needs no barrier against
+// the reads of plane z.
+template <typename T>
+using MarchTile = T[2][6][kMarchTY + 2][kMarchTX + 2];
+
+// The sweep over one tile and z chunk.  FP32 (EMF form): each node's
+// (e1, e2, e3) is formed once, where its (b, u) is loaded, and the tile and the
+// column registers hold (b, e); about half the arithmetic and shared-memory
+// traffic of forming the flux per neighbour, the same sweep up to the order of
+// rounding.  FP64 (direct form): the tile holds (b, u) and every neighbour's
+// flux is formed as in sweep_node, with the same expressions and neighbour
+// order, so that it rounds like the other FP64 sweep kernels.
+// Every global load of plane z + 2 (interior) and z + 1 (halo) is issued one
+// plane ahead of its use, and one barrier per plane orders the tile buffers.
 template <typename T>
 __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
                                            const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
-                                           int chunk, T (*tile)[kMarchTY + 2][kMarchTX + 2]) {
+                                           int chunk, MarchTile<T>& tile) {
+    constexpr bool EMF = sizeof(T) == 4;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int n = (int)g.n, P = nx * ny;
     const int tx = threadIdx.x % kMarchTX, ty = threadIdx.x / kMarchTX;
@@ -283,28 +343,11 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     const int z0 = bz * chunk;
     const int z1 = min(z0 + chunk, nz);
     const T* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
-    // halo cells of the tile: ring of (kMarchTX + 2) x (kMarchTY + 2) minus the interior
-    constexpr int W = kMarchTX + 2, H = kMarchTY + 2, NH = 2 * W + 2 * kMarchTY;
-    int hx = 0, hy = 0;
-    const int hid = threadIdx.x;
-    if (hid < NH) {
-        if (hid < W) {
-            hx = hid;
-            hy = 0;
-        } else if (hid < 2 * W) {
-            hx = hid - W;
-            hy = H - 1;
-        } else {
-            const int r = hid - 2 * W;
-            hx = (r & 1) ? W - 1 : 0;
-            hy = 1 + (r >> 1);
-        }
-    }
-    const int gx = (x0 + hx - 1 + nx) % nx, gy = (y0 + hy - 1 + ny) % ny;
-    const int hp = hid < NH ? gy * nx + gx : -1;
-    // prv / cur / nxt hold planes z - 1, z, z + 1; ahd is loaded one plane
-    // ahead (z + 2) so that its memory latency overlaps the work on plane z
-    T prv[6], cur[6], nxt[6], ahd[6];
+    int hx, hy, hp;
+    march_halo(threadIdx.x, x0, y0, nx, ny, hx, hy, hp);
+    // prv / cur / nxt: the column at z - 1, z, z + 1 ((b, e) or (b, u));
+    // ahd: raw (b, u) of plane z + 2.  hcur / hnxt: raw halo cell of z, z + 1.
+    T prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
     {
         const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
 #pragma unroll
@@ -312,75 +355,121 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             prv[v] = src[v][zm * P + p];
             cur[v] = src[v][z0 * P + p];
             nxt[v] = src[v][zn * P + p];
+            hcur[v] = hp >= 0 ? src[v][z0 * P + hp] : T(0);
+        }
+        if constexpr (EMF) {
+            T be[3];
+            bext_at(c.bext_z, c.be, zm, be);
+            node_emf(prv, be, c.sq);
+            bext_at(c.bext_z, c.be, z0, be);
+            node_emf(cur, be, c.sq);
+            bext_at(c.bext_z, c.be, zn, be);
+            node_emf(nxt, be, c.sq);
         }
     }
+    const T w1k = c.w1 * c.kappa;
     for (int z = z0; z < z1; ++z) {
         const int zn = wrap_inc(z, nz);
+        const int za = wrap_inc(zn, nz);
+        const int buf = z & 1;
         if (z + 1 < z1) {
-            const int za = wrap_inc(zn, nz);
 #pragma unroll
-            for (int v = 0; v < 6; ++v) ahd[v] = src[v][za * P + p];
-        }
-        // stage plane z (interior from registers, halo from global)
-#pragma unroll
-        for (int v = 0; v < 6; ++v) tile[v][ty + 1][tx + 1] = cur[v];
-        if (hp >= 0) {
-#pragma unroll
-            for (int v = 0; v < 6; ++v) tile[v][hy][hx] = src[v][z * P + hp];
-        }
-        __syncthreads();
-        if (active) {
-            T be_c[3], be_m[3], be_p[3];
-            bext_at(c.bext_z, c.be, z, be_c);
-            bext_at(c.bext_z, c.be, wrap_dec(z, nz), be_m);
-            bext_at(c.bext_z, c.be, zn, be_p);
-            T acc[3] = {c.w0 * cur[0], c.w0 * cur[1], c.w0 * cur[2]};
-            T diff[3] = {T(0), T(0), T(0)};
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                T bq[3], uq[3];
-                if (d < 4) {
-                    const int ix = tx + 1 + (d == 0 ? -1 : d == 1 ? 1 : 0);
-                    const int iy = ty + 1 + (d == 2 ? -1 : d == 3 ? 1 : 0);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        bq[a] = tile[a][iy][ix];
-                        uq[a] = tile[3 + a][iy][ix];
-                    }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        bq[a] = d == 4 ? prv[a] : nxt[a];
-                        uq[a] = d == 4 ? prv[3 + a] : nxt[3 + a];
-                    }
-                }
-                const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
-                T B[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
-                flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
+            for (int v = 0; v < 6; ++v) {
+                ahd[v] = src[v][za * P + p];
+                if (hp >= 0) hnxt[v] = src[v][zn * P + hp];
             }
-            const int k = z * P + p;
+        }
+        // stage plane z: interior from the column registers, halo cell from
+        // the values loaded one plane earlier
 #pragma unroll
-            for (int a = 0; a < 3; ++a) bout[k + a * n] = acc[a] + c.w1 * c.kappa * diff[a];
+        for (int v = 0; v < 6; ++v) tile[buf][v][ty + 1][tx + 1] = cur[v];
+        if (hp >= 0) {
+            if constexpr (EMF) {
+                T be[3];
+                bext_at(c.bext_z, c.be, z, be);
+                node_emf(hcur, be, c.sq);
+            }
+#pragma unroll
+            for (int v = 0; v < 6; ++v) tile[buf][v][hy][hx] = hcur[v];
         }
         __syncthreads();
+        const auto& t = tile[buf];
+        if (active) {
+            const int cx = tx + 1, cy = ty + 1;
+            const int k = z * P + p;
+            if constexpr (EMF) {
+                T s[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    s[a] = (t[a][cy][cx - 1] + t[a][cy][cx + 1]) + (t[a][cy - 1][cx] + t[a][cy + 1][cx]) +
+                           (prv[a] + nxt[a]);
+                const T dx = (t[3][cy + 1][cx] - t[3][cy - 1][cx]) + (nxt[4] - prv[4]);
+                const T dy = (t[3][cy][cx - 1] - t[3][cy][cx + 1]) + (nxt[5] - prv[5]);
+                const T dz = (t[4][cy][cx - 1] - t[4][cy][cx + 1]) + (t[5][cy - 1][cx] - t[5][cy + 1][cx]);
+                bout[k] = c.w0 * cur[0] + (c.w1 * s[0] + w1k * dx);
+                bout[k + n] = c.w0 * cur[1] + (c.w1 * s[1] + w1k * dy);
+                bout[k + 2 * n] = c.w0 * cur[2] + (c.w1 * s[2] + w1k * dz);
+            } else {
+                T be_c[3], be_m[3], be_p[3];
+                bext_at(c.bext_z, c.be, z, be_c);
+                bext_at(c.bext_z, c.be, wrap_dec(z, nz), be_m);
+                bext_at(c.bext_z, c.be, zn, be_p);
+                T acc[3] = {c.w0 * cur[0], c.w0 * cur[1], c.w0 * cur[2]};
+                T diff[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    T bq[3], uq[3];
+                    if (d < 4) {
+                        const int ix = cx + (d == 0 ? -1 : d == 1 ? 1 : 0);
+                        const int iy = cy + (d == 2 ? -1 : d == 3 ? 1 : 0);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            bq[a] = t[a][iy][ix];
+                            uq[a] = t[3 + a][iy][ix];
+                        }
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            bq[a] = d == 4 ? prv[a] : nxt[a];
+                            uq[a] = d == 4 ? prv[3 + a] : nxt[3 + a];
+                        }
+                    }
+                    const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
+                    T B[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
+                    flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) bout[k + a * n] = acc[a] + c.w1 * c.kappa * diff[a];
+            }
+        }
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
             prv[v] = cur[v];
             cur[v] = nxt[v];
-            nxt[v] = ahd[v];
+            hcur[v] = hnxt[v];
+        }
+        if (z + 1 < z1) {
+            if constexpr (EMF) {
+                T be[3];
+                bext_at(c.bext_z, c.be, za, be);
+                node_emf(ahd, be, c.sq);
+            }
+#pragma unroll
+            for (int v = 0; v < 6; ++v) nxt[v] = ahd[v];
         }
     }
+    __syncthreads();  // the tile buffers are free for the caller's next chunk
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_sweep_march(Geo g, const T* __restrict__ bin,
                                                                     T* __restrict__ bout, const T* __restrict__ u,
                                                                     SweepCoef<T> c, int chunk) {
-    __shared__ T tile[6][kMarchTY + 2][kMarchTX + 2];  // b0 b1 b2 u0 u1 u2 of plane z with halo
+    __shared__ MarchTile<T> tile;
     march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, chunk, tile);
 }
 
@@ -435,14 +524,76 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_shell(Geo g, T* __restrict_
     if (i < ib.ns) ib_shell<T>(ib, f, (int)g.n, i);
 }
 
-// IB corrector alone, one CTA per z plane (after k_sweep_nodes).
+// IB corrector alone, one CTA per z plane, after a sweep kernel without the
+// IB (k_sweep_march, k_sweep_nodes).  With z-invariant tables (a straight
+// pipe) every CTA reads plane 0's tables, which then stay in cache.
 template <typename T>
 __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<T> ib) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sdelta = reinterpret_cast<T*>(smem_raw);
     const long long n = g.n;
     const long long base = (long long)blockIdx.x * g.nx * g.ny;
-    ib_plane<T>(ib, f, f + n, f + 2 * n, base, blockIdx.x, sdelta);
+    ib_plane<T>(ib, f, f + n, f + 2 * n, base, ib.zinv ? 0 : (int)blockIdx.x, sdelta);
+}
+
+// The same corrector with the plane's shell nodes staged in shared memory:
+// their values are read from memory once (independent loads), the markers
+// interpolate from the staged copy through mk_slot, and every shell node is
+// written once.  Same sums in the same order as ib_plane.  Shared memory:
+// 3 max_ring deltas, then 3 max_shell staged values.
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    T* sf = sdelta + 3 * max_ring;
+    const int z = blockIdx.x, tz = ib.zinv ? 0 : z;
+    const int m0 = ib.ring_off[tz], R = ib.ring_off[tz + 1] - m0;
+    if (R == 0) return;
+    const int s0 = ib.shell_off[tz], S = ib.shell_off[tz + 1] - s0;
+    const int n = (int)g.n;
+    const int base = z * g.nx * g.ny;
+    T* f0 = f + base;
+    T* f1 = f0 + n;
+    T* f2 = f1 + n;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < S; i += kNodeThreads) {
+        const int q = ib.shell_xy[s0 + i];
+        sf[i] = f0[q];
+        sf[S + i] = f1[q];
+        sf[2 * S + i] = f2[q];
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < R; m += kNodeThreads) {
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const T w = ib.mk_w[9 * (m0 + m) + j];
+            const int q = ib.mk_slot[9 * (m0 + m) + j];
+            a0 += w * sf[q];
+            a1 += w * sf[S + q];
+            a2 += w * sf[2 * S + q];
+        }
+        const T s = ib.mk_s[m0 + m];
+        sdelta[3 * m + 0] = -s * a0;
+        sdelta[3 * m + 1] = -s * a1;
+        sdelta[3 * m + 2] = -s * a2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < S; i += kNodeThreads) {
+        T c0 = T(0), c1 = T(0), c2 = T(0);
+        const int e0 = ib.csr_off[s0 + i], e1 = ib.csr_off[s0 + i + 1];
+        for (int e = e0; e < e1; ++e) {
+            const T w = ib.csr_w[e];
+            const int l = ib.csr_m[e];
+            c0 += w * sdelta[3 * l + 0];
+            c1 += w * sdelta[3 * l + 1];
+            c2 += w * sdelta[3 * l + 2];
+        }
+        const int q = ib.shell_xy[s0 + i];
+        f0[q] = sf[i] + c0;
+        f1[q] = sf[S + i] + c1;
+        f2[q] = sf[2 * S + i] + c2;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +792,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __res
         const int x = p - y * nx;
         flow_node<T, DIM>(drho, u, F, drho_out, uout, n, nx, ny, nz, x, y, z, base + p, c);
     }
-    ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, z, sdelta);
+    ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, ib.zinv ? 0 : z, sdelta);
     if (blockIdx.x == 0 && threadIdx.x == 0) *tstep += 1;
 }
 

@@ -31,6 +31,8 @@ struct Launch {
         v.delta = static_cast<T*>(s.ib.delta);
         v.nm = s.ib.nm;
         v.ns = s.ib.ns;
+        v.zinv = s.ib.zinv;
+        v.mk_slot = s.ib.mk_slot;
         return v;
     }
 
@@ -81,7 +83,9 @@ struct Launch {
                     k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
-                if (s.ib.nm > 0) {
+                if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
+                    k_ib_staged<T><<<s.nz, kNodeThreads, s.ib_staged_smem, st>>>(geo(s), bout, v, s.ib.max_ring);
+                } else if (s.ib.nm > 0) {
                     k_ib_markers<T><<<(s.ib.nm + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
                     k_ib_shell<T><<<(s.ib.ns + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
                 }
@@ -197,6 +201,19 @@ struct Launch {
         long long chunk = (s.nz + per_column - 1) / per_column;
         chunk = std::max<long long>(chunk, 4);  // keep the z halo overhead small
         s.march_chunk = (int)std::min<long long>(chunk, s.nz);
+        // the staged IB corrector, when the plane's shell fits shared memory
+        s.ib_staged_smem = 0;
+        if (s.ib.nm > 0) {
+            const size_t smem = (size_t)3 * (s.ib.max_ring + s.ib.max_shell) * sizeof(T);
+            int max_optin = 0;
+            e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (e != cudaSuccess) return e;
+            if (smem <= (size_t)max_optin) {
+                e = cudaFuncSetAttribute(k_ib_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                s.ib_staged_smem = smem;
+            }
+        }
         return cudaSuccess;
     }
 

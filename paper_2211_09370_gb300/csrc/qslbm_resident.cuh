@@ -52,6 +52,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// Wait (one thread) until the counters *fa and *fb reach target, comparing
+// modulo 2^32.  Gives up after timeout_ns of the GPU's global timer and
+// returns false, so that no wait outlasts its limit.
+__device__ __forceinline__ bool wait_counters(const unsigned int* fa, const unsigned int* fb, unsigned int target,
+                                              unsigned long long timeout_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    while ((int)(ld_acquire_u32(fa) - target) < 0 || (int)(ld_acquire_u32(fb) - target) < 0) {
+        if (globaltimer_ns() - t0 > timeout_ns) return false;
+        __nanosleep(16);
+    }
+    return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {
     return __ldcg(p);
@@ -198,10 +211,11 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     }
     LocalIB<T> lib;
     {
-        const int m0 = ib.ring_off[z];
-        lib.R = ib.ring_off[z + 1] - m0;
-        const int s0 = ib.shell_off[z];
-        lib.S = ib.shell_off[z + 1] - s0;
+        const int tz = ib.zinv ? 0 : z;
+        const int m0 = ib.ring_off[tz];
+        lib.R = ib.ring_off[tz + 1] - m0;
+        const int s0 = ib.shell_off[tz];
+        lib.S = ib.shell_off[tz + 1] - s0;
         const int e0 = lib.S > 0 ? ib.csr_off[s0] : 0;
         const int E = lib.S > 0 ? ib.csr_off[s0 + lib.S] - e0 : 0;
         for (int i = tid; i < 9 * lib.R; i += kResidentThreads) {
@@ -289,18 +303,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         }
         // (2) neighbour planes of the previous sweep
         if (DIM == 3 && s > 0) {
-            if (tid == 0) {
-                const unsigned int target = epoch + (unsigned int)s;
-                const unsigned long long t0 = globaltimer_ns();
-                while ((int)(ld_acquire_u32(&sync->flags[zm]) - target) < 0 ||
-                       (int)(ld_acquire_u32(&sync->flags[zp]) - target) < 0) {
-                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
-                        atomicExch(&sync->err, 1);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(16);
-                }
+            if (tid == 0 &&
+                !wait_counters(&sync->flags[zm], &sync->flags[zp], epoch + (unsigned int)s, kWaitTimeoutNs)) {
+                atomicExch(&sync->err, 1);
+                s_abort = 1;
             }
             __syncthreads();
             if (s_abort) return;
@@ -389,18 +395,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         }
         // (2) neighbour planes of the previous sweep
         if (DIM == 3 && s > 0) {
-            if (tid == 0) {
-                const unsigned int target = epoch + (unsigned int)s;
-                const unsigned long long t0 = globaltimer_ns();
-                while ((int)(ld_acquire_u32(&sync->flags[zm]) - target) < 0 ||
-                       (int)(ld_acquire_u32(&sync->flags[zp]) - target) < 0) {
-                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
-                        atomicExch(&sync->err, 1);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(16);
-                }
+            if (tid == 0 &&
+                !wait_counters(&sync->flags[zm], &sync->flags[zp], epoch + (unsigned int)s, kWaitTimeoutNs)) {
+                atomicExch(&sync->err, 1);
+                s_abort = 1;
             }
             __syncthreads();
             if (s_abort) return;

@@ -59,3 +59,11 @@ def test_null_arguments():
     assert L.qslbm_observables(None, None, None, None, None) == _lib.EINVAL
     assert L.qslbm_destroy(None) == _lib.EINVAL
     assert L.qslbm_strerror(_lib.EBUDGET).decode().startswith("request exceeds")
+
+
+def test_bounded_wait_check_rejects_bad_limits_before_the_device():
+    L = _lib.load()
+    g, w = C.c_int32(), C.c_double()
+    assert L.qslbm_check_bounded_wait(0.0, 0, C.byref(g), C.byref(w)) == _lib.EINVAL
+    assert L.qslbm_check_bounded_wait(5.0, 0, C.byref(g), C.byref(w)) == _lib.EINVAL
+    assert L.qslbm_check_bounded_wait(0.1, 0, None, C.byref(w)) == _lib.EINVAL
