@@ -302,30 +302,36 @@ __device__ __forceinline__ void march_halo(int hid, int x0, int y0, int nx, int 
 //   D_z = e2(-x) - e2(+x) + e3(-y) - e3(+y),
 // where D_a = sum_b [Phi_ab(x - e_b) - Phi_ab(x + e_b)] as in sweep_node.
 // node_emf turns a node's (b, u) into (b, e) in place.
-template <typename T>
-__device__ __forceinline__ void node_emf(T r[6], const T be[3], T sq) {
-    const T B0 = be[0] + sq * r[0], B1 = be[1] + sq * r[1], B2 = be[2] + sq * r[2];
-    const T u0 = r[3], u1 = r[4], u2 = r[5];
-    r[3] = u0 * B1 - u1 * B0;
-    r[4] = u0 * B2 - u2 * B0;
-    r[5] = u1 * B2 - u2 * B1;
+// The EMF form is the FP32 path; its roundings are spelled out (fused
+// multiply-adds where written, nothing left to contraction) so that every
+// kernel using it (march_tile, the node-pair sweep, the batched sweep)
+// produces bitwise the same values.
+__device__ __forceinline__ void node_emf(float r[6], const float be[3], float sq) {
+    const float B0 = __fmaf_rn(sq, r[0], be[0]), B1 = __fmaf_rn(sq, r[1], be[1]), B2 = __fmaf_rn(sq, r[2], be[2]);
+    const float u0 = r[3], u1 = r[4], u2 = r[5];
+    r[3] = __fmaf_rn(u0, B1, -__fmul_rn(u1, B0));
+    r[4] = __fmaf_rn(u0, B2, -__fmul_rn(u2, B0));
+    r[5] = __fmaf_rn(u1, B2, -__fmul_rn(u2, B1));
+}
+
+// New b of one node in the EMF form: w0 b + (w1 s + w1 kappa D).
+__device__ __forceinline__ float emf_update(float w0, float w1, float w1k, float b, float s, float d) {
+    return __fmaf_rn(w0, b, __fmaf_rn(w1k, d, __fmul_rn(w1, s)));
 }
 
 // Shared tile of one march plane: six fields of (kMarchTY + 2) x (kMarchTX + 2)
-// cells, double-buffered so that staging plane z + 1 needs no barrier against
-// the reads of plane z.
+// cells, the tile and its one-cell halo.
 template <typename T>
-using MarchTile = T[2][6][kMarchTY + 2][kMarchTX + 2];
+using MarchTile = T[6][kMarchTY + 2][kMarchTX + 2];
 
-// The sweep over one tile and z chunk.  FP32 (EMF form): each node's
-// (e1, e2, e3) is formed once, where its (b, u) is loaded, and the tile and the
-// column registers hold (b, e); about half the arithmetic and shared-memory
-// traffic of forming the flux per neighbour, the same sweep up to the order of
-// rounding.  FP64 (direct form): the tile holds (b, u) and every neighbour's
-// flux is formed as in sweep_node, with the same expressions and neighbour
-// order, so that it rounds like the other FP64 sweep kernels.
-// Every global load of plane z + 2 (interior) and z + 1 (halo) is issued one
-// plane ahead of its use, and one barrier per plane orders the tile buffers.
+// The sweep over one tile and z chunk, one node per thread.  FP32 (EMF form):
+// each node's (e1, e2, e3) is formed once, where its (b, u) is loaded, and the
+// tile and the column registers hold (b, e); about half the arithmetic and
+// shared-memory traffic of forming the flux per neighbour, the same sweep up
+// to the order of rounding.  FP64 (direct form): the tile holds (b, u) and
+// every neighbour's flux is formed as in sweep_node, with the same
+// expressions and neighbour order, so that it rounds like the other FP64 sweep
+// kernels.  The column's plane z + 2 is loaded one plane ahead of its use.
 template <typename T>
 __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
                                            const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
@@ -345,9 +351,9 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     const T* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
     int hx, hy, hp;
     march_halo(threadIdx.x, x0, y0, nx, ny, hx, hy, hp);
-    // prv / cur / nxt: the column at z - 1, z, z + 1 ((b, e) or (b, u));
-    // ahd: raw (b, u) of plane z + 2.  hcur / hnxt: raw halo cell of z, z + 1.
-    T prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
+    // prv / cur / nxt: the column at z - 1, z, z + 1 ((b, e) or (b, u)); ahd:
+    // raw (b, u) of plane z + 2
+    T prv[6], cur[6], nxt[6], ahd[6];
     {
         const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
 #pragma unroll
@@ -355,7 +361,6 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             prv[v] = src[v][zm * P + p];
             cur[v] = src[v][z0 * P + p];
             nxt[v] = src[v][zn * P + p];
-            hcur[v] = hp >= 0 ? src[v][z0 * P + hp] : T(0);
         }
         if constexpr (EMF) {
             T be[3];
@@ -371,29 +376,26 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     for (int z = z0; z < z1; ++z) {
         const int zn = wrap_inc(z, nz);
         const int za = wrap_inc(zn, nz);
-        const int buf = z & 1;
         if (z + 1 < z1) {
 #pragma unroll
-            for (int v = 0; v < 6; ++v) {
-                ahd[v] = src[v][za * P + p];
-                if (hp >= 0) hnxt[v] = src[v][zn * P + hp];
-            }
+            for (int v = 0; v < 6; ++v) ahd[v] = src[v][za * P + p];
         }
-        // stage plane z: interior from the column registers, halo cell from
-        // the values loaded one plane earlier
+        // stage plane z: interior from the column registers, halo from global
 #pragma unroll
-        for (int v = 0; v < 6; ++v) tile[buf][v][ty + 1][tx + 1] = cur[v];
+        for (int v = 0; v < 6; ++v) tile[v][ty + 1][tx + 1] = cur[v];
         if (hp >= 0) {
+            T r[6];
+#pragma unroll
+            for (int v = 0; v < 6; ++v) r[v] = src[v][z * P + hp];
             if constexpr (EMF) {
                 T be[3];
                 bext_at(c.bext_z, c.be, z, be);
-                node_emf(hcur, be, c.sq);
+                node_emf(r, be, c.sq);
             }
 #pragma unroll
-            for (int v = 0; v < 6; ++v) tile[buf][v][hy][hx] = hcur[v];
+            for (int v = 0; v < 6; ++v) tile[v][hy][hx] = r[v];
         }
         __syncthreads();
-        const auto& t = tile[buf];
         if (active) {
             const int cx = tx + 1, cy = ty + 1;
             const int k = z * P + p;
@@ -401,14 +403,15 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                 T s[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    s[a] = (t[a][cy][cx - 1] + t[a][cy][cx + 1]) + (t[a][cy - 1][cx] + t[a][cy + 1][cx]) +
+                    s[a] = (tile[a][cy][cx - 1] + tile[a][cy][cx + 1]) + (tile[a][cy - 1][cx] + tile[a][cy + 1][cx]) +
                            (prv[a] + nxt[a]);
-                const T dx = (t[3][cy + 1][cx] - t[3][cy - 1][cx]) + (nxt[4] - prv[4]);
-                const T dy = (t[3][cy][cx - 1] - t[3][cy][cx + 1]) + (nxt[5] - prv[5]);
-                const T dz = (t[4][cy][cx - 1] - t[4][cy][cx + 1]) + (t[5][cy - 1][cx] - t[5][cy + 1][cx]);
-                bout[k] = c.w0 * cur[0] + (c.w1 * s[0] + w1k * dx);
-                bout[k + n] = c.w0 * cur[1] + (c.w1 * s[1] + w1k * dy);
-                bout[k + 2 * n] = c.w0 * cur[2] + (c.w1 * s[2] + w1k * dz);
+                const T dx = (tile[3][cy + 1][cx] - tile[3][cy - 1][cx]) + (nxt[4] - prv[4]);
+                const T dy = (tile[3][cy][cx - 1] - tile[3][cy][cx + 1]) + (nxt[5] - prv[5]);
+                const T dz =
+                    (tile[4][cy][cx - 1] - tile[4][cy][cx + 1]) + (tile[5][cy - 1][cx] - tile[5][cy + 1][cx]);
+                bout[k] = emf_update(c.w0, c.w1, w1k, cur[0], s[0], dx);
+                bout[k + n] = emf_update(c.w0, c.w1, w1k, cur[1], s[1], dy);
+                bout[k + 2 * n] = emf_update(c.w0, c.w1, w1k, cur[2], s[2], dz);
             } else {
                 T be_c[3], be_m[3], be_p[3];
                 bext_at(c.bext_z, c.be, z, be_c);
@@ -424,8 +427,8 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                         const int iy = cy + (d == 2 ? -1 : d == 3 ? 1 : 0);
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            bq[a] = t[a][iy][ix];
-                            uq[a] = t[3 + a][iy][ix];
+                            bq[a] = tile[a][iy][ix];
+                            uq[a] = tile[3 + a][iy][ix];
                         }
                     } else {
 #pragma unroll
@@ -446,11 +449,11 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                 for (int a = 0; a < 3; ++a) bout[k + a * n] = acc[a] + c.w1 * c.kappa * diff[a];
             }
         }
+        __syncthreads();
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
             prv[v] = cur[v];
             cur[v] = nxt[v];
-            hcur[v] = hnxt[v];
         }
         if (z + 1 < z1) {
             if constexpr (EMF) {
@@ -462,7 +465,6 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             for (int v = 0; v < 6; ++v) nxt[v] = ahd[v];
         }
     }
-    __syncthreads();  // the tile buffers are free for the caller's next chunk
 }
 
 template <typename T>
@@ -471,6 +473,182 @@ __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_sweep_march(Geo g, const
                                                                     SweepCoef<T> c, int chunk) {
     __shared__ MarchTile<T> tile;
     march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, chunk, tile);
+}
+
+// FP32 z-marching sweep on x-adjacent node pairs (nx even): a CTA of 256
+// threads owns a tile of kPairTXP pairs (32 nodes) x kPairTY rows and walks a
+// chunk of z planes; every global access moves two nodes (8 bytes), so the
+// address arithmetic, loads, stores and loop overhead per node are half those
+// of march_tile.  EMF form as in march_tile.  The staged plane is
+// double-buffered (one barrier per plane) and every global load is issued one
+// plane ahead of its use: the column's plane z + 2, the halo's plane z + 1.
+constexpr int kPairTXP = 16, kPairTY = 16;
+constexpr int kPairThreads = kPairTXP * kPairTY;
+// tile row: pad, left halo, 32 nodes, right halo, pad (pairs start at even columns)
+constexpr int kPairW = 2 * kPairTXP + 4;
+using PairTile = float[2][6][kPairTY + 2][kPairW];
+
+// Halo item hid of a pair tile (64 items): 0-15 the pairs of the row above,
+// 16-31 the row below, 32-47 the column left of the tile, 48-63 the column
+// right of it (corners are not needed by the 5-point in-plane stencil).
+// kind: 0 none, 1 pair, 2 single node; gp: in-plane index (periodic image).
+__device__ __forceinline__ void pair_halo(int hid, int x0, int y0, int nx, int ny, int& kind, int& row, int& col,
+                                          int& gp) {
+    kind = 0;
+    row = 0;
+    col = 0;
+    gp = 0;
+    if (hid >= 64) return;
+    int gx, gy;
+    if (hid < 32) {
+        const int j = hid & 15;
+        kind = 1;
+        row = hid < 16 ? 0 : kPairTY + 1;
+        col = 2 + 2 * j;
+        gx = (x0 + 2 * j) % nx;
+        gy = hid < 16 ? (y0 - 1 + ny) % ny : (y0 + kPairTY) % ny;
+    } else {
+        const int i = hid & 15;
+        kind = 2;
+        row = 1 + i;
+        col = hid < 48 ? 1 : 2 * kPairTXP + 2;
+        gx = hid < 48 ? (x0 - 1 + nx) % nx : (x0 + 2 * kPairTXP) % nx;
+        gy = (y0 + i) % ny;
+    }
+    gp = gy * nx + gx;
+}
+
+__device__ __forceinline__ void pair_emf(float2 r[6], const float be[3], float sq) {
+    float a[6] = {r[0].x, r[1].x, r[2].x, r[3].x, r[4].x, r[5].x};
+    float b[6] = {r[0].y, r[1].y, r[2].y, r[3].y, r[4].y, r[5].y};
+    node_emf(a, be, sq);
+    node_emf(b, be, sq);
+#pragma unroll
+    for (int v = 0; v < 6; ++v) r[v] = make_float2(a[v], b[v]);
+}
+
+template <typename F>
+__global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const F* __restrict__ bin,
+                                                                   F* __restrict__ bout, const F* __restrict__ u,
+                                                                   SweepCoef<F> c, int chunk) {
+    static_assert(sizeof(F) == 4, "the pair sweep is the FP32 path");
+    __shared__ __align__(16) PairTile tile;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int n = (int)g.n, P = nx * ny;
+    const int tx = threadIdx.x % kPairTXP, ty = threadIdx.x / kPairTXP;
+    const int x0 = blockIdx.x * 2 * kPairTXP, y0 = blockIdx.y * kPairTY;
+    const int x = x0 + 2 * tx, y = y0 + ty;
+    const bool active = x < nx && y < ny;
+    const int p = (y % ny) * nx + (x % nx);  // even: a pair never straddles a row end
+    const int z0 = blockIdx.z * chunk;
+    const int z1 = min(z0 + chunk, nz);
+    const float* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
+    int hkind, hrow, hcol, hp;
+    pair_halo(threadIdx.x, x0, y0, nx, ny, hkind, hrow, hcol, hp);
+    auto ld2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
+    // halo values of plane zz (raw), pair or single node (in .x)
+    auto load_halo = [&](int zz, float2 h[6]) {
+        if (hkind == 1) {
+#pragma unroll
+            for (int v = 0; v < 6; ++v) h[v] = ld2(src[v] + zz * P + hp);
+        } else if (hkind == 2) {
+#pragma unroll
+            for (int v = 0; v < 6; ++v) h[v] = make_float2(src[v][zz * P + hp], 0.f);
+        }
+    };
+    float2 prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
+    {
+        const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            prv[v] = ld2(src[v] + zm * P + p);
+            cur[v] = ld2(src[v] + z0 * P + p);
+            nxt[v] = ld2(src[v] + zn * P + p);
+        }
+        load_halo(z0, hcur);
+        float be[3];
+        bext_at(c.bext_z, c.be, zm, be);
+        pair_emf(prv, be, c.sq);
+        bext_at(c.bext_z, c.be, z0, be);
+        pair_emf(cur, be, c.sq);
+        bext_at(c.bext_z, c.be, zn, be);
+        pair_emf(nxt, be, c.sq);
+    }
+    const float w0 = c.w0, w1 = c.w1, w1k = c.w1 * c.kappa;
+    const int r = ty + 1, cc = 2 + 2 * tx;
+    for (int z = z0; z < z1; ++z) {
+        const int zn = wrap_inc(z, nz);
+        const int za = wrap_inc(zn, nz);
+        const int buf = z & 1;
+        if (z + 1 < z1) {
+#pragma unroll
+            for (int v = 0; v < 6; ++v) ahd[v] = ld2(src[v] + za * P + p);
+            load_halo(zn, hnxt);
+        }
+        auto& t = tile[buf];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) *reinterpret_cast<float2*>(&t[v][r][cc]) = cur[v];
+        if (hkind != 0) {
+            float be[3];
+            bext_at(c.bext_z, c.be, z, be);
+            pair_emf(hcur, be, c.sq);
+            if (hkind == 1) {
+#pragma unroll
+                for (int v = 0; v < 6; ++v) *reinterpret_cast<float2*>(&t[v][hrow][hcol]) = hcur[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < 6; ++v) t[v][hrow][hcol] = hcur[v].x;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            float lf[6], rt[6];
+            float2 up[6], dn[6];
+#pragma unroll
+            for (int v = 0; v < 6; ++v) {
+                if (v != 5) {  // x neighbours: b, e1, e2
+                    lf[v] = t[v][r][cc - 1];
+                    rt[v] = t[v][r][cc + 2];
+                }
+                if (v != 4) {  // y neighbours: b, e1, e3
+                    up[v] = *reinterpret_cast<const float2*>(&t[v][r - 1][cc]);
+                    dn[v] = *reinterpret_cast<const float2*>(&t[v][r + 1][cc]);
+                }
+            }
+            const int k = z * P + p;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float sL = (lf[a] + cur[a].y) + (up[a].x + dn[a].x) + (prv[a].x + nxt[a].x);
+                const float sR = (cur[a].x + rt[a]) + (up[a].y + dn[a].y) + (prv[a].y + nxt[a].y);
+                float dL, dR;
+                if (a == 0) {
+                    dL = (dn[3].x - up[3].x) + (nxt[4].x - prv[4].x);
+                    dR = (dn[3].y - up[3].y) + (nxt[4].y - prv[4].y);
+                } else if (a == 1) {
+                    dL = (lf[3] - cur[3].y) + (nxt[5].x - prv[5].x);
+                    dR = (cur[3].x - rt[3]) + (nxt[5].y - prv[5].y);
+                } else {
+                    dL = (lf[4] - cur[4].y) + (up[5].x - dn[5].x);
+                    dR = (cur[4].x - rt[4]) + (up[5].y - dn[5].y);
+                }
+                *reinterpret_cast<float2*>(bout + k + a * n) =
+                    make_float2(emf_update(w0, w1, w1k, cur[a].x, sL, dL), emf_update(w0, w1, w1k, cur[a].y, sR, dR));
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            prv[v] = cur[v];
+            cur[v] = nxt[v];
+            hcur[v] = hnxt[v];
+        }
+        if (z + 1 < z1) {
+            float be[3];
+            bext_at(c.bext_z, c.be, za, be);
+            pair_emf(ahd, be, c.sq);
+#pragma unroll
+            for (int v = 0; v < 6; ++v) nxt[v] = ahd[v];
+        }
+    }
 }
 
 // Two-phase IB corrector over the whole domain (Sec. V.C-V.F): first one

@@ -79,7 +79,12 @@ struct Launch {
                 const T* bin = (const T*)s.b[s.bcur];
                 T* bout = (T*)s.b[1 - s.bcur];
                 const T* u = (const T*)s.u[s.fcur];
-                if (s.dim == 3)
+                if (pair_march(s)) {
+                    const dim3 pgrid((unsigned)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)),
+                                     (unsigned)((s.ny + kPairTY - 1) / kPairTY), (unsigned)((s.nz + chunk - 1) / chunk));
+                    k_sweep_march_pair<float><<<pgrid, kPairThreads, 0, st>>>(geo(s), (const float*)bin, (float*)bout,
+                                                                       (const float*)u, fcoef(c), chunk);
+                } else if (s.dim == 3)
                     k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
@@ -187,15 +192,28 @@ struct Launch {
         return try_resident_npt<DIM, UHALO, 2 * RN>(s, smem, ok);
     }
 
+    // The FP32 pair kernel serves 3-D domains with an even nx.
+    static bool pair_march(const State& s) { return sizeof(T) == 4 && s.dim == 3 && s.nx % 2 == 0; }
+    static SweepCoef<float> fcoef(const SweepCoef<T>& c) {
+        if constexpr (sizeof(T) == 4)
+            return c;
+        else
+            return SweepCoef<float>{};  // never launched: the pair kernel is FP32 only
+    }
+
     // z planes per CTA of the marching sweep such that the grid fills one wave
     static cudaError_t plan_march(State& s) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const bool pair = pair_march(s);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T>, kMarchTX * kMarchTY, 0);
+            e = pair ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march_pair<float>, kPairThreads, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T>, kMarchTX * kMarchTY, 0);
         if (e != cudaSuccess) return e;
-        const long long tiles = (long long)((s.nx + kMarchTX - 1) / kMarchTX) * ((s.ny + kMarchTY - 1) / kMarchTY);
+        const long long tiles =
+            pair ? (long long)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)) * ((s.ny + kPairTY - 1) / kPairTY)
+                 : (long long)((s.nx + kMarchTX - 1) / kMarchTX) * ((s.ny + kMarchTY - 1) / kMarchTY);
         const long long slots = (long long)std::max(1, per_sm) * std::max(1, sms);
         const long long per_column = std::max<long long>(1, slots / std::max<long long>(1, tiles));
         long long chunk = (s.nz + per_column - 1) / per_column;

@@ -311,37 +311,67 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             __syncthreads();
             if (s_abort) return;
         }
-        // (3) the z terms, two nodes at a time
-        const T* xin = xbuf + (long long)((s - 1) & 1) * nz * xplane;
+        // (3) the z terms, two nodes at a time.  All neighbour-plane loads of
+        // the thread are issued before any is used: one L2 round trip per sweep.
+        if constexpr (DIM == 3) {
+            const T* xin = xbuf + (long long)((s - 1) & 1) * nz * xplane;
+            const T* zsrc[2];
+            long long cs;  // stride between components
+            if (s == 0) {
+                zsrc[0] = b_in + (long long)zm * P;
+                zsrc[1] = b_in + (long long)zp * P;
+                cs = n;
+            } else {
+                zsrc[0] = xin + (long long)zm * xplane;
+                zsrc[1] = xin + (long long)zp * xplane;
+                cs = P;
+            }
+            // groups of up to 4 pairs (FP32; one pair in FP64, whose 1024-thread
+            // CTAs have half the registers) bound the registers holding loads in flight
+            constexpr int G = sizeof(T) == 8 ? 1 : (NPAIR < 4 ? NPAIR : 4);
 #pragma unroll
-        for (int k = 0; k < NPAIR; ++k) {
-            const int p0 = 2 * (tid + k * kResidentThreads);
-            if (DIM == 3 && p0 < P) {
+            for (int g0 = 0; g0 < NPAIR; g0 += G) {
+                typename Two<T>::V zb[G][2][3];
 #pragma unroll
-                for (int d = 4; d < 6; ++d) {
-                    const int zn = d == 4 ? zm : zp;
-                    const T* bez = d == 4 ? be_m : be_p;
-                    T bq[2][3], uq[2][3];
+                for (int j = 0; j < G; ++j) {
+                    const int p0 = 2 * (tid + (g0 + j) * kResidentThreads);
+                    if (p0 < P) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const auto vb = s == 0 ? ld2(b_in + a * n + (long long)zn * P + p0)
-                                               : ldcg2(xin + (long long)zn * xplane + (long long)a * P + p0);
-                        const auto vu = UHALO ? ld2(suh + ((d == 4 ? 0 : 3) + a) * P + p0)
-                                              : ld2(u + a * n + (long long)zn * P + p0);
-                        bq[0][a] = vb.x;
-                        bq[1][a] = vb.y;
-                        uq[0][a] = vu.x;
-                        uq[1][a] = vu.y;
+                        for (int d = 0; d < 2; ++d)
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) zb[j][d][a] = ldcg2(zsrc[d] + a * cs + p0);
                     }
+                }
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        T B[3];
+                for (int j = 0; j < G; ++j) {
+                    const int k = g0 + j;
+                    const int p0 = 2 * (tid + k * kResidentThreads);
+                    if (p0 < P) {
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[h][a];
-                        T phz[3] = {T(0), T(0), T(0)};
-                        flux_acc(uq[h], B, 2, d == 5 ? -c.w1 * c.kappa : c.w1 * c.kappa, phz);
+                        for (int d = 0; d < 2; ++d) {
+                            const int zn = d == 0 ? zm : zp;
+                            const T* bez = d == 0 ? be_m : be_p;
+                            T bq[2][3], uq[2][3];
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) nv[k][h][a] += c.w1 * bq[h][a] + phz[a];
+                            for (int a = 0; a < 3; ++a) {
+                                const auto vu = UHALO ? ld2(suh + (3 * d + a) * P + p0)
+                                                      : ld2(u + a * n + (long long)zn * P + p0);
+                                bq[0][a] = zb[j][d][a].x;
+                                bq[1][a] = zb[j][d][a].y;
+                                uq[0][a] = vu.x;
+                                uq[1][a] = vu.y;
+                            }
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                T B[3];
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[h][a];
+                                T phz[3] = {T(0), T(0), T(0)};
+                                flux_acc(uq[h], B, 2, d == 1 ? -c.w1 * c.kappa : c.w1 * c.kappa, phz);
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) nv[k][h][a] += c.w1 * bq[h][a] + phz[a];
+                            }
+                        }
                     }
                 }
             }

@@ -105,6 +105,28 @@ def test_mag_sweeps_with_frozen_velocity_fp64(kernel):
     np.testing.assert_array_equal(gu, u)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(22, 22, 6), (36, 21, 7), (64, 40, 9)])
+def test_mag_sweeps_with_frozen_velocity_fp32(kernel, shape):
+    # FP32 sweeps (the flux-component form and, for even nx, the node-pair
+    # kernel): tiles with ghost columns and rows, ramped field
+    nx, ny, nz = shape
+    p = W.small_pipe(nx=nx, ny=ny, nz=nz, diameter=min(nx, ny) - 6.0, precision="fp32", sweep_kernel=kernel,
+                     b0_kind="tanh", ramp_center=nz / 2, ramp_width=2.0, Ha=30.0, Rm=0.05)
+    z, y, x = np.meshgrid(np.arange(float(nz)), np.arange(float(ny)), np.arange(float(nx)), indexing="ij")
+    u = np.stack([0.01 * np.sin(2 * np.pi * y / ny), 0.02 * np.cos(2 * np.pi * x / nx), 0.03 + 0.001 * z])
+    o = oracle.Oracle(dict(p, precision="fp64"))
+    o.set_state(np.ones_like(x), u, np.zeros_like(u), t=0)
+    o.mag_sweeps(120)
+    with Solver(p) as s:
+        s.set_state(np.ones_like(x), u, np.zeros_like(u), t=0)
+        s.mag_sweeps(120)
+        _, gu, gb = s.state()
+    _, ou, ob = o.state()
+    assert rel(gb, ob) <= 1e-4
+    np.testing.assert_array_equal(gu, u.astype(np.float32).astype(np.float64))
+
+
 def test_observables_match_oracle_fp64():
     p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
