@@ -424,8 +424,13 @@ def main():
         kernel_name = "k_sweeps_resident<float,3> (all sweeps + IB on b, planes held in shared memory)"
         launches_per_step = 2 + 1
         per_launch_units = n_mag  # one launch runs every sweep of the step
+    elif solver.units["sweep_kernel"] == "split" and p["nx"] % 2 == 0:
+        kernel_name = ("k_sweep_march_pair<float> + k_ib_staged<float> (one sweep: z-marching stencil on node "
+                       "pairs, then the IB corrector on b, one CTA per plane)")
+        launches_per_step = 2 * n_mag + 2
+        per_launch_units = 1
     elif solver.units["sweep_kernel"] == "split":
-        kernel_name = ("k_sweep_march<float> + k_ib_planes<float> (one sweep: z-marching stencil, then the IB "
+        kernel_name = ("k_sweep_march<float> + k_ib_staged<float> (one sweep: z-marching stencil, then the IB "
                        "corrector on b, one CTA per plane)")
         launches_per_step = 2 * n_mag + 2
         per_launch_units = 1
