@@ -354,14 +354,6 @@ int upload_ib(State& s) {
     d.max_shell = h.max_shell;
     d.max_nnz = h.max_nnz;
     d.zinv = ib_tables_z_invariant(s, q9, w9) ? 1 : 0;
-    if (d.zinv && s.dim == 3 && d.nm > 0 && s.p.precision == QSLBM_FP32 && s.nx % 2 == 0) {
-        // the FP32 pair sweep hands the shell values to the IB pass in shell
-        // order: each in-plane node's position in plane 0's shell list
-        std::vector<int> slot((size_t)s.nx * s.ny, -1);
-        for (int i = 0; i < h.shell_off[1] - h.shell_off[0]; ++i) slot[h.shell_xy[h.shell_off[0] + i]] = i;
-        if ((rc = upload(s, (void**)&d.shell_slot_xy, slot))) return rc;
-        if ((rc = dev_alloc(s, &d.shell_buf, (size_t)3 * s.nz * std::max(1, d.max_shell) * s.esz))) return rc;
-    }
     return QSLBM_OK;
 }
 

@@ -25,8 +25,6 @@ struct DeviceIB {
     int nm = 0, ns = 0, nnz = 0, max_ring = 0, max_shell = 0, max_nnz = 0;
     int zinv = 0;  // 1: every z plane carries plane 0's ring and shell tables
     int* mk_slot = nullptr;  // [9 nm] shell-list position of each support node
-    int* shell_slot_xy = nullptr;  // [nx ny] position in plane 0's shell list, -1 off the shell (zinv only)
-    void* shell_buf = nullptr;     // [nz][3][max_shell] shell values in shell order (zinv, FP32 pair sweep)
 };
 
 // Host copy of the marker geometry and IB weights (binary64).

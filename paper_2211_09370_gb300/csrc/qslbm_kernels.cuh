@@ -530,9 +530,7 @@ __device__ __forceinline__ void pair_emf(float2 r[6], const float be[3], float s
 template <typename F>
 __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const F* __restrict__ bin,
                                                                    F* __restrict__ bout, const F* __restrict__ u,
-                                                                   SweepCoef<F> c, int chunk,
-                                                                   const int* __restrict__ slot_xy,
-                                                                   F* __restrict__ sbuf, int S) {
+                                                                   SweepCoef<F> c, int chunk) {
     static_assert(sizeof(F) == 4, "the pair sweep is the FP32 path");
     __shared__ __align__(16) PairTile tile;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -542,12 +540,6 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
     const int x = x0 + 2 * tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
     const int p = (y % ny) * nx + (x % nx);  // even: a pair never straddles a row end
-    // When sbuf is given (tables the same on every plane), a node of the IB
-    // shell also writes its new b to sbuf[z][component][slot], the plane's
-    // shell values in shell order, which the IB pass then reads contiguously
-    // instead of gathering them from the plane.
-    const int slL = (sbuf && active) ? slot_xy[p] : -1;
-    const int slR = (sbuf && active) ? slot_xy[p + 1] : -1;
     const int z0 = blockIdx.z * chunk;
     const int z1 = min(z0 + chunk, nz);
     const float* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
@@ -639,11 +631,8 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
                     dL = (lf[4] - cur[4].y) + (up[5].x - dn[5].x);
                     dR = (cur[4].x - rt[4]) + (up[5].y - dn[5].y);
                 }
-                const float oL = emf_update(w0, w1, w1k, cur[a].x, sL, dL);
-                const float oR = emf_update(w0, w1, w1k, cur[a].y, sR, dR);
-                *reinterpret_cast<float2*>(bout + k + a * n) = make_float2(oL, oR);
-                if (slL >= 0) sbuf[((size_t)z * 3 + a) * S + slL] = oL;
-                if (slR >= 0) sbuf[((size_t)z * 3 + a) * S + slR] = oR;
+                *reinterpret_cast<float2*>(bout + k + a * n) =
+                    make_float2(emf_update(w0, w1, w1k, cur[a].x, sL, dL), emf_update(w0, w1, w1k, cur[a].y, sR, dR));
             }
         }
 #pragma unroll
@@ -731,8 +720,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<
 // written once.  Same sums in the same order as ib_plane.  Shared memory:
 // 3 max_ring deltas, then 3 max_shell staged values.
 template <typename T>
-__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring,
-                                                              const T* __restrict__ sbuf) {
+__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sdelta = reinterpret_cast<T*>(smem_raw);
     T* sf = sdelta + 3 * max_ring;
@@ -745,17 +733,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<
     T* f0 = f + base;
     T* f1 = f0 + n;
     T* f2 = f1 + n;
-    if (sbuf) {  // the sweep left the plane's shell values contiguous, in shell order
-        const T* sb = sbuf + (size_t)z * 3 * S;
-        for (int i = threadIdx.x; i < 3 * S; i += kNodeThreads) sf[i] = sb[i];
-    } else {
 #pragma unroll 4
-        for (int i = threadIdx.x; i < S; i += kNodeThreads) {
-            const int q = ib.shell_xy[s0 + i];
-            sf[i] = f0[q];
-            sf[S + i] = f1[q];
-            sf[2 * S + i] = f2[q];
-        }
+    for (int i = threadIdx.x; i < S; i += kNodeThreads) {
+        const int q = ib.shell_xy[s0 + i];
+        sf[i] = f0[q];
+        sf[S + i] = f1[q];
+        sf[2 * S + i] = f2[q];
     }
     __syncthreads();
     for (int m = threadIdx.x; m < R; m += kNodeThreads) {

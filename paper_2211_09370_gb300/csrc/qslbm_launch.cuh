@@ -79,21 +79,17 @@ struct Launch {
                 const T* bin = (const T*)s.b[s.bcur];
                 T* bout = (T*)s.b[1 - s.bcur];
                 const T* u = (const T*)s.u[s.fcur];
-                // shell values handed from the pair sweep to the IB pass in shell order
-                const bool compact = pair_march(s) && s.ib.shell_buf != nullptr && s.ib_staged_smem > 0;
                 if (pair_march(s)) {
                     const dim3 pgrid((unsigned)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)),
                                      (unsigned)((s.ny + kPairTY - 1) / kPairTY), (unsigned)((s.nz + chunk - 1) / chunk));
-                    k_sweep_march_pair<float><<<pgrid, kPairThreads, 0, st>>>(
-                        geo(s), (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk, s.ib.shell_slot_xy,
-                        compact ? (float*)s.ib.shell_buf : nullptr, s.ib.max_shell);
+                    k_sweep_march_pair<float><<<pgrid, kPairThreads, 0, st>>>(geo(s), (const float*)bin, (float*)bout,
+                                                                       (const float*)u, fcoef(c), chunk);
                 } else if (s.dim == 3)
                     k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
                 if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
-                    k_ib_staged<T><<<s.nz, kNodeThreads, s.ib_staged_smem, st>>>(
-                        geo(s), bout, v, s.ib.max_ring, compact ? (const T*)s.ib.shell_buf : nullptr);
+                    k_ib_staged<T><<<s.nz, kNodeThreads, s.ib_staged_smem, st>>>(geo(s), bout, v, s.ib.max_ring);
                 } else if (s.ib.nm > 0) {
                     k_ib_markers<T><<<(s.ib.nm + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
                     k_ib_shell<T><<<(s.ib.ns + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
