@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "qslbm_internal.h"
 
 namespace qslbm {
@@ -1063,19 +1065,25 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
                                                             const T* __restrict__ usnap, ObsCoef<T> c,
                                                             double* partial) {
     __shared__ double red[kObs][kReduceThreads / 32];
+    // The node-local derivatives (flow-lattice Laplacian of u, gradient of b,
+    // the field lattice's QS operators) are formed in the fields' own
+    // precision; every product that enters a sum, and the sums, are FP64.
+    using L = typename std::conditional<sizeof(T) == 4, float, double>::type;
     double acc[kObs];
 #pragma unroll
     for (int i = 0; i < kObs; ++i) acc[i] = 0.0;
-    const long long n = g.n;
+    const int n = (int)g.n;  // the library keeps 3 n below 2^31
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(k % nx);
-        const int y = (int)((k / nx) % ny);
-        const int z = (int)(k / ((long long)nx * ny));
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int x = k % nx;
+        const int t = k / nx;
+        const int y = t % ny;
+        const int z = t / ny;
         const double rho = 1.0 + (double)drho[k];
-        const double uk[3] = {(double)u[k], (double)u[k + n], (double)u[k + 2 * n]};
-        const double bk[3] = {(double)b[k], (double)b[k + n], (double)b[k + 2 * n]};
+        const T ut[3] = {u[k], u[k + n], u[k + 2 * n]};
+        const T bt[3] = {b[k], b[k + n], b[k + 2 * n]};
+        const double uk[3] = {(double)ut[0], (double)ut[1], (double)ut[2]};
+        const double bk[3] = {(double)bt[0], (double)bt[1], (double)bt[2]};
         acc[0] += rho;
         bool bad = !isfinite(rho);
 #pragma unroll
@@ -1104,8 +1112,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         acc[2] += 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
         acc[3] += c.fb * uk[c.axis];
         // flow-lattice Laplacian of u and isotropic gradient of b
-        double lap[3] = {0.0, 0.0, 0.0};
-        double db[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        L lap[3] = {L(0), L(0), L(0)};
+        L db[3][3] = {{L(0), L(0), L(0)}, {L(0), L(0), L(0)}, {L(0), L(0), L(0)}};
 #pragma unroll
         for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
             int cx, cy, cz;
@@ -1113,49 +1121,50 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
                 flow_dir3(j, cx, cy, cz);
             else
                 flow_dir2(j, cx, cy, cz);
-            const long long q = ((long long)wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
-            const double w = flow_w<DIM>(j);
+            const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
+            const L w = (L)flow_w<DIM>(j);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                lap[a] += w * ((double)u[q + a * n] - uk[a]);
-                const double bq = (double)b[q + a * n];
-                db[0][a] += 3.0 * w * cx * bq;
-                db[1][a] += 3.0 * w * cy * bq;
-                db[2][a] += 3.0 * w * cz * bq;
+                lap[a] += w * ((L)u[q + a * n] - (L)ut[a]);
+                const L bq = (L)b[q + a * n];
+                db[0][a] += L(3) * w * L(cx) * bq;
+                db[1][a] += L(3) * w * L(cy) * bq;
+                db[2][a] += L(3) * w * L(cz) * bq;
             }
         }
         double ulap = 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ulap += uk[a] * 6.0 * lap[a];
+        for (int a = 0; a < 3; ++a) ulap += uk[a] * 6.0 * (double)lap[a];
         acc[4] += ulap;
-        const double J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
-        const double L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
-        acc[5] += -(uk[0] * L[0] + uk[1] * L[1] + uk[2] * L[2]);
+        const double J[3] = {(double)db[1][2] - (double)db[2][1], (double)db[2][0] - (double)db[0][2],
+                             (double)db[0][1] - (double)db[1][0]};
+        const double Lf[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
+        acc[5] += -(uk[0] * Lf[0] + uk[1] * Lf[1] + uk[2] * Lf[2]);
         // QS residual with the field lattice's operators
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double lapb = 0.0, div = 0.0;
+            L lapb = L(0), div = L(0);
 #pragma unroll
             for (int be = 0; be < DIM; ++be) {
                 const int ex = be == 0, ey = be == 1, ez = be == 2;
                 const int zpp = wrapi(z + ez, nz), zmm = wrapi(z - ez, nz);
-                const long long kp = ((long long)zpp * ny + wrapi(y + ey, ny)) * nx + wrapi(x + ex, nx);
-                const long long km = ((long long)zmm * ny + wrapi(y - ey, ny)) * nx + wrapi(x - ex, nx);
-                lapb += (double)b[kp + a * n] + (double)b[km + a * n] - 2.0 * bk[a];
+                const int kp = (zpp * ny + wrapi(y + ey, ny)) * nx + wrapi(x + ex, nx);
+                const int km = (zmm * ny + wrapi(y - ey, ny)) * nx + wrapi(x - ex, nx);
+                lapb += (L)b[kp + a * n] + (L)b[km + a * n] - L(2) * (L)bt[a];
                 T Bep_t[3], Bem_t[3];
                 bext_at(c.bext_z, c.be, zpp, Bep_t);
                 bext_at(c.bext_z, c.be, zmm, Bem_t);
-                double Bp[3], Bm[3];
+                L Bp[3], Bm[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
-                    Bp[cc] = (double)Bep_t[cc] + (c.strict_qs ? 0.0 : (double)b[kp + cc * n]);
-                    Bm[cc] = (double)Bem_t[cc] + (c.strict_qs ? 0.0 : (double)b[km + cc * n]);
+                    Bp[cc] = (L)Bep_t[cc] + (c.strict_qs ? L(0) : (L)b[kp + cc * n]);
+                    Bm[cc] = (L)Bem_t[cc] + (c.strict_qs ? L(0) : (L)b[km + cc * n]);
                 }
-                const double phip = (double)u[kp + be * n] * Bp[a] - (double)u[kp + a * n] * Bp[be];
-                const double phim = (double)u[km + be * n] * Bm[a] - (double)u[km + a * n] * Bm[be];
-                div += 0.5 * (phip - phim);
+                const L phip = (L)u[kp + be * n] * Bp[a] - (L)u[kp + a * n] * Bp[be];
+                const L phim = (L)u[km + be * n] * Bm[a] - (L)u[km + a * n] * Bm[be];
+                div += L(0.5) * (phip - phim);
             }
-            const double r = c.eta * lapb - div;
+            const double r = c.eta * (double)lapb - (double)div;
             acc[6] += r * r;
         }
     }
