@@ -110,12 +110,10 @@ struct Launch {
         }
     }
 
-    static constexpr int RT = ResidentShape<T>::threads;
-    static constexpr int RN = ResidentShape<T>::npt_small;
-
-    template <int DIM, bool UHALO, int NPT>
+    template <int DIM, bool UHALO, bool SMALL>
     static void resident_launch_one(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
                                     cudaStream_t st) {
+        constexpr int RT = ResidentShape<T, SMALL>::threads, NPT = ResidentShape<T, SMALL>::npt;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)s.nz);
         cfg.blockDim = dim3(RT);
@@ -142,31 +140,34 @@ struct Launch {
         if (e != cudaSuccess) s.launch_error = true;
     }
 
+    static bool small_plane(const State& s) { return (long long)s.nx * s.ny <= (long long)kResidentSmallPlane; }
+
     static void launch_resident(State& s, int nsweeps, const SweepCoef<T>& c, const IBView<T>& v,
                                 cudaStream_t st) {
-        const bool small = (long long)s.nx * s.ny <= (long long)RT * RN;
+        const bool small = small_plane(s);
         if (s.dim == 3) {
             if (s.resident_uhalo) {
                 if (small)
-                    resident_launch_one<3, true, RN>(s, nsweeps, c, v, st);
+                    resident_launch_one<3, true, true>(s, nsweeps, c, v, st);
                 else
-                    resident_launch_one<3, true, 2 * RN>(s, nsweeps, c, v, st);
+                    resident_launch_one<3, true, false>(s, nsweeps, c, v, st);
             } else {
                 if (small)
-                    resident_launch_one<3, false, RN>(s, nsweeps, c, v, st);
+                    resident_launch_one<3, false, true>(s, nsweeps, c, v, st);
                 else
-                    resident_launch_one<3, false, 2 * RN>(s, nsweeps, c, v, st);
+                    resident_launch_one<3, false, false>(s, nsweeps, c, v, st);
             }
         } else {
             if (small)
-                resident_launch_one<2, false, RN>(s, nsweeps, c, v, st);
+                resident_launch_one<2, false, true>(s, nsweeps, c, v, st);
             else
-                resident_launch_one<2, false, 2 * RN>(s, nsweeps, c, v, st);
+                resident_launch_one<2, false, false>(s, nsweeps, c, v, st);
         }
     }
 
-    template <int DIM, bool UHALO, int NPT>
-    static cudaError_t try_resident_npt(State& s, size_t smem, bool& ok) {
+    template <int DIM, bool UHALO, bool SMALL>
+    static cudaError_t try_resident_shape(State& s, size_t smem, bool& ok) {
+        constexpr int RT = ResidentShape<T, SMALL>::threads, NPT = ResidentShape<T, SMALL>::npt;
         ok = false;
         auto kern = k_sweeps_resident<T, DIM, UHALO, RT, NPT, false>;
         auto kern2 = k_sweeps_resident<T, DIM, UHALO, RT, NPT, true>;
@@ -188,8 +189,8 @@ struct Launch {
 
     template <int DIM, bool UHALO>
     static cudaError_t try_resident(State& s, size_t smem, bool& ok) {
-        if ((long long)s.nx * s.ny <= (long long)RT * RN) return try_resident_npt<DIM, UHALO, RN>(s, smem, ok);
-        return try_resident_npt<DIM, UHALO, 2 * RN>(s, smem, ok);
+        if (small_plane(s)) return try_resident_shape<DIM, UHALO, true>(s, smem, ok);
+        return try_resident_shape<DIM, UHALO, false>(s, smem, ok);
     }
 
     // The FP32 pair kernel serves 3-D domains with an even nx.

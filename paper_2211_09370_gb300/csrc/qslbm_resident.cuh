@@ -16,15 +16,17 @@
 
 namespace qslbm {
 
-// Launch shape: FP32 uses 512 threads, FP64 1024 (the register budget of a
-// thread holds its nodes' new values until the whole plane has been read).
-// Each thread takes up to NPT nodes: NPT = 8 / 4 covers planes of 4096 nodes,
-// twice that covers the 8192-node maximum.
-template <typename T>
+// Launch shape: a thread holds its NPT nodes' new values in registers until
+// the whole plane has been read.  Planes of up to 4096 nodes (SMALL) take
+// 1024 threads x 4 nodes in both precisions (64 registers a thread; the most
+// warps to hide each sweep's latencies); larger planes, up to 8192 nodes, take
+// 512 x 16 in FP32 and 1024 x 8 in FP64.
+template <typename T, bool SMALL>
 struct ResidentShape {
-    static constexpr int threads = sizeof(T) == 4 ? 512 : 1024;
-    static constexpr int npt_small = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int threads = (sizeof(T) == 4 && !SMALL) ? 512 : 1024;
+    static constexpr int npt = SMALL ? 4 : (sizeof(T) == 4 ? 16 : 8);
 };
+constexpr int kResidentSmallPlane = 4096;
 constexpr int kResidentMaxPlane = 8192;
 constexpr unsigned long long kWaitTimeoutNs = 1000000000ULL;
 
