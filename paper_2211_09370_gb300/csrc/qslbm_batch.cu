@@ -103,6 +103,23 @@ __global__ void __launch_bounds__(kNodeThreads) k_batch_ib_shell(const InstDesc<
     ib_shell<T>(D.ibm, D.b[((D.bpar + s) & 1) ^ 1], (int)D.g.n, w - sfirst[i]);
 }
 
+// The staged IB corrector over every active instance: one CTA per
+// (instance, plane) in the plane prefix table; shared memory for the largest
+// ring and shell of the batch.
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_batch_ib_staged(const InstDesc<T>* __restrict__ d,
+                                                                  const int* __restrict__ pfirst, int kact, int s,
+                                                                  int max_ring) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int i = find_inst(pfirst, kact, blockIdx.x);
+    const InstDesc<T>& D = d[i];
+    const int z = blockIdx.x - pfirst[i];
+    T* f = D.b[((D.bpar + s) & 1) ^ 1];
+    ib_staged_plane<T, kNodeThreads>(D.ibm, f, (int)D.g.n, z * D.g.nx * D.g.ny, D.ibm.zinv ? 0 : z, sdelta,
+                                     sdelta + 3 * max_ring);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kNodeThreads) k_batch_ib(const InstDesc<T>* __restrict__ d,
                                                            const int* __restrict__ pfirst, int kact, int s) {
@@ -186,6 +203,8 @@ struct qslbm_batch {
     bool owns_members = true;
     bool tuned = false;
     size_t ib_smem = 0;
+    size_t ib_staged_smem = 0;  // shared memory of k_batch_ib_staged, 0 when it does not fit
+    int max_ring = 1;           // largest ring of the batch (layout of that shared memory)
     int threads = 256, grid = 0;         // autotuned sweep launch
     cudaGraphExec_t graph = nullptr;
     long long steps = 0;
@@ -272,7 +291,10 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     (void)threads;
     qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s);
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
-    if (nm > 0) {
+    if (nm > 0 && B.ib_staged_smem > 0) {
+        qslbm::k_batch_ib_staged<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
+            d, B.pfirst, kact, s, B.max_ring);
+    } else if (nm > 0) {
         qslbm::k_batch_ib_markers<T><<<(nm + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
                                         st>>>(d, B.mfirst, kact, s);
         qslbm::k_batch_ib_shell<T><<<(ns + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
@@ -299,7 +321,7 @@ int build_tables(qslbm_batch& B, int threads) {
     B.h_pfirst.assign(K + 1, 0);
     B.h_mfirst.assign(K + 1, 0);
     B.h_sfirst.assign(K + 1, 0);
-    size_t ring = 1;
+    size_t ring = 1, shell = 1;
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
@@ -312,8 +334,23 @@ int build_tables(qslbm_batch& B, int threads) {
         B.h_mfirst[k + 1] = B.h_mfirst[k] + s.ib.nm;
         B.h_sfirst[k + 1] = B.h_sfirst[k] + s.ib.ns;
         ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
+        shell = std::max(shell, (size_t)std::max(1, s.ib.max_shell));
     }
     B.ib_smem = 3 * ring * sizeof(T);
+    // the staged IB corrector, when the largest plane's ring and shell fit
+    B.max_ring = (int)ring;
+    B.ib_staged_smem = 0;
+    {
+        const size_t smem = 3 * (ring + shell) * sizeof(T);
+        int dev = 0, optin = 0;
+        BCHK(cudaGetDevice(&dev));
+        BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (smem <= (size_t)optin) {
+            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+            B.ib_staged_smem = smem;
+        }
+    }
     if (K > B.capacity) {
         if (B.desc) cudaFree(B.desc);
         if (B.first) cudaFree(B.first);
@@ -557,7 +594,7 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
     info->nodes = nodes;
     info->node_sweeps_per_step = sweeps;
     info->device_bytes = bytes;
-    info->launches_per_step = 2 * B->max_nmag + 3;
+    info->launches_per_step = (B->ib_staged_smem ? 2 : 3) * B->max_nmag + 3;  // sweep + IB per sweep; force, flow, advance
     info->steps = B->steps;
     for (size_t c = 0; c < B->tune_us.size() && c < 8; ++c) info->tune_us[c] = B->tune_us[c];
     return QSLBM_OK;

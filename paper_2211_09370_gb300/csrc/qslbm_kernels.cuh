@@ -716,34 +716,30 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<
     ib_plane<T>(ib, f, f + n, f + 2 * n, base, ib.zinv ? 0 : (int)blockIdx.x, sdelta);
 }
 
-// The same corrector with the plane's shell nodes staged in shared memory:
-// their values are read from memory once (independent loads), the markers
-// interpolate from the staged copy through mk_slot, and every shell node is
-// written once.  Same sums in the same order as ib_plane.  Shared memory:
-// 3 max_ring deltas, then 3 max_shell staged values.
-template <typename T>
-__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sdelta = reinterpret_cast<T*>(smem_raw);
-    T* sf = sdelta + 3 * max_ring;
-    const int z = blockIdx.x, tz = ib.zinv ? 0 : z;
+// The IB corrector with the plane's shell nodes staged in shared memory, on
+// plane `base` of f (three components n apart): the shell values are read
+// from memory once (independent loads), the markers interpolate from the
+// staged copy through mk_slot, and every shell node is written once.  Same
+// sums in the same order as ib_plane.  tz: the plane whose tables apply;
+// sdelta holds 3 R values, sf 3 S.  Called by every thread of the CTA.
+template <typename T, int THREADS>
+__device__ __forceinline__ void ib_staged_plane(const IBView<T>& ib, T* f, int n, int base, int tz, T* sdelta,
+                                                T* sf) {
     const int m0 = ib.ring_off[tz], R = ib.ring_off[tz + 1] - m0;
-    if (R == 0) return;
+    if (R == 0) return;  // uniform across the CTA
     const int s0 = ib.shell_off[tz], S = ib.shell_off[tz + 1] - s0;
-    const int n = (int)g.n;
-    const int base = z * g.nx * g.ny;
     T* f0 = f + base;
     T* f1 = f0 + n;
     T* f2 = f1 + n;
 #pragma unroll 4
-    for (int i = threadIdx.x; i < S; i += kNodeThreads) {
+    for (int i = threadIdx.x; i < S; i += THREADS) {
         const int q = ib.shell_xy[s0 + i];
         sf[i] = f0[q];
         sf[S + i] = f1[q];
         sf[2 * S + i] = f2[q];
     }
     __syncthreads();
-    for (int m = threadIdx.x; m < R; m += kNodeThreads) {
+    for (int m = threadIdx.x; m < R; m += THREADS) {
         T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -759,7 +755,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<
         sdelta[3 * m + 2] = -s * a2;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < S; i += kNodeThreads) {
+    for (int i = threadIdx.x; i < S; i += THREADS) {
         T c0 = T(0), c1 = T(0), c2 = T(0);
         const int e0 = ib.csr_off[s0 + i], e1 = ib.csr_off[s0 + i + 1];
         for (int e = e0; e < e1; ++e) {
@@ -774,6 +770,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<
         f1[q] = sf[S + i] + c1;
         f2[q] = sf[2 * S + i] + c2;
     }
+}
+
+// The staged corrector as a launch of its own, one CTA per plane.  Shared
+// memory: 3 max_ring deltas, then 3 max_shell staged values.
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sdelta = reinterpret_cast<T*>(smem_raw);
+    const int z = blockIdx.x;
+    ib_staged_plane<T, kNodeThreads>(ib, f, (int)g.n, z * g.nx * g.ny, ib.zinv ? 0 : z, sdelta, sdelta + 3 * max_ring);
 }
 
 // ---------------------------------------------------------------------------
