@@ -37,7 +37,7 @@ class _Params(C.Structure):
         ("b0_kind", C.c_int), ("b0_dir", C.c_double * 3), ("ramp_center", C.c_double),
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
-        ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int),
+        ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
     ]
 
 
@@ -129,6 +129,7 @@ def make_params(p: dict) -> _Params:
     q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
     q.perturb = float(p.get("perturb", 0.0))
     q.strict_qs = int(p.get("strict_qs", 0))
+    q.alpha = float(p.get("alpha", 1.0))
     return q
 
 

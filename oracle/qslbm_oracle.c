@@ -30,6 +30,9 @@
  *               c = 6 eta (c_s^2 = c^2/3), N_mag = ceil(1/dt)
  *   Sec. IV     Eq. "Energy balance equations", Eq. "variable force"
  *   Sec. V.H    Eq. "Error l2 decay" (QS residual)
+ *   Sec. V.H    "Strategies for very high values of resistivity": the sweep
+ *               with the extra coefficient alpha (Eq. "magnetic field
+ *               quasi-static acelerated"); alpha = 1 is the plain sweep
  *
  * Readings where the paper is silent or garbled (each one is also listed in the
  * design notes of the repository):
@@ -57,6 +60,11 @@
  *      nu = U0 R/Re, eta = U0 R/Rm, B0 = Ha sqrt(eta nu)/R, F0 = 4 nu U0/R^2
  *      (pipe) or 2 nu U0/R^2 (channel); automatic U0 = min(0.05, Re c_s^2/(2R),
  *      Re R/(2 Ha^2)).
+ *   R13 Accelerated sweep: the printed rest equilibrium "(1 - w_1) B + alpha B"
+ *      would not keep a uniform field fixed under B <- (1/alpha) sum_i g_i.  It
+ *      is read as (w_1 - 1 + alpha) b (w_1 the rest weight), which keeps it
+ *      fixed and gives the plain sweep at alpha = 1; the moving equilibria are
+ *      unchanged.  Per node this is b + (sweep(b) - b)/alpha.
  */
 #include <math.h>
 #include <stdint.h>
@@ -82,6 +90,7 @@ typedef struct orc_params {
     uint64_t seed;
     double perturb;
     int strict_qs;
+    double alpha; /* accelerated sweep (Sec. V.H); 0 means 1, the plain sweep */
 } orc_params;
 
 typedef struct orc_derived {
@@ -421,13 +430,17 @@ static double geq(const orc* o, int i, int a, long y) {
         if (e == 0) continue;
         flux += (double)e / (o->d.c_mag * o->d.cm2) * (u[be] * B[a] - u[a] * B[be]);
     }
+    if (i == 0) /* rest direction: (w_0 - 1 + alpha) b (reading R13) */
+        return (o->p.alpha - 1.0 + o->field.w[0]) * o->b[a][y];
     return o->field.w[i] * (o->b[a][y] + flux);
 }
 
 /* One sweep of the tau_m = 1 scheme (Sec. V.G, Eq. "Single step algoritm for
- * magnetic field"): b_alpha(x) <- sum_i g^eq_{i alpha}(x - e_i). */
+ * magnetic field"): b_alpha(x) <- sum_i g^eq_{i alpha}(x - e_i); with the
+ * accelerated equilibria of Sec. V.H the sum is multiplied by 1/alpha. */
 static void sweep(orc* o) {
     long n = o->n;
+    const double inv_alpha = 1.0 / o->p.alpha;
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) {
         int x, y, z;
@@ -438,7 +451,7 @@ static void sweep(orc* o) {
                 long yk = node(o, x - o->field.c[i][0], y - o->field.c[i][1], z - o->field.c[i][2]);
                 s += geq(o, i, a, yk);
             }
-            o->b_new[a][k] = s;
+            o->b_new[a][k] = s * inv_alpha;
         }
     }
     for (int a = 0; a < 3; ++a) {
@@ -617,6 +630,7 @@ orc* orc_create(const orc_params* p) {
     orc* o = calloc(1, sizeof(orc));
     o->p = *p;
     if (o->p.dim == 2) o->p.nz = 1;
+    if (o->p.alpha == 0.0) o->p.alpha = 1.0;
     if (orc_derive(&o->p, &o->d) != 0) {
         free(o);
         return NULL;

@@ -250,15 +250,20 @@ def test_mass_conserved_to_roundoff():
 
 # ------------------------------------------------------------ magnetic sweep
 
-def test_sweep_single_mode_amplification():
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.75])
+def test_sweep_single_mode_amplification(alpha):
     # With u = 0 one tau_m = 1 sweep multiplies a Fourier mode cos(k x) by
-    # sum_i w_i cos(k e_ix): 3/4 + cos(k)/4 on D3Q7, 2/3 + cos(k)/3 on D2Q5.
-    for dim, gain in ((3, lambda k: 0.75 + 0.25 * math.cos(k)), (2, lambda k: 2 / 3 + math.cos(k) / 3)):
+    # g = sum_i w_i cos(k e_ix): 3/4 + cos(k)/4 on D3Q7, 2/3 + cos(k)/3 on D2Q5.
+    # The accelerated sweep of Sec. V.H, b <- (1/alpha) [(w_0 - 1 + alpha) b +
+    # sum_{i>0} w_i b(x - e_i)], multiplies it by (g - 1 + alpha)/alpha: the
+    # decay per sweep 1 - g grows by 1/alpha, and a uniform field stays fixed.
+    for dim, g0 in ((3, lambda k: 0.75 + 0.25 * math.cos(k)), (2, lambda k: 2 / 3 + math.cos(k) / 3)):
+        gain = lambda k, g0=g0: (g0(k) - 1.0 + alpha) / alpha  # noqa: E731
         if dim == 3:
-            p = W.small_pipe(nx=12, ny=4, nz=4, geometry="none", perturb=0.0)
+            p = W.small_pipe(nx=12, ny=4, nz=4, geometry="none", perturb=0.0, alpha=alpha)
             shape = (4, 4, 12)
         else:
-            p = W.hartmann_channel_2d(nx=12, ny=4, geometry="none")
+            p = W.hartmann_channel_2d(nx=12, ny=4, geometry="none", alpha=alpha)
             shape = (1, 4, 12)
         o = oracle.Oracle(p)
         x = np.arange(12, dtype=float)
@@ -271,14 +276,17 @@ def test_sweep_single_mode_amplification():
         np.testing.assert_allclose(bb[1], gain(k) * b[1], rtol=0, atol=1e-17)
 
 
-def test_sweep_fixed_point_is_discrete_qs_poisson_solution():
+@pytest.mark.parametrize("alpha,sweeps", [(1.0, 3000), (0.75, 2250)])
+def test_sweep_fixed_point_is_discrete_qs_poisson_solution(alpha, sweeps):
     # Sec. V.G: iterated to convergence the sweep solves
     # eta lap b = div(u B^ext - B^ext u) (strict QS flux).  Compare with an FFT
     # solve of the same discrete operators (7-point Laplacian, central
-    # divergence) on a periodic box without walls.
+    # divergence) on a periodic box without walls.  The accelerated sweep of
+    # Sec. V.H (alpha = 3/4, the smallest value stable on D3Q7) reaches the
+    # same fixed point in 3/4 of the sweeps.
     n = 12
     p = W.small_pipe(nx=n, ny=n, nz=n, geometry="none", diameter=10.0, Re=10.0, Ha=5.0, Rm=0.05,
-                     U0=0.05, strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0)
+                     U0=0.05, strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0, alpha=alpha)
     o = oracle.Oracle(p)
     d = o.derived()
     eta = d["eta"]
@@ -287,7 +295,7 @@ def test_sweep_fixed_point_is_discrete_qs_poisson_solution():
     u = np.stack([0.02 * np.sin(t * y) * np.cos(t * z), 0.03 * np.cos(t * x + 2 * t * z),
                   0.01 * np.sin(t * x + t * y)])
     o.set_state(rho=np.ones((n, n, n)), u=u, b=np.zeros_like(u), t=0)
-    o.mag_sweeps(3000)
+    o.mag_sweeps(sweeps)
     _, _, b = o.state()
     Be = d["B0"] * np.array([0.6, 0.8, 0.0])
     k = [np.fft.fftfreq(n) * 2 * np.pi] * 3
@@ -307,6 +315,30 @@ def test_sweep_fixed_point_is_discrete_qs_poisson_solution():
         np.testing.assert_allclose(b[a], want, rtol=0, atol=1e-10 * np.abs(want).max() + 1e-18)
     # at the fixed point the QS residual of the observables vanishes
     assert o.observables()["qs_residual"] < 1e-9 * np.abs(u).max() * np.abs(Be).max()
+
+
+def test_accelerated_sweep_stability_bound():
+    # The checkerboard mode has the smallest plain-sweep gain, g = 2 w_0 - 1
+    # (-1/2 on D3Q7, -1/3 on D2Q5); the accelerated gain (g - 1 + alpha)/alpha
+    # reaches -1 at alpha = 1 - w_0 (3/4, 2/3) and falls below it for smaller
+    # alpha, so on these lattices alpha must stay >= 1 - w_0 (the paper's
+    # alpha >= 1/2 is for its own lattice).
+    for dim, w0, shape in ((3, 0.25, (4, 4, 4)), (2, 1 / 3, (1, 4, 4))):
+        for alpha, want in ((1.0 - w0, -1.0), (0.5, (2 * w0 - 1 - 1 + 0.5) / 0.5)):
+            if dim == 3:
+                p = W.small_pipe(nx=4, ny=4, nz=4, geometry="none", perturb=0.0, alpha=alpha)
+            else:
+                p = W.hartmann_channel_2d(nx=4, ny=4, geometry="none", alpha=alpha)
+            o = oracle.Oracle(p)
+            z, y, x = np.meshgrid(*(np.arange(float(m)) for m in shape), indexing="ij")
+            cb = (-1.0) ** (x + y + (z if dim == 3 else 0))
+            b = np.zeros((3,) + shape)
+            b[0] = 1e-3 * cb
+            o.set_state(rho=np.ones(shape), u=np.zeros((3,) + shape), b=b, t=0)
+            o.mag_sweeps(1)
+            _, _, bb = o.state()
+            np.testing.assert_allclose(bb[0], want * b[0], rtol=0, atol=1e-17)
+            assert abs(want) > 1.0 or want == -1.0
 
 
 # --------------------------------------------------- converged physical flows
