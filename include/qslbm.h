@@ -107,6 +107,10 @@ typedef struct qslbm_params {
     double perturb;         /* initial |u| noise, fraction of U0, inside the wall  */
     int32_t init_kind;      /* QSLBM_INIT_REST (default) | QSLBM_INIT_POISEUILLE   */
     int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT | _SPLIT */
+    double alpha;           /* accelerated sweep (Sec. V.H, Eq. "magnetic field
+                               quasi-static acelerated"): b <- b + (sweep(b) - b)/alpha;
+                               1 (default; 0 also means 1) is the plain sweep; stable
+                               for 1 - w_0 <= alpha <= 1 (3/4 in 3-D, 2/3 in 2-D) */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 

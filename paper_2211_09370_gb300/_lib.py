@@ -35,7 +35,7 @@ class qslbm_params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
-        ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("stream", C.c_void_p),
+        ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double), ("stream", C.c_void_p),
     ]
 
 
@@ -200,6 +200,7 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.init_kind = {"rest": 0, "poiseuille": 1}[ik] if isinstance(ik, str) else int(ik)
     k = p.get("sweep_kernel", "auto")
     q.sweep_kernel = SWEEP_KERNEL[k] if isinstance(k, str) else int(k)
+    q.alpha = float(p.get("alpha", 1.0))
     q.stream = stream
     return q
 

@@ -119,6 +119,13 @@ int validate(const qslbm_params& p) {
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
     if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_SPLIT) return QSLBM_EINVAL;
     if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
+    {
+        // accelerated sweep: the checkerboard gain (2 w_0 - 2 + alpha)/alpha
+        // stays >= -1 only for alpha >= 1 - w_0 (w_0 = 1/4 on D3Q7, 1/3 on D2Q5)
+        const double a = p.alpha == 0.0 ? 1.0 : p.alpha;
+        const double w0 = p.dim == 3 ? 0.25 : 1.0 / 3.0;
+        if (!(a >= 1.0 - w0 && a <= 1.0)) return QSLBM_EINVAL;
+    }
     // kernels index the three components of a field with 32-bit offsets
     long long n = (long long)p.nx * p.ny * p.nz;
     if (3 * n > (1LL << 31) - 1) return QSLBM_EINVAL;
@@ -411,9 +418,11 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
     s.omega = s.p.force_amp != 0.0 ? 2.0 * M_PI / s.p.force_period : 0.0;
     if (s.dim == 3) {
         s.w0 = 0.25;
+        s.alpha = s.p.alpha == 0.0 ? 1.0 : s.p.alpha;
         s.w1 = 0.125;
     } else {
         s.w0 = 1.0 / 3.0;
+        s.alpha = s.p.alpha == 0.0 ? 1.0 : s.p.alpha;
         s.w1 = 1.0 / 6.0;
     }
     s.kappa = 1.0 / (s.units.c_mag * s.units.cm2);
@@ -683,6 +692,7 @@ void qslbm_params_init(qslbm_params* p) {
     p->ramp_width = 1.0;
     p->n_mag_cap = 270;
     p->precision = QSLBM_FP32;
+    p->alpha = 1.0;
 }
 
 int qslbm_create(const qslbm_params* p, qslbm_handle** out) {

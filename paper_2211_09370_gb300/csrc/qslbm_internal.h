@@ -48,6 +48,7 @@ struct State {
     size_t esz = 4;
     double cx = 0, cy = 0, R = 0;
     double w0 = 0, w1 = 0, kappa = 0;  // field lattice weights, 1/(2 eta)
+    double alpha = 1.0;                // accelerated-sweep coefficient (1: plain sweep)
     double be[3] = {0, 0, 0};          // uniform B^ext
     int axis = 2;                      // body-force direction
     double omega = 0;                  // 2 pi / period

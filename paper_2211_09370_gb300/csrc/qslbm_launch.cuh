@@ -55,7 +55,8 @@ struct Launch {
 
     static void sweeps(State& s, int nsweeps, cudaStream_t st) {
         SweepCoef<T> c;
-        c.w0 = (T)s.w0;
+        c.w0 = (T)((s.alpha - 1.0) + s.w0);
+        c.ia = (T)(1.0 / s.alpha);
         c.w1 = (T)s.w1;
         c.kappa = (T)s.kappa;
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];

@@ -35,13 +35,14 @@ def test_struct_layouts_match_header_sizes():
     p = _lib.qslbm_params()
     _lib.load().qslbm_params_init(C.byref(p))
     assert p.dim == 3 and p.geometry == _lib.PIPE and p.n_mag_cap == 270 and p.marker_spacing == 1.0
-    assert math.isnan(p.center[0]) and p.b0_dir[0] == 1.0 and p.precision == _lib.FP32
+    assert math.isnan(p.center[0]) and p.b0_dir[0] == 1.0 and p.precision == _lib.FP32 and p.alpha == 1.0
 
 
 @pytest.mark.parametrize("bad", [
     dict(dim=4), dict(nx=0), dict(diameter=-1.0), dict(Re=0.0), dict(Rm=-1.0), dict(Ha=-2.0),
     dict(marker_spacing=0.0), dict(b0_kind=7), dict(b0_kind="tanh", ramp_width=0.0),
     dict(force_amp=0.2, force_period=0.0), dict(precision=5), dict(n_mag=-3), dict(perturb=-1.0),
+    dict(alpha=0.7), dict(alpha=1.5), dict(alpha=-1.0),
 ])
 def test_invalid_parameters_rejected_before_device(bad):
     p = W.small_pipe(**bad)

@@ -127,6 +127,31 @@ def test_mag_sweeps_with_frozen_velocity_fp32(kernel, shape):
     np.testing.assert_array_equal(gu, u.astype(np.float32).astype(np.float64))
 
 
+ACCEL_CASES = {
+    # accelerated sweep (Sec. V.H) at the smallest stable alpha of each lattice
+    "pipe_ramp": (dict(nx=24, ny=22, nz=10, diameter=16.0, Re=200.0, Ha=30.0, Rm=0.05, b0_kind="tanh",
+                       ramp_center=5.0, ramp_width=2.0, perturb=0.0, n_mag=30, alpha=0.75), 30),
+    "pipe_odd": (dict(nx=21, ny=19, nz=6, diameter=14.0, perturb=0.0, n_mag=20, alpha=0.8), 25),
+}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(ACCEL_CASES))
+def test_accelerated_sweep_parity(name, precision, kernel):
+    kw, steps = ACCEL_CASES[name]
+    p = W.small_pipe(precision=precision, sweep_kernel=kernel, **kw)
+    got, want, _ = run_both(p, steps)
+    check_fields(got, want, precision, name)
+
+
+def test_accelerated_sweep_parity_2d_channel():
+    p = W.hartmann_channel_2d(nx=37, ny=20, diameter=19.0, n_mag=40, perturb=0.0, alpha=2.0 / 3.0,
+                              precision="fp64")
+    got, want, _ = run_both(p, 40)
+    check_fields(got, want, "fp64", "channel alpha 2/3")
+
+
 def test_observables_match_oracle_fp64():
     p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
