@@ -124,7 +124,7 @@ int validate(const qslbm_params& p) {
         // stays >= -1 only for alpha >= 1 - w_0 (w_0 = 1/4 on D3Q7, 1/3 on D2Q5)
         const double a = p.alpha == 0.0 ? 1.0 : p.alpha;
         const double w0 = p.dim == 3 ? 0.25 : 1.0 / 3.0;
-        if (!(a >= 1.0 - w0 && a <= 1.0)) return QSLBM_EINVAL;
+        if (!(a >= 1.0 - w0 - 1e-12 && a <= 1.0)) return QSLBM_EINVAL;
     }
     // kernels index the three components of a field with 32-bit offsets
     long long n = (long long)p.nx * p.ny * p.nz;

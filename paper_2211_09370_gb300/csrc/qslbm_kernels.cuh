@@ -62,11 +62,10 @@ struct IBView {
 // Coefficients of the tau_m = 1 magnetic sweep (Sec. V.G).
 template <typename T>
 struct SweepCoef {
-    // w0: the rest weight in the sum, (w_0 - 1 + alpha) for the accelerated
-    // sweep of Sec. V.H (w_0 itself when alpha = 1); the sum is multiplied by
-    // ia = 1/alpha (exactly 1 for the plain sweep)
-    T w0, w1;      // field-lattice weights: rest (as above), axis
-    T ia;
+    // The accelerated sweep of Sec. V.H, b <- (1/alpha) [(w_0 - 1 + alpha) b +
+    // sum_{i>0} g_i(x - e_i)], is carried by the weights: w0 = (w_0 - 1 +
+    // alpha)/alpha, w1 = w_axis/alpha (the plain weights, exactly, at alpha = 1).
+    T w0, w1;      // scaled field-lattice weights: rest, axis
     T kappa;       // 1 / (c c_m^2) = 1 / (2 eta)
     T be[3];       // uniform B^ext (used when bext_z == nullptr)
     const T* bext_z;  // [3 * nz] B^ext per plane for the ramp, or nullptr
@@ -211,7 +210,7 @@ __device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* _
         flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out[a] = (acc[a] + c.w1 * c.kappa * diff[a]) * c.ia;
+    for (int a = 0; a < 3; ++a) out[a] = acc[a] + c.w1 * c.kappa * diff[a];
 }
 
 template <typename T, int DIM>
@@ -415,9 +414,9 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                 const T dy = (tile[3][cy][cx - 1] - tile[3][cy][cx + 1]) + (nxt[5] - prv[5]);
                 const T dz =
                     (tile[4][cy][cx - 1] - tile[4][cy][cx + 1]) + (tile[5][cy - 1][cx] - tile[5][cy + 1][cx]);
-                bout[k] = emf_update(c.w0, c.w1, w1k, cur[0], s[0], dx) * c.ia;
-                bout[k + n] = emf_update(c.w0, c.w1, w1k, cur[1], s[1], dy) * c.ia;
-                bout[k + 2 * n] = emf_update(c.w0, c.w1, w1k, cur[2], s[2], dz) * c.ia;
+                bout[k] = emf_update(c.w0, c.w1, w1k, cur[0], s[0], dx);
+                bout[k + n] = emf_update(c.w0, c.w1, w1k, cur[1], s[1], dy);
+                bout[k + 2 * n] = emf_update(c.w0, c.w1, w1k, cur[2], s[2], dz);
             } else {
                 T be_c[3], be_m[3], be_p[3];
                 bext_at(c.bext_z, c.be, z, be_c);
@@ -452,7 +451,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                     flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
                 }
 #pragma unroll
-                for (int a = 0; a < 3; ++a) bout[k + a * n] = (acc[a] + c.w1 * c.kappa * diff[a]) * c.ia;
+                for (int a = 0; a < 3; ++a) bout[k + a * n] = acc[a] + c.w1 * c.kappa * diff[a];
             }
         }
         __syncthreads();
@@ -638,8 +637,7 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
                     dR = (cur[4].x - rt[4]) + (up[5].y - dn[5].y);
                 }
                 *reinterpret_cast<float2*>(bout + k + a * n) =
-                    make_float2(emf_update(w0, w1, w1k, cur[a].x, sL, dL) * c.ia,
-                                emf_update(w0, w1, w1k, cur[a].y, sR, dR) * c.ia);
+                    make_float2(emf_update(w0, w1, w1k, cur[a].x, sL, dL), emf_update(w0, w1, w1k, cur[a].y, sR, dR));
             }
         }
 #pragma unroll

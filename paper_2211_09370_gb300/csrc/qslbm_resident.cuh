@@ -385,9 +385,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             if (p0 < P) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const T v0 = nv[k][0][a] * c.ia, v1 = nv[k][1][a] * c.ia;  // 1/alpha (exact 1: plain sweep)
-                    st2(sb + a * P + p0, v0, v1);
-                    if (publish) stcg2(xout + a * P + p0, v0, v1);
+                    st2(sb + a * P + p0, nv[k][0][a], nv[k][1][a]);
+                    if (publish) stcg2(xout + a * P + p0, nv[k][0][a], nv[k][1][a]);
                 }
             }
         }
@@ -470,11 +469,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             if (p < P) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const T v = nv[k][a] * c.ia;  // 1/alpha (exact 1: plain sweep)
-                    sb[a * P + p] = v;
+                    sb[a * P + p] = nv[k][a];
                     // nodes off the wall shell are final now; shell nodes are
                     // rewritten after the IB correction below
-                    if (publish) __stcg(xout + a * P + p, v);
+                    if (publish) __stcg(xout + a * P + p, nv[k][a]);
                 }
             }
         }
