@@ -38,13 +38,14 @@ class _Params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
+        ("mag_scheme", C.c_int),
     ]
 
 
 class _Derived(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
-    _fields_ += [("n_mag", C.c_int), ("n_markers", C.c_int)]
+    _fields_ += [("n_mag", C.c_int), ("n_markers", C.c_int), ("tau_m", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -130,6 +131,7 @@ def make_params(p: dict) -> _Params:
     q.perturb = float(p.get("perturb", 0.0))
     q.strict_qs = int(p.get("strict_qs", 0))
     q.alpha = float(p.get("alpha", 1.0))
+    q.mag_scheme = int(p.get("mag_scheme", 0))
     return q
 
 

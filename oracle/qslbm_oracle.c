@@ -30,6 +30,9 @@
  *               c = 6 eta (c_s^2 = c^2/3), N_mag = ceil(1/dt)
  *   Sec. IV     Eq. "Energy balance equations", Eq. "variable force"
  *   Sec. V.H    Eq. "Error l2 decay" (QS residual)
+ *   Sec. III.E  Eq. "single-step algorithm for MHD de rosis": the magnetic
+ *               update for any tau_m (mag_scheme = 1: one update per flow step,
+ *               the induction equation advanced in time, not quasi-static)
  *   Sec. V.H    "Strategies for very high values of resistivity": the sweep
  *               with the extra coefficient alpha (Eq. "magnetic field
  *               quasi-static acelerated"); alpha = 1 is the plain sweep
@@ -65,6 +68,10 @@
  *      is read as (w_1 - 1 + alpha) b (w_1 the rest weight), which keeps it
  *      fixed and gives the plain sweep at alpha = 1; the moving equilibria are
  *      unchanged.  Per node this is b + (sweep(b) - b)/alpha.
+ *   R14 Time-resolved magnetic update (mag_scheme = 1): the field lattice runs
+ *      at the flow's speed (c = 1, dx = dt = 1), so eta = c_m^2 (tau_m - 1/2),
+ *      tau_m = eta/c_m^2 + 1/2, the flux coefficient is e_beta / c_m^2, and the
+ *      update runs once per flow step, followed by the IB on b.
  */
 #include <math.h>
 #include <stdint.h>
@@ -91,11 +98,13 @@ typedef struct orc_params {
     double perturb;
     int strict_qs;
     double alpha; /* accelerated sweep (Sec. V.H); 0 means 1, the plain sweep */
+    int mag_scheme; /* 0: quasi-static sweeps (tau_m = 1); 1: one update per step (R14) */
 } orc_params;
 
 typedef struct orc_derived {
     double R, U0, nu, tau, eta, B0, F0, c_mag, lambda, lambda_m, cs2, cm2;
     int n_mag, n_markers;
+    double tau_m; /* relaxation time of the magnetic update: 1, or R14 */
 } orc_derived;
 
 typedef struct lattice {
@@ -235,9 +244,15 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     /* eta = c_s^2 (tau_m - 1/2) dt with tau_m = 1, c_s^2 = c^2 c_m^2, dx = c dt = 1
      * gives eta = c c_m^2 / 2, so c = 2 eta / c_m^2 and N_mag = ceil(c).          */
     d->c_mag = 2.0 * d->eta / d->cm2;
+    d->tau_m = 1.0;
     int n = p->n_mag > 0 ? p->n_mag : ceil_tol(d->c_mag);
     if (p->n_mag <= 0 && p->n_mag_cap > 0 && n > p->n_mag_cap) n = p->n_mag_cap;
     if (n < 1) n = 1;
+    if (p->mag_scheme == 1) { /* R14 */
+        d->c_mag = 1.0;
+        d->tau_m = d->eta / d->cm2 + 0.5;
+        n = 1;
+    }
     d->n_mag = n;
     double nu_ref = p->nu_ref > 0 ? p->nu_ref : d->nu;
     double eta_ref = p->eta_ref > 0 ? p->eta_ref : 0.5 * d->cm2;
@@ -437,10 +452,14 @@ static double geq(const orc* o, int i, int a, long y) {
 
 /* One sweep of the tau_m = 1 scheme (Sec. V.G, Eq. "Single step algoritm for
  * magnetic field"): b_alpha(x) <- sum_i g^eq_{i alpha}(x - e_i); with the
- * accelerated equilibria of Sec. V.H the sum is multiplied by 1/alpha. */
+ * accelerated equilibria of Sec. V.H the sum is multiplied by 1/alpha.  With
+ * mag_scheme = 1 the update of Sec. III.E for any tau_m:
+ * b_alpha(x) <- sum_i { g_i(x - e_i) + (tau_m - 1) [g_i(x + e_i) - 2 g_i(x) + g_i(x - e_i)] }. */
 static void sweep(orc* o) {
     long n = o->n;
     const double inv_alpha = 1.0 / o->p.alpha;
+    const double tm = o->d.tau_m;
+    const int full = o->p.mag_scheme == 1;
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) {
         int x, y, z;
@@ -448,8 +467,14 @@ static void sweep(orc* o) {
         for (int a = 0; a < 3; ++a) {
             double s = 0.0;
             for (int i = 0; i < o->field.q; ++i) {
-                long yk = node(o, x - o->field.c[i][0], y - o->field.c[i][1], z - o->field.c[i][2]);
-                s += geq(o, i, a, yk);
+                long ym = node(o, x - o->field.c[i][0], y - o->field.c[i][1], z - o->field.c[i][2]);
+                if (!full) {
+                    s += geq(o, i, a, ym);
+                } else {
+                    long yp = node(o, x + o->field.c[i][0], y + o->field.c[i][1], z + o->field.c[i][2]);
+                    double gm = geq(o, i, a, ym), gp = geq(o, i, a, yp), g0 = geq(o, i, a, k);
+                    s += gm + (tm - 1.0) * (gp - 2.0 * g0 + gm);
+                }
             }
             o->b_new[a][k] = s * inv_alpha;
         }

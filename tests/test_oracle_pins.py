@@ -341,6 +341,60 @@ def test_accelerated_sweep_stability_bound():
             assert abs(want) > 1.0 or want == -1.0
 
 
+def _full_update_case(dim, **kw):
+    # mag_scheme = 1 (Sec. III.E update for any tau_m, one per flow step);
+    # U0 = 0.05, R = 5: eta = 0.25 / Rm, tau_m = eta / c_m^2 + 1/2
+    if dim == 3:
+        p = W.small_pipe(nx=12, ny=4, nz=4, geometry="none", diameter=10.0, U0=0.05, Rm=3.0, Ha=0.0,
+                         perturb=0.0, mag_scheme=1, **kw)
+        shape = (4, 4, 12)
+    else:
+        p = W.hartmann_channel_2d(nx=12, ny=4, geometry="none", diameter=10.0, U0=0.05, Rm=3.0, Ha=0.0,
+                                  mag_scheme=1, **kw)
+        shape = (1, 4, 12)
+    return oracle.Oracle(p), shape
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_time_resolved_update_single_mode_and_advection(dim):
+    # With u = 0 the update multiplies cos(k x) by (2 tau_m - 1) g - 2 (tau_m - 1),
+    # g the plain-sweep gain (3/4 + cos(k)/4 on D3Q7, 2/3 + cos(k)/3 on D2Q5).
+    # With a uniform u_x = U, b_y = cos(k x) and no applied field, the flux
+    # adds U sin(k) sin(k x) (the axis weight times the flux coefficient
+    # 1/c_m^2 is 1/2 on both lattices: a central difference of U b): the
+    # profile moves toward +x.
+    o, shape = _full_update_case(dim)
+    d = o.derived()
+    assert d["n_mag"] == 1 and d["c_mag"] == 1.0
+    tm = d["tau_m"]
+    assert tm == pytest.approx(d["eta"] / d["cm2"] + 0.5, rel=1e-15)
+    g0 = (lambda k: 0.75 + 0.25 * math.cos(k)) if dim == 3 else (lambda k: 2 / 3 + math.cos(k) / 3)
+    x = np.arange(12, dtype=float)
+    k = 2 * np.pi * 2 / 12
+    amp = (2 * tm - 1) * g0(k) - 2 * (tm - 1)
+    for U in (0.0, 0.04):
+        o, shape = _full_update_case(dim)
+        b = np.zeros((3,) + shape)
+        b[1] = 1e-3 * np.cos(k * x)
+        u = np.zeros((3,) + shape)
+        u[0] = U
+        o.set_state(rho=np.ones(shape), u=u, b=b, t=0)
+        o.mag_sweeps(1)
+        _, _, bb = o.state()
+        want = 1e-3 * (amp * np.cos(k * x) + U * math.sin(k) * np.sin(k * x))
+        np.testing.assert_allclose(bb[1], np.broadcast_to(want, bb[1].shape), rtol=0, atol=1e-17)
+        np.testing.assert_allclose(bb[0], 0.0, atol=1e-20)
+        np.testing.assert_allclose(bb[2], 0.0, atol=1e-20)
+
+
+def test_time_resolved_update_stability_bound():
+    # The checkerboard gain (2 tau_m - 1)(2 w_0 - 1) - 2 (tau_m - 1) reaches -1
+    # at tau_m = 7/6 on D3Q7 (w_0 = 1/4) and 5/4 on D2Q5 (w_0 = 1/3): the
+    # library accepts 1/2 < tau_m <= that bound.
+    for w0, tmax in ((0.25, 7 / 6), (1 / 3, 5 / 4)):
+        assert (2 * tmax - 1) * (2 * w0 - 1) - 2 * (tmax - 1) == pytest.approx(-1.0, abs=1e-15)
+
+
 # --------------------------------------------------- converged physical flows
 
 @pytest.fixture(scope="module")
