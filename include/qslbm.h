@@ -79,6 +79,12 @@ extern "C" {
 #define QSLBM_SWEEP_RESIDENT 2
 #define QSLBM_SWEEP_SPLIT 3
 
+#define QSLBM_MAG_QS 0   /* quasi-static: N_mag tau_m = 1 sweeps per flow step  */
+#define QSLBM_MAG_TIME 1 /* time-resolved: one update of Sec. III.E Eq. "single-
+                            step algorithm for MHD de rosis" per flow step, with
+                            tau_m = eta/c_m^2 + 1/2 (lattice speed 1); needs
+                            1/2 < tau_m <= 7/6 (3-D) or 5/4 (2-D) and alpha = 1 */
+
 /* Problem statement of the paper (Sec. II: Re, Rm, Ha with L = pipe radius;
  * Sec. IV: pipe, insulating walls, pressure gradient; Sec. VI: non-uniform
  * applied field).  qslbm_params_init fills the defaults noted here. */
@@ -111,6 +117,7 @@ typedef struct qslbm_params {
                                quasi-static acelerated"): b <- b + (sweep(b) - b)/alpha;
                                1 (default; 0 also means 1) is the plain sweep; stable
                                for 1 - w_0 <= alpha <= 1 (3/4 in 3-D, 2/3 in 2-D) */
+    int32_t mag_scheme;     /* QSLBM_MAG_QS (default) | QSLBM_MAG_TIME             */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 
@@ -123,6 +130,7 @@ typedef struct qslbm_units {
     int64_t device_bytes; /* device memory the handle holds */
     int64_t shell_nodes;  /* nodes inside the support of some wall marker */
     int32_t sweep_kernel; /* the QSLBM_SWEEP_* kernel in use (never AUTO)        */
+    double tau_m;         /* relaxation time of the magnetic update (1 for QS)  */
 } qslbm_units;
 
 /* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2

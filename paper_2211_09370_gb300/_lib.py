@@ -35,7 +35,8 @@ class qslbm_params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
-        ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double), ("stream", C.c_void_p),
+        ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double),
+        ("mag_scheme", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -43,7 +44,7 @@ class qslbm_units(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
     _fields_ += [("n_mag", C.c_int32), ("n_markers", C.c_int32), ("nodes", C.c_int64), ("device_bytes", C.c_int64),
-                ("shell_nodes", C.c_int64), ("sweep_kernel", C.c_int32)]
+                ("shell_nodes", C.c_int64), ("sweep_kernel", C.c_int32), ("tau_m", C.c_double)]
 
 
 class qslbm_obs(C.Structure):
@@ -201,6 +202,7 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     k = p.get("sweep_kernel", "auto")
     q.sweep_kernel = SWEEP_KERNEL[k] if isinstance(k, str) else int(k)
     q.alpha = float(p.get("alpha", 1.0))
+    q.mag_scheme = int(p.get("mag_scheme", 0))
     q.stream = stream
     return q
 

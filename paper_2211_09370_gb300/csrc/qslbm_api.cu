@@ -95,9 +95,16 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     u.B0 = p.Ha * std::sqrt(u.eta * u.nu) / u.R;
     u.F0 = (p.geometry == QSLBM_CHANNEL ? 2.0 : 4.0) * u.nu * U0 / (u.R * u.R);
     u.c_mag = 2.0 * u.eta / u.cm2;
+    u.tau_m = 1.0;
     int n = p.n_mag > 0 ? p.n_mag : ceil_rel(u.c_mag);
     if (p.n_mag <= 0 && p.n_mag_cap > 0) n = std::min(n, p.n_mag_cap);
     u.n_mag = std::max(n, 1);
+    if (p.mag_scheme == QSLBM_MAG_TIME) {
+        // the field lattice at the flow's speed: eta = c_m^2 (tau_m - 1/2)
+        u.c_mag = 1.0;
+        u.tau_m = u.eta / u.cm2 + 0.5;
+        u.n_mag = 1;
+    }
     double nu_ref = p.nu_ref > 0 ? p.nu_ref : u.nu;
     double eta_ref = p.eta_ref > 0 ? p.eta_ref : 0.5 * u.cm2;
     u.lambda = u.nu / nu_ref;
@@ -125,6 +132,19 @@ int validate(const qslbm_params& p) {
         const double a = p.alpha == 0.0 ? 1.0 : p.alpha;
         const double w0 = p.dim == 3 ? 0.25 : 1.0 / 3.0;
         if (!(a >= 1.0 - w0 - 1e-12 && a <= 1.0)) return QSLBM_EINVAL;
+        if (p.mag_scheme != QSLBM_MAG_QS && p.mag_scheme != QSLBM_MAG_TIME) return QSLBM_EINVAL;
+        if (p.mag_scheme == QSLBM_MAG_TIME && a != 1.0) return QSLBM_EINVAL;
+    }
+    if (p.mag_scheme == QSLBM_MAG_TIME) {
+        // checkerboard gain (2 tau_m - 1)(2 w_0 - 1) - 2 (tau_m - 1) >= -1
+        qslbm_units u;
+        map_units(p, u);
+        const double tmax = p.dim == 3 ? 7.0 / 6.0 : 5.0 / 4.0;
+        if (!(u.tau_m > 0.5 && u.tau_m <= tmax + 1e-12)) {
+            g_last_error = "time-resolved magnetic update: tau_m = " + std::to_string(u.tau_m) + " outside (1/2, " +
+                           std::to_string(tmax) + "]";
+            return QSLBM_EINVAL;
+        }
     }
     // kernels index the three components of a field with 32-bit offsets
     long long n = (long long)p.nx * p.ny * p.nz;

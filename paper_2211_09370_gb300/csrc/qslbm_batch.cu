@@ -243,9 +243,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     }
     D.F = (T*)s.F;
     D.tdev = s.tdev;
-    D.sc.w0 = (T)(((s.alpha - 1.0) + s.w0) / s.alpha);  // accelerated sweep; exact w_0 at alpha = 1
-    D.sc.w1 = (T)(s.w1 / s.alpha);
-    D.sc.kappa = (T)s.kappa;
+    sweep_weights(s, D.sc.w0, D.sc.w1, D.sc.kappa);
     for (int a = 0; a < 3; ++a) D.sc.be[a] = (T)s.be[a];
     D.sc.bext_z = (const T*)s.bext_z;
     D.sc.strict_qs = s.p.strict_qs;

@@ -81,6 +81,25 @@ struct State {
     long long device_bytes = 0;
 };
 
+// Weights of the magnetic update as the sweep kernels use them,
+//   b <- w0 b + w1 sum_{axis nbrs} b + (w1 kappa) D   (D: the flux differences),
+// covering three forms of the same sum:
+//   - the tau_m = 1 sweep (Sec. V.G): w_0, w_axis, 1/(c c_m^2);
+//   - the accelerated sweep (Sec. V.H): (w_0 - 1 + alpha)/alpha, w_axis/alpha;
+//   - the time-resolved update for any tau_m (Sec. III.E, de Rosis form), whose
+//     sum_i {g_i(x - e_i) + (tau_m - 1)[g_i(x + e_i) - 2 g_i(x) + g_i(x - e_i)]}
+//     is (2 tau_m - 1) times the plain neighbour sum of b, plus the plain flux
+//     sum, minus 2 (tau_m - 1) b, since the flux terms of g_i(x + e_i) are
+//     those of g_i(x - e_i) with the sign reversed and sum_i g_i(x) = b.
+// At alpha = 1 and tau_m = 1 every weight is exactly the plain one.
+template <typename T>
+inline void sweep_weights(const State& s, T& w0, T& w1, T& kappa) {
+    const double tm = s.units.tau_m, a = s.alpha;
+    w0 = (T)(((2.0 * tm - 1.0) * s.w0 - 2.0 * (tm - 1.0) + (a - 1.0)) / a);
+    w1 = (T)((2.0 * tm - 1.0) * s.w1 / a);
+    kappa = (T)(s.kappa / (2.0 * tm - 1.0));
+}
+
 // Kernel launchers, one table per storage precision.
 struct Ops {
     void (*init)(State&, cudaStream_t);

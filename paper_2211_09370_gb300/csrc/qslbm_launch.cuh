@@ -55,9 +55,7 @@ struct Launch {
 
     static void sweeps(State& s, int nsweeps, cudaStream_t st) {
         SweepCoef<T> c;
-        c.w0 = (T)(((s.alpha - 1.0) + s.w0) / s.alpha);  // accelerated sweep; exact w_0 at alpha = 1
-        c.w1 = (T)(s.w1 / s.alpha);
-        c.kappa = (T)s.kappa;
+        sweep_weights(s, c.w0, c.w1, c.kappa);
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
         c.bext_z = static_cast<const T*>(s.bext_z);
         c.strict_qs = s.p.strict_qs;

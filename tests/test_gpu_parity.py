@@ -152,6 +152,34 @@ def test_accelerated_sweep_parity_2d_channel():
     check_fields(got, want, "fp64", "channel alpha 2/3")
 
 
+TIME_CASES = {
+    # time-resolved magnetic update (Sec. III.E, one per flow step), tau_m 0.9 and 0.7
+    "pipe_ramp": (dict(nx=24, ny=22, nz=10, diameter=16.0, U0=0.05, Re=50.0, Ha=10.0, Rm=4.0, b0_kind="tanh",
+                       ramp_center=5.0, ramp_width=2.0, perturb=0.0, mag_scheme=1), 60),
+    "pipe_odd": (dict(nx=21, ny=19, nz=6, diameter=14.0, U0=0.05, Re=30.0, Ha=8.0, Rm=7.0, perturb=0.0,
+                      mag_scheme=1), 60),
+}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(TIME_CASES))
+def test_time_resolved_update_parity(name, precision, kernel):
+    kw, steps = TIME_CASES[name]
+    p = W.small_pipe(precision=precision, sweep_kernel=kernel, **kw)
+    with Solver(p) as s:
+        assert s.units["n_mag"] == 1 and 0.5 < s.units["tau_m"] <= 7 / 6
+    got, want, _ = run_both(p, steps)
+    check_fields(got, want, precision, name)
+
+
+def test_time_resolved_update_parity_2d_channel():
+    p = W.hartmann_channel_2d(nx=37, ny=20, diameter=19.0, U0=0.05, Rm=3.0, perturb=0.0, mag_scheme=1,
+                              precision="fp64")
+    got, want, _ = run_both(p, 80)
+    check_fields(got, want, "fp64", "channel time-resolved")
+
+
 def test_observables_match_oracle_fp64():
     p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
