@@ -60,10 +60,12 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, i
 }
 
 // Persistent z-marching sweep over every active instance's tiles: work item w
-// is (instance, tile x, tile y, z chunk) in the prefix table `first`.
+// is (instance, tile x, tile y, z chunk of `chunk` planes) in the prefix table
+// `first`.
 template <typename T>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
-                                                                    const int* __restrict__ first, int kact, int s) {
+                                                                    const int* __restrict__ first, int kact, int s,
+                                                                    int chunk) {
     __shared__ MarchTile<T> tile;
     const int total = first[kact];
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDe
         const int r = local - bz * tiles_x * tiles_y;
         const int by = r / tiles_x, bx = r - by * tiles_x;
         const int par = (D.bpar + s) & 1;
-        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, kMarchChunk, tile);
+        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, chunk, tile);
         __syncthreads();
     }
 }
@@ -205,6 +207,7 @@ struct qslbm_batch {
     size_t ib_smem = 0;
     size_t ib_staged_smem = 0;  // shared memory of k_batch_ib_staged, 0 when it does not fit
     int max_ring = 1;           // largest ring of the batch (layout of that shared memory)
+    int chunk = 16;             // z planes per work item of the marching sweep
     int threads = 256, grid = 0;         // autotuned sweep launch
     cudaGraphExec_t graph = nullptr;
     long long steps = 0;
@@ -287,7 +290,7 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
     (void)threads;
-    qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s);
+    qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
     if (nm > 0 && B.ib_staged_smem > 0) {
         qslbm::k_batch_ib_staged<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
@@ -320,12 +323,31 @@ int build_tables(qslbm_batch& B, int threads) {
     B.h_mfirst.assign(K + 1, 0);
     B.h_sfirst.assign(K + 1, 0);
     size_t ring = 1, shell = 1;
+    {
+        // z planes per work item of the marching sweep: 16, halved while the
+        // batch would give fewer than 8 work items per SM (small instances:
+        // shorter serial chains, more of them)
+        int dev = 0, sms = 0;
+        BCHK(cudaGetDevice(&dev));
+        BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        auto items = [&](int chunk) {
+            long long w = 0;
+            for (int k = 0; k < K; ++k) {
+                const State& s = qslbm::handle_state_mut(B.members[k]);
+                w += (long long)((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
+                     ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) * ((s.nz + chunk - 1) / chunk);
+            }
+            return w;
+        };
+        B.chunk = qslbm::kMarchChunk;
+        while (B.chunk > 2 && items(B.chunk) < 8LL * sms) B.chunk /= 2;
+    }
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
         const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
                           ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
-                          ((s.nz + qslbm::kMarchChunk - 1) / qslbm::kMarchChunk);
+                          ((s.nz + B.chunk - 1) / B.chunk);
         h[k].bpp = tiles;
         B.h_first[k + 1] = B.h_first[k] + tiles;
         B.h_pfirst[k + 1] = B.h_pfirst[k] + s.nz;
