@@ -38,7 +38,7 @@ class _Params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
-        ("mag_scheme", C.c_int),
+        ("mag_scheme", C.c_int), ("gamma", C.c_double),
     ]
 
 
@@ -90,7 +90,8 @@ def lib():
         L.orc_kernel1d.argtypes = [C.c_double]
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_splitmix64.argtypes = [C.c_uint64]
-        L.orc_gzs_terms.argtypes = [C.c_int, C.c_double, dp, dp, dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_gzs_terms.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, dp, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -132,6 +133,7 @@ def make_params(p: dict) -> _Params:
     q.strict_qs = int(p.get("strict_qs", 0))
     q.alpha = float(p.get("alpha", 1.0))
     q.mag_scheme = int(p.get("mag_scheme", 0))
+    q.gamma = float(p.get("gamma", 1.0))
     return q
 
 
@@ -226,13 +228,14 @@ def splitmix64(x: int) -> int:
     return int(lib().orc_splitmix64(int(x) & ((1 << 64) - 1)))
 
 
-def gzs_terms(dim: int, tau: float, u, F):
-    """GZS forcing terms F_i for every flow-lattice direction; returns (F_i, c_i)."""
+def gzs_terms(dim: int, tau: float, u, F, gamma: float = 1.0):
+    """GZS forcing terms F_i for every flow-lattice direction (with the time
+    step rescaled by gamma); returns (F_i, c_i)."""
     u = np.asarray(u, dtype=np.float64)
     F = np.asarray(F, dtype=np.float64)
     Fi = np.zeros(19)
     c = np.zeros(57, dtype=np.int32)
     q = C.c_int(0)
-    lib().orc_gzs_terms(int(dim), float(tau), _ptr(u), _ptr(F), _ptr(Fi), C.byref(q),
+    lib().orc_gzs_terms(int(dim), float(tau), float(gamma), _ptr(u), _ptr(F), _ptr(Fi), C.byref(q),
                         c.ctypes.data_as(C.POINTER(C.c_int)))
     return Fi[: q.value], c.reshape(19, 3)[: q.value]

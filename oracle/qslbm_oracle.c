@@ -33,6 +33,10 @@
  *   Sec. III.E  Eq. "single-step algorithm for MHD de rosis": the magnetic
  *               update for any tau_m (mag_scheme = 1: one update per flow step,
  *               the induction equation advanced in time, not quasi-static)
+ *   Sec. V.I    rescaled time step dt/gamma (Eq. "adaptative time step delta t",
+ *               "adaptative time step lattice velocities", "rescaled relaxation
+ *               time"): second-order f^eq terms and the g^eq flux over gamma,
+ *               tau = nu/(gamma c_s^2) + 1/2, the GZS terms with gamma
  *   Sec. V.H    "Strategies for very high values of resistivity": the sweep
  *               with the extra coefficient alpha (Eq. "magnetic field
  *               quasi-static acelerated"); alpha = 1 is the plain sweep
@@ -72,6 +76,13 @@
  *      at the flow's speed (c = 1, dx = dt = 1), so eta = c_m^2 (tau_m - 1/2),
  *      tau_m = eta/c_m^2 + 1/2, the flux coefficient is e_beta / c_m^2, and the
  *      update runs once per flow step, followed by the IB on b.
+ *   R15 Rescaled time step (gamma): a step advances physical time by 1/gamma.
+ *      Per step the forces (body and Lorentz, physical rates) add F/gamma to
+ *      rho u, the body-force modulation runs on t/gamma, and the magnetic
+ *      algorithm uses the per-step resistivity eta/gamma (sweeps: c = 2 eta /
+ *      (gamma c_m^2); time-resolved: tau_m = eta/(gamma c_m^2) + 1/2) with the
+ *      flux over gamma, so that the quasi-static fixed point does not depend
+ *      on gamma.  lambda and lambda_m use nu/gamma and eta/gamma.
  */
 #include <math.h>
 #include <stdint.h>
@@ -99,6 +110,7 @@ typedef struct orc_params {
     int strict_qs;
     double alpha; /* accelerated sweep (Sec. V.H); 0 means 1, the plain sweep */
     int mag_scheme; /* 0: quasi-static sweeps (tau_m = 1); 1: one update per step (R14) */
+    double gamma;   /* time-step rescaling (Sec. V.I); 0 means 1 */
 } orc_params;
 
 typedef struct orc_derived {
@@ -124,6 +136,7 @@ typedef struct orc {
     double *usnap[3];
     long t, tsnap;
     double mass0;
+    double ig; /* 1/gamma */
     int nm;
     double *X, *Y, *Z, *dj, *sj, *smj;
 } orc;
@@ -234,7 +247,8 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     }
     d->U0 = U0;
     d->nu = U0 * R / p->Re;                 /* Re = U0 L / nu  (Sec. II)        */
-    d->tau = d->nu / d->cs2 + 0.5;          /* nu = c_s^2 (tau - 1/2)          */
+    const double g = p->gamma > 0 ? p->gamma : 1.0;
+    d->tau = d->nu / (g * d->cs2) + 0.5;    /* nu = gamma c_s^2 (tau - 1/2)    */
     d->eta = U0 * R / p->Rm;                /* Rm = U0 L / eta                  */
     d->B0 = p->Ha * sqrt(d->eta * d->nu) / R; /* Ha = B0 L / sqrt(eta nu)       */
     if (p->geometry == ORC_CHANNEL)
@@ -243,21 +257,21 @@ int orc_derive(const orc_params* p, orc_derived* d) {
         d->F0 = 4.0 * d->nu * U0 / (R * R);
     /* eta = c_s^2 (tau_m - 1/2) dt with tau_m = 1, c_s^2 = c^2 c_m^2, dx = c dt = 1
      * gives eta = c c_m^2 / 2, so c = 2 eta / c_m^2 and N_mag = ceil(c).          */
-    d->c_mag = 2.0 * d->eta / d->cm2;
+    d->c_mag = 2.0 * d->eta / (g * d->cm2);
     d->tau_m = 1.0;
     int n = p->n_mag > 0 ? p->n_mag : ceil_tol(d->c_mag);
     if (p->n_mag <= 0 && p->n_mag_cap > 0 && n > p->n_mag_cap) n = p->n_mag_cap;
     if (n < 1) n = 1;
     if (p->mag_scheme == 1) { /* R14 */
         d->c_mag = 1.0;
-        d->tau_m = d->eta / d->cm2 + 0.5;
+        d->tau_m = d->eta / (g * d->cm2) + 0.5;
         n = 1;
     }
     d->n_mag = n;
-    double nu_ref = p->nu_ref > 0 ? p->nu_ref : d->nu;
+    double nu_ref = p->nu_ref > 0 ? p->nu_ref : d->nu / g;
     double eta_ref = p->eta_ref > 0 ? p->eta_ref : 0.5 * d->cm2;
-    d->lambda = d->nu / nu_ref;
-    d->lambda_m = d->eta / eta_ref;
+    d->lambda = d->nu / g / nu_ref;
+    d->lambda_m = d->eta / g / eta_ref;
     return 0;
 }
 
@@ -443,7 +457,7 @@ static double geq(const orc* o, int i, int a, long y) {
     for (int be = 0; be < 3; ++be) {
         int e = o->field.c[i][be];
         if (e == 0) continue;
-        flux += (double)e / (o->d.c_mag * o->d.cm2) * (u[be] * B[a] - u[a] * B[be]);
+        flux += (double)e / (o->d.c_mag * o->d.cm2) * (u[be] * B[a] - u[a] * B[be]) * o->ig;
     }
     if (i == 0) /* rest direction: (w_0 - 1 + alpha) b (reading R13) */
         return (o->p.alpha - 1.0 + o->field.w[0]) * o->b[a][y];
@@ -504,7 +518,8 @@ static double feq(const orc* o, int i, long y) {
         cu += o->flow.c[i][a] * o->u[a][y];
         uu += o->u[a][y] * o->u[a][y];
     }
-    return o->flow.w[i] * o->rho[y] * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+    return o->flow.w[i] * o->rho[y] *
+           (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) * o->ig - uu / (2.0 * cs2) * o->ig);
 }
 
 /* Isotropic first derivative on the flow lattice: d_beta phi(x) ~
@@ -524,7 +539,7 @@ static double d_iso(const orc* o, const double* phi, int x, int y, int z, int be
 static double body_force(const orc* o, long t) {
     double f = o->d.F0;
     if (o->p.force_amp != 0.0 && o->p.force_period > 0.0)
-        f *= 1.0 + o->p.force_amp * sin(2.0 * M_PI * (double)t / o->p.force_period);
+        f *= 1.0 + o->p.force_amp * sin(2.0 * M_PI * ((double)t * o->ig) / o->p.force_period);
     return f;
 }
 static int axis(const orc* o) { return o->p.dim == 3 ? 2 : 0; }
@@ -568,11 +583,14 @@ static double gzs(const orc* o, int i, long y) {
         uF += o->u[a][y] * o->F[a][y];
     }
     ciF = cF;
-    return (1.0 - 1.0 / (2.0 * o->d.tau)) * o->flow.w[i] * ((ciF - uF) / cs2 + cu * cF / (cs2 * cs2));
+    /* rescaled (Sec. V.I): [(c_i - u/gamma)/(gamma c_s^2) + (c_i . u) c_i/(gamma^2 c_s^4)] . F */
+    const double ig = o->ig, ig2 = o->ig * o->ig;
+    return (1.0 - 1.0 / (2.0 * o->d.tau)) * o->flow.w[i] *
+           ((ciF * ig - uF * ig2) / cs2 + cu * cF * ig2 / (cs2 * cs2));
 }
 
 /* Same forcing term for caller-given u and F (used to pin its moments). */
-void orc_gzs_terms(int dim, double tau, const double* u, const double* F, double* Fi, int* q_out,
+void orc_gzs_terms(int dim, double tau, double gamma, const double* u, const double* F, double* Fi, int* q_out,
                    int* c_out) {
     orc tmp;
     memset(&tmp, 0, sizeof(tmp));
@@ -588,7 +606,8 @@ void orc_gzs_terms(int dim, double tau, const double* u, const double* F, double
             uF += u[a] * F[a];
             c_out[3 * i + a] = tmp.flow.c[i][a];
         }
-        Fi[i] = (1.0 - 1.0 / (2.0 * tau)) * tmp.flow.w[i] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
+        const double ig = 1.0 / gamma, ig2 = ig * ig;
+        Fi[i] = (1.0 - 1.0 / (2.0 * tau)) * tmp.flow.w[i] * ((cF * ig - uF * ig2) / cs2 + cu * cF * ig2 / (cs2 * cs2));
     }
     *q_out = tmp.flow.q;
 }
@@ -614,7 +633,7 @@ static void flow_update(orc* o) {
             double corr = -0.5 * tau * (gzs(o, i, kp) - gzs(o, i, km));
             for (int a = 0; a < 3; ++a) m[a] += c[a] * mom + c[a] * corr;
         }
-        for (int a = 0; a < 3; ++a) m[a] += o->F[a][k];
+        for (int a = 0; a < 3; ++a) m[a] += o->F[a][k] * o->ig; /* F dt, dt = 1/gamma (R15) */
         o->rho_new[k] = rho;
         for (int a = 0; a < 3; ++a) o->u_new[a][k] = m[a] / rho;
     }
@@ -656,6 +675,8 @@ orc* orc_create(const orc_params* p) {
     o->p = *p;
     if (o->p.dim == 2) o->p.nz = 1;
     if (o->p.alpha == 0.0) o->p.alpha = 1.0;
+    if (!(o->p.gamma > 0.0)) o->p.gamma = 1.0;
+    o->ig = 1.0 / o->p.gamma;
     if (orc_derive(&o->p, &o->d) != 0) {
         free(o);
         return NULL;

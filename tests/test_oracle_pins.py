@@ -156,10 +156,13 @@ def test_explicit_ib_close_to_implicit_on_curved_wall():
 
 # ------------------------------------------------------------ forcing moments
 
+@pytest.mark.parametrize("gamma", [1.0, 2.5])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_gzs_moments(dim):
+def test_gzs_moments(dim, gamma):
     # Sec. V.A: sum F_i = 0, sum c_i F_i = (1-1/2tau) F,
-    # sum c_i c_i F_i = (1-1/2tau)(u F + F u), exactly on the lattice.
+    # sum c_i c_i F_i = (1-1/2tau)(u F + F u), exactly on the lattice.  With the
+    # time step rescaled (Sec. V.I) the first moment is (1-1/2tau) F/gamma and
+    # the second (1-1/2tau)(u F + F u)/gamma^2.
     rng = np.random.default_rng(7 + dim)
     for _ in range(20):
         tau = rng.uniform(0.51, 1.0)
@@ -167,22 +170,26 @@ def test_gzs_moments(dim):
         F = rng.uniform(-1e-3, 1e-3, 3)
         if dim == 2:
             u[2] = F[2] = 0.0
-        Fi, c = oracle.gzs_terms(dim, tau, u, F)
+        Fi, c = oracle.gzs_terms(dim, tau, u, F, gamma)
         k = 1 - 1 / (2 * tau)
         assert abs(Fi.sum()) < 1e-18
-        np.testing.assert_allclose(c.T @ Fi, k * F, rtol=1e-12, atol=1e-19)
+        np.testing.assert_allclose(c.T @ Fi, k * F / gamma, rtol=1e-12, atol=1e-19)
         second = np.einsum("ia,ib,i->ab", c, c, Fi)
-        np.testing.assert_allclose(second, k * (np.outer(u, F) + np.outer(F, u)), rtol=1e-11, atol=1e-19)
+        np.testing.assert_allclose(second, k * (np.outer(u, F) + np.outer(F, u)) / gamma**2, rtol=1e-11,
+                                   atol=1e-19)
 
 
 # --------------------------------------------------- closed forms of the scheme
 
-def test_channel_shear_mode_decays_at_discrete_rate():
+@pytest.mark.parametrize("gamma", [1.0, 2.0])
+def test_channel_shear_mode_decays_at_discrete_rate(gamma):
     # Ha = 0 channel, walls on nodes y = 0, 31 (Sec. III.C update): for a
     # unidirectional u_x(y) the update reduces to u <- u + nu lap_h u + F, so
     # the parabola F y (31 - y)/(2 nu) is steady and the mode sin(pi y/31)
-    # decays by exactly 1 - 4 nu sin^2(pi/62) per step.
-    p = W.hartmann_channel_2d(Ha=0.0, n_mag=1)
+    # decays by exactly 1 - 4 nu sin^2(pi/62) per step.  With the time step
+    # rescaled by gamma (Sec. V.I) a step carries nu/gamma and F/gamma: the
+    # same parabola, the mode decaying by 1 - 4 (nu/gamma) sin^2(pi/62).
+    p = W.hartmann_channel_2d(Ha=0.0, n_mag=1, gamma=gamma)
     o = oracle.Oracle(p)
     d = o.derived()
     nu, F = d["nu"], d["F0"]
@@ -196,18 +203,19 @@ def test_channel_shear_mode_decays_at_discrete_rate():
     n = 400
     o.step(n)
     rho, uu, b = o.state()
-    g = (1 - 4 * nu * math.sin(math.pi / 62) ** 2) ** n
+    g = (1 - 4 * nu / gamma * math.sin(math.pi / 62) ** 2) ** n
     want = parab + eps * g * np.sin(np.pi * y / 31)
     np.testing.assert_allclose(uu[0, 0], np.broadcast_to(want[:, None], (32, 64)), rtol=0, atol=1e-14)
     np.testing.assert_allclose(rho, 1.0, atol=1e-14)
     np.testing.assert_allclose(uu[1], 0.0, atol=1e-15)
 
 
-def test_uniform_flow_gains_exactly_the_body_force():
+@pytest.mark.parametrize("gamma", [1.0, 3.0])
+def test_uniform_flow_gains_exactly_the_body_force(gamma):
     # Uniform fields in a periodic box: every neighbour equilibrium equals the
     # local one, the discrete-effect correction vanishes and rho u gains F per
-    # step (Sec. V.A update); rho stays one.
-    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0)
+    # step (Sec. V.A update), F/gamma with the rescaled time step; rho stays one.
+    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0, gamma=gamma)
     o = oracle.Oracle(p)
     d = o.derived()
     u0 = np.array([0.01, -0.02, 0.005])
@@ -215,7 +223,7 @@ def test_uniform_flow_gains_exactly_the_body_force():
     o.set_state(rho=np.ones((4, 5, 6)), u=u, b=np.zeros_like(u), t=0)
     o.step(40)
     rho, uu, _ = o.state()
-    want = u0 + np.array([0.0, 0.0, 40 * d["F0"]])
+    want = u0 + np.array([0.0, 0.0, 40 * d["F0"] / gamma])
     for a in range(3):
         np.testing.assert_allclose(uu[a], want[a], rtol=1e-13, atol=1e-17)
     np.testing.assert_allclose(rho, 1.0, atol=1e-14)
@@ -276,17 +284,19 @@ def test_sweep_single_mode_amplification(alpha):
         np.testing.assert_allclose(bb[1], gain(k) * b[1], rtol=0, atol=1e-17)
 
 
-@pytest.mark.parametrize("alpha,sweeps", [(1.0, 3000), (0.75, 2250)])
-def test_sweep_fixed_point_is_discrete_qs_poisson_solution(alpha, sweeps):
+@pytest.mark.parametrize("alpha,sweeps,gamma", [(1.0, 3000, 1.0), (0.75, 2250, 1.0), (1.0, 3000, 4.0)])
+def test_sweep_fixed_point_is_discrete_qs_poisson_solution(alpha, sweeps, gamma):
     # Sec. V.G: iterated to convergence the sweep solves
     # eta lap b = div(u B^ext - B^ext u) (strict QS flux).  Compare with an FFT
     # solve of the same discrete operators (7-point Laplacian, central
     # divergence) on a periodic box without walls.  The accelerated sweep of
     # Sec. V.H (alpha = 3/4, the smallest value stable on D3Q7) reaches the
-    # same fixed point in 3/4 of the sweeps.
+    # same fixed point in 3/4 of the sweeps.  With the time step rescaled
+    # (gamma = 4) the sweep uses eta/gamma and the flux over gamma: the same
+    # fixed point.
     n = 12
     p = W.small_pipe(nx=n, ny=n, nz=n, geometry="none", diameter=10.0, Re=10.0, Ha=5.0, Rm=0.05,
-                     U0=0.05, strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0, alpha=alpha)
+                     U0=0.05, strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0, alpha=alpha, gamma=gamma)
     o = oracle.Oracle(p)
     d = o.derived()
     eta = d["eta"]
@@ -355,25 +365,27 @@ def _full_update_case(dim, **kw):
     return oracle.Oracle(p), shape
 
 
+@pytest.mark.parametrize("gamma", [1.0, 2.0])
 @pytest.mark.parametrize("dim", [3, 2])
-def test_time_resolved_update_single_mode_and_advection(dim):
+def test_time_resolved_update_single_mode_and_advection(dim, gamma):
     # With u = 0 the update multiplies cos(k x) by (2 tau_m - 1) g - 2 (tau_m - 1),
     # g the plain-sweep gain (3/4 + cos(k)/4 on D3Q7, 2/3 + cos(k)/3 on D2Q5).
     # With a uniform u_x = U, b_y = cos(k x) and no applied field, the flux
     # adds U sin(k) sin(k x) (the axis weight times the flux coefficient
     # 1/c_m^2 is 1/2 on both lattices: a central difference of U b): the
     # profile moves toward +x.
-    o, shape = _full_update_case(dim)
+    # (gamma: tau_m = eta/(gamma c_m^2) + 1/2 and the flux over gamma)
+    o, shape = _full_update_case(dim, gamma=gamma)
     d = o.derived()
     assert d["n_mag"] == 1 and d["c_mag"] == 1.0
     tm = d["tau_m"]
-    assert tm == pytest.approx(d["eta"] / d["cm2"] + 0.5, rel=1e-15)
+    assert tm == pytest.approx(d["eta"] / (gamma * d["cm2"]) + 0.5, rel=1e-15)
     g0 = (lambda k: 0.75 + 0.25 * math.cos(k)) if dim == 3 else (lambda k: 2 / 3 + math.cos(k) / 3)
     x = np.arange(12, dtype=float)
     k = 2 * np.pi * 2 / 12
     amp = (2 * tm - 1) * g0(k) - 2 * (tm - 1)
     for U in (0.0, 0.04):
-        o, shape = _full_update_case(dim)
+        o, shape = _full_update_case(dim, gamma=gamma)
         b = np.zeros((3,) + shape)
         b[1] = 1e-3 * np.cos(k * x)
         u = np.zeros((3,) + shape)
@@ -381,7 +393,7 @@ def test_time_resolved_update_single_mode_and_advection(dim):
         o.set_state(rho=np.ones(shape), u=u, b=b, t=0)
         o.mag_sweeps(1)
         _, _, bb = o.state()
-        want = 1e-3 * (amp * np.cos(k * x) + U * math.sin(k) * np.sin(k * x))
+        want = 1e-3 * (amp * np.cos(k * x) + U / gamma * math.sin(k) * np.sin(k * x))
         np.testing.assert_allclose(bb[1], np.broadcast_to(want, bb[1].shape), rtol=0, atol=1e-17)
         np.testing.assert_allclose(bb[0], 0.0, atol=1e-20)
         np.testing.assert_allclose(bb[2], 0.0, atol=1e-20)
