@@ -106,7 +106,8 @@ typedef struct qslbm_params {
     int32_t n_mag;          /* sweeps per step; 0 = min(ceil(2 eta / c_m^2), cap)  */
     int32_t n_mag_cap;      /* cap for the automatic count; <= 0 = no cap; 270     */
     double nu_ref;          /* IB reference viscosity; 0 = nu (lambda = 1)         */
-    double eta_ref;         /* IB reference resistivity; 0 = c_m^2 / 2             */
+    double eta_ref;         /* IB reference resistivity; 0 = c_m^2 / 2 (QS sweeps),
+                               eta (lambda_m = 1) for QSLBM_MAG_TIME              */
     int32_t precision;      /* QSLBM_FP32 (default) | QSLBM_FP64                   */
     int32_t strict_qs;      /* 1: induction flux from B^ext only; default 0        */
     uint64_t seed;          /* initial perturbation seed                           */
@@ -118,6 +119,10 @@ typedef struct qslbm_params {
                                1 (default; 0 also means 1) is the plain sweep; stable
                                for 1 - w_0 <= alpha <= 1 (3/4 in 3-D, 2/3 in 2-D) */
     int32_t mag_scheme;     /* QSLBM_MAG_QS (default) | QSLBM_MAG_TIME             */
+    double gamma;           /* time step rescaled to dt/gamma (Sec. V.I): equilibria,
+                               relaxation times and forcing rescaled; forces and
+                               resistivity per step over gamma; 1 (default; 0 also
+                               means 1); the body-force period is in physical time */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 

@@ -75,7 +75,8 @@
  *   R14 Time-resolved magnetic update (mag_scheme = 1): the field lattice runs
  *      at the flow's speed (c = 1, dx = dt = 1), so eta = c_m^2 (tau_m - 1/2),
  *      tau_m = eta/c_m^2 + 1/2, the flux coefficient is e_beta / c_m^2, and the
- *      update runs once per flow step, followed by the IB on b.
+ *      update runs once per flow step, followed by the IB on b, with
+ *      eta_ref = eta (lambda_m = 1) unless given, as for nu_ref in R7.
  *   R15 Rescaled time step (gamma): a step advances physical time by 1/gamma.
  *      Per step the forces (body and Lorentz, physical rates) add F/gamma to
  *      rho u, the body-force modulation runs on t/gamma, and the magnetic
@@ -269,7 +270,10 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     }
     d->n_mag = n;
     double nu_ref = p->nu_ref > 0 ? p->nu_ref : d->nu / g;
-    double eta_ref = p->eta_ref > 0 ? p->eta_ref : 0.5 * d->cm2;
+    /* eta_ref: c_m^2/2 for the tau_m = 1 sweeps (lambda_m = c); eta/gamma for
+     * the time-resolved update (lambda_m = 1, R14: below one the scaling's pole
+     * 1/(1 - lambda_m) falls inside the rings' range of d) */
+    double eta_ref = p->eta_ref > 0 ? p->eta_ref : (p->mag_scheme == 1 ? d->eta / g : 0.5 * d->cm2);
     d->lambda = d->nu / g / nu_ref;
     d->lambda_m = d->eta / g / eta_ref;
     return 0;

@@ -36,7 +36,7 @@ class qslbm_params(C.Structure):
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
         ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double),
-        ("mag_scheme", C.c_int32), ("stream", C.c_void_p),
+        ("mag_scheme", C.c_int32), ("gamma", C.c_double), ("stream", C.c_void_p),
     ]
 
 
@@ -203,6 +203,7 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.sweep_kernel = SWEEP_KERNEL[k] if isinstance(k, str) else int(k)
     q.alpha = float(p.get("alpha", 1.0))
     q.mag_scheme = int(p.get("mag_scheme", 0))
+    q.gamma = float(p.get("gamma", 1.0))
     q.stream = stream
     return q
 

@@ -90,11 +90,12 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     }
     u.U0 = U0;
     u.nu = U0 * u.R / p.Re;
-    u.tau = u.nu / u.cs2 + 0.5;
+    const double g = p.gamma > 0 ? p.gamma : 1.0;  // time step dt/gamma (Sec. V.I)
+    u.tau = u.nu / (g * u.cs2) + 0.5;
     u.eta = U0 * u.R / p.Rm;
     u.B0 = p.Ha * std::sqrt(u.eta * u.nu) / u.R;
     u.F0 = (p.geometry == QSLBM_CHANNEL ? 2.0 : 4.0) * u.nu * U0 / (u.R * u.R);
-    u.c_mag = 2.0 * u.eta / u.cm2;
+    u.c_mag = 2.0 * u.eta / (g * u.cm2);
     u.tau_m = 1.0;
     int n = p.n_mag > 0 ? p.n_mag : ceil_rel(u.c_mag);
     if (p.n_mag <= 0 && p.n_mag_cap > 0) n = std::min(n, p.n_mag_cap);
@@ -102,13 +103,16 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     if (p.mag_scheme == QSLBM_MAG_TIME) {
         // the field lattice at the flow's speed: eta = c_m^2 (tau_m - 1/2)
         u.c_mag = 1.0;
-        u.tau_m = u.eta / u.cm2 + 0.5;
+        u.tau_m = u.eta / (g * u.cm2) + 0.5;
         u.n_mag = 1;
     }
-    double nu_ref = p.nu_ref > 0 ? p.nu_ref : u.nu;
-    double eta_ref = p.eta_ref > 0 ? p.eta_ref : 0.5 * u.cm2;
-    u.lambda = u.nu / nu_ref;
-    u.lambda_m = u.eta / eta_ref;
+    double nu_ref = p.nu_ref > 0 ? p.nu_ref : u.nu / g;
+    // eta_ref: c_m^2/2 for the tau_m = 1 sweeps (lambda_m = c); the per-step
+    // eta for the time-resolved update (lambda_m = 1: below one the scaling's
+    // pole at d = 1/(1 - lambda_m) falls inside the rings' range of d)
+    double eta_ref = p.eta_ref > 0 ? p.eta_ref : (p.mag_scheme == QSLBM_MAG_TIME ? u.eta / g : 0.5 * u.cm2);
+    u.lambda = u.nu / g / nu_ref;
+    u.lambda_m = u.eta / g / eta_ref;
     return QSLBM_OK;
 }
 
@@ -134,6 +138,7 @@ int validate(const qslbm_params& p) {
         if (!(a >= 1.0 - w0 - 1e-12 && a <= 1.0)) return QSLBM_EINVAL;
         if (p.mag_scheme != QSLBM_MAG_QS && p.mag_scheme != QSLBM_MAG_TIME) return QSLBM_EINVAL;
         if (p.mag_scheme == QSLBM_MAG_TIME && a != 1.0) return QSLBM_EINVAL;
+        if (!(p.gamma >= 0.0) || p.gamma > 1e6) return QSLBM_EINVAL;
     }
     if (p.mag_scheme == QSLBM_MAG_TIME) {
         // checkerboard gain (2 tau_m - 1)(2 w_0 - 1) - 2 (tau_m - 1) >= -1
@@ -435,7 +440,9 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
     s.cy = std::isnan(s.p.center[1]) ? 0.5 * (s.ny - 1) : s.p.center[1];
     s.R = s.units.R;
     s.axis = s.dim == 3 ? 2 : 0;
-    s.omega = s.p.force_amp != 0.0 ? 2.0 * M_PI / s.p.force_period : 0.0;
+    s.ig = 1.0 / (s.p.gamma > 0 ? s.p.gamma : 1.0);
+    // the modulation runs on physical time t/gamma
+    s.omega = s.p.force_amp != 0.0 ? 2.0 * M_PI / s.p.force_period * s.ig : 0.0;
     if (s.dim == 3) {
         s.w0 = 0.25;
         s.alpha = s.p.alpha == 0.0 ? 1.0 : s.p.alpha;

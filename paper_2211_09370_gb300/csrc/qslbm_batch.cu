@@ -296,6 +296,8 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     D.fc.bext_z = (const T*)s.bext_z;
     D.flc.tau = (T)s.units.tau;
     D.flc.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+    D.flc.ig = (T)s.ig;
+    D.flc.ig2 = (T)(s.ig * s.ig);
     for (int m = 0; m < 2; ++m) {
         qslbm::IBView<T>& v = m ? D.ibu : D.ibm;
         v.ring_off = s.ib.ring_off;

@@ -49,6 +49,7 @@ struct State {
     double cx = 0, cy = 0, R = 0;
     double w0 = 0, w1 = 0, kappa = 0;  // field lattice weights, 1/(2 eta)
     double alpha = 1.0;                // accelerated-sweep coefficient (1: plain sweep)
+    double ig = 1.0;                   // 1/gamma: the time step in physical time
     double be[3] = {0, 0, 0};          // uniform B^ext
     int axis = 2;                      // body-force direction
     double omega = 0;                  // 2 pi / period
@@ -91,13 +92,14 @@ struct State {
 //     is (2 tau_m - 1) times the plain neighbour sum of b, plus the plain flux
 //     sum, minus 2 (tau_m - 1) b, since the flux terms of g_i(x + e_i) are
 //     those of g_i(x - e_i) with the sign reversed and sum_i g_i(x) = b.
-// At alpha = 1 and tau_m = 1 every weight is exactly the plain one.
+// With the time step rescaled by gamma (Sec. V.I) the flux carries 1/gamma.
+// At alpha = 1, tau_m = 1 and gamma = 1 every weight is exactly the plain one.
 template <typename T>
 inline void sweep_weights(const State& s, T& w0, T& w1, T& kappa) {
     const double tm = s.units.tau_m, a = s.alpha;
     w0 = (T)(((2.0 * tm - 1.0) * s.w0 - 2.0 * (tm - 1.0) + (a - 1.0)) / a);
     w1 = (T)((2.0 * tm - 1.0) * s.w1 / a);
-    kappa = (T)(s.kappa / (2.0 * tm - 1.0));
+    kappa = (T)(s.kappa / (2.0 * tm - 1.0) * s.ig);  // flux over gamma (Sec. V.I)
 }
 
 // Kernel launchers, one table per storage precision.

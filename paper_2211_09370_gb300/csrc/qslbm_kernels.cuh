@@ -78,6 +78,7 @@ template <typename T>
 struct FlowCoef {
     T tau;        // relaxation time
     T kforce;     // 1 - 1/(2 tau)
+    T ig, ig2;    // 1/gamma, 1/gamma^2 (time step rescaled, Sec. V.I; 1 by default)
 };
 
 template <typename T>
@@ -910,7 +911,7 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
     const T dr0 = drho[k];
     const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
     const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
-    const T q0 = T(-1.5) * uu0;
+    const T q0 = T(-1.5) * uu0 * c.ig;
     const T w0 = (T)flow_w<DIM>(0);
     T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
     T m[3] = {T(0), T(0), T(0)};
@@ -931,13 +932,13 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
         const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
         const T uF = uq[0] * Fq[0] + uq[1] * Fq[1] + uq[2] * Fq[2];
         const T w = (T)flow_w<DIM>(j);
-        const T sq = T(4.5) * a * a - T(1.5) * uu;
+        const T sq = (T(4.5) * a * a - T(1.5) * uu) * c.ig;
         const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
         const T fj = w * (dr + qp + dr * qp);
         const T fjb = w * (dr + qm + dr * qm);
         rho_acc += T(0.5) * fj + T(1.5) * fjb;
         const T mom = tm1 * fj - tau * fjb;
-        const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF);
+        const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF) * c.ig2;
         if (cx) {
             m[0] += (T)cx * mom;
             corr[0] += (T)cx * fs;
@@ -959,7 +960,7 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
     drho_out[k] = rho_acc;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const T mm = m[a] - T(2) * tm1 * rho0 * u0v[a] - half_tau * corr[a] + Fk[a];
+        const T mm = m[a] - T(2) * tm1 * rho0 * u0v[a] - half_tau * corr[a] + Fk[a] * c.ig;
         uout[k + a * n] = mm * inv;
     }
 }

@@ -281,6 +281,8 @@ struct Launch {
         FlowCoef<T> c;
         c.tau = (T)s.units.tau;
         c.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+        c.ig = (T)s.ig;
+        c.ig2 = (T)(s.ig * s.ig);
         const IBView<T> v = view(s, false);
         const T* b = (const T*)s.b[s.bcur];
         const T* dr = (const T*)s.drho[s.fcur];

@@ -180,6 +180,28 @@ def test_time_resolved_update_parity_2d_channel():
     check_fields(got, want, "fp64", "channel time-resolved")
 
 
+GAMMA_CASES = {
+    # time step rescaled by gamma (Sec. V.I): quasi-static sweeps, gamma = 2
+    "qs_ramp": (dict(nx=24, ny=22, nz=10, diameter=16.0, U0=0.05, Re=50.0, Ha=20.0, Rm=0.05, b0_kind="tanh",
+                     ramp_center=5.0, ramp_width=2.0, perturb=0.0, n_mag=30, force_amp=0.2, force_period=40.0,
+                     gamma=2.0), 40),
+    # Pr_m = 4 as in the paper's example (nu = 0.08, eta = 0.02), gamma = 4, time-resolved
+    # update; U0 = 0.02 keeps the cell Peclet number U0 / eta at one
+    "time_prm4": (dict(nx=22, ny=20, nz=8, diameter=16.0, U0=0.02, Re=2.0, Ha=6.0, Rm=8.0, perturb=0.0,
+                       mag_scheme=1, gamma=4.0), 60),
+}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(GAMMA_CASES))
+def test_rescaled_time_step_parity(name, precision, kernel):
+    kw, steps = GAMMA_CASES[name]
+    p = W.small_pipe(precision=precision, sweep_kernel=kernel, **kw)
+    got, want, o = run_both(p, steps)
+    check_fields(got, want, precision, name)
+
+
 def test_observables_match_oracle_fp64():
     p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
