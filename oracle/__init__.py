@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 GEOMETRY = {"channel": 0, "pipe": 1, "none": 2}
-B0_KIND = {"uniform": 0, "tanh": 1}
+B0_KIND = {"uniform": 0, "tanh": 1, "field": 2}
 
 
 class _Params(C.Structure):
@@ -38,7 +38,7 @@ class _Params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
-        ("mag_scheme", C.c_int), ("gamma", C.c_double),
+        ("mag_scheme", C.c_int), ("gamma", C.c_double), ("b0_field", C.c_void_p),
     ]
 
 
@@ -134,6 +134,10 @@ def make_params(p: dict) -> _Params:
     q.alpha = float(p.get("alpha", 1.0))
     q.mag_scheme = int(p.get("mag_scheme", 0))
     q.gamma = float(p.get("gamma", 1.0))
+    f = p.get("b0_field")
+    if f is not None:  # copied by orc_create; the array only has to outlive the call
+        q._field = np.ascontiguousarray(f, dtype=np.float64)
+        q.b0_field = q._field.ctypes.data
     return q
 
 

@@ -96,6 +96,7 @@
 
 #define ORC_B0_UNIFORM 0
 #define ORC_B0_TANH 1
+#define ORC_B0_FIELD 2 /* B0 times a caller-given in-plane field [3][ny][nx] */
 
 typedef struct orc_params {
     int dim, nx, ny, nz, geometry;
@@ -112,6 +113,7 @@ typedef struct orc_params {
     double alpha; /* accelerated sweep (Sec. V.H); 0 means 1, the plain sweep */
     int mag_scheme; /* 0: quasi-static sweeps (tau_m = 1); 1: one update per step (R14) */
     double gamma;   /* time-step rescaling (Sec. V.I); 0 means 1 */
+    const double* b0_field; /* ORC_B0_FIELD: [3][ny][nx], copied at creation */
 } orc_params;
 
 typedef struct orc_derived {
@@ -138,6 +140,7 @@ typedef struct orc {
     long t, tsnap;
     double mass0;
     double ig; /* 1/gamma */
+    double* b0f; /* ORC_B0_FIELD: [3][ny][nx] */
     int nm;
     double *X, *Y, *Z, *dj, *sj, *smj;
 } orc;
@@ -211,8 +214,11 @@ uint64_t orc_splitmix64(uint64_t x) {
 /* Applied field B^ext at node (x, y, z): uniform B0 * dir, or the ramp
  * B0 * 0.5 (1 + tanh((z - zc)/w)) * dir along the pipe axis (Sec. VI). */
 static void bext(const orc* o, int x, int y, int z, double B[3]) {
-    (void)x;
-    (void)y;
+    if (o->p.b0_kind == ORC_B0_FIELD) { /* a z-invariant field, e.g. of magnets (Sec. VI) */
+        long P = (long)o->p.nx * o->p.ny, q = (long)y * o->p.nx + x;
+        for (int a = 0; a < 3; ++a) B[a] = o->d.B0 * o->b0f[a * P + q];
+        return;
+    }
     double amp = o->d.B0;
     if (o->p.b0_kind == ORC_B0_TANH) amp = o->d.B0 * 0.5 * (1.0 + tanh(((double)z - o->p.ramp_center) / o->p.ramp_width));
     for (int a = 0; a < 3; ++a) B[a] = amp * o->p.b0_dir[a];
@@ -686,6 +692,17 @@ orc* orc_create(const orc_params* p) {
         return NULL;
     }
     make_lattices(o);
+    if (o->p.b0_kind == ORC_B0_FIELD) {
+        long P = (long)o->p.nx * o->p.ny;
+        o->b0f = malloc(3 * P * sizeof(double));
+        if (!o->b0f || !o->p.b0_field) {
+            free(o->b0f);
+            free(o);
+            return NULL;
+        }
+        memcpy(o->b0f, o->p.b0_field, 3 * P * sizeof(double));
+        o->p.b0_field = NULL;
+    }
     o->n = (long)o->p.nx * o->p.ny * o->p.nz;
     long n = o->n;
     o->rho = calloc(n, sizeof(double));
@@ -726,6 +743,7 @@ orc* orc_create(const orc_params* p) {
 
 void orc_destroy(orc* o) {
     if (!o) return;
+    free(o->b0f);
     free(o->rho);
     free(o->rho_new);
     for (int a = 0; a < 3; ++a) {

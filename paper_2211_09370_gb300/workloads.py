@@ -6,8 +6,8 @@ parity tests use.  Both the CUDA library and the CPU oracle receive these
 dictionaries; each side maps them to lattice units on its own.
 
 Keys: dim, nx, ny, nz, geometry ('channel' | 'pipe'), diameter, center,
-marker_spacing, Re, Ha, Rm, U0 (0 = automatic), b0_kind ('uniform' | 'tanh'),
-b0_dir, ramp_center, ramp_width, force_amp, force_period, n_mag (0 = automatic),
+marker_spacing, Re, Ha, Rm, U0 (0 = automatic), b0_kind ('uniform' | 'tanh' |
+'field'), b0_dir, ramp_center, ramp_width, b0_field ([3][ny][nx] for 'field'), force_amp, force_period, n_mag (0 = automatic),
 n_mag_cap (0 = no cap), nu_ref, eta_ref, precision ('fp32' | 'fp64'), seed,
 perturb, steps (horizon of the workload).
 """
@@ -15,6 +15,8 @@ from __future__ import annotations
 
 import math
 import random
+
+import numpy as np
 
 NAN2 = (float("nan"), float("nan"))
 
@@ -116,3 +118,48 @@ def nodes(p: dict) -> int:
 
 def isclose(a, b):
     return math.isclose(a, b, rel_tol=1e-12)
+
+
+def six_magnet_field(nx, ny, diameter, center=None, gap=2.0, half_width=None):
+    """Applied field of six slab magnets with alternating poles on a hexagon
+    around the pipe (the non-uniform-field configuration of Sec. VI), as an
+    in-plane array [3][ny][nx] (the z component of the pipe frame is zero).
+
+    Each magnet's field in its own frame (y' along its face, z' from its face
+    toward the pipe axis) is the Biot-Savart field of a slab of half width L:
+    B_y' = 2 [atan((y' - L)/z') - atan((y' + L)/z')],
+    B_z' = log(((y' + L)^2 + z'^2) / ((y' - L)^2 + z'^2)), L = R/6.  The faces
+    sit at R + gap from the axis at angles k pi/3; pole signs alternate; the sum
+    is scaled to max |B| = 1 inside the pipe.  Outside the pipe z' is kept
+    >= 1/2 (those nodes are computed but not physical)."""
+    R = 0.5 * float(diameter)
+    if center is None:
+        center = ((nx - 1) / 2.0, (ny - 1) / 2.0)
+    L = R / 6.0 if half_width is None else float(half_width)
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    B = magnet_ring_at(x - center[0], y - center[1], R, gap, L)
+    inside = (x - center[0]) ** 2 + (y - center[1]) ** 2 <= R * R
+    scale = np.sqrt(B[0] ** 2 + B[1] ** 2)[inside].max()
+    return np.stack([B[0] / scale, B[1] / scale, np.zeros_like(x)])
+
+
+def magnet_ring_at(X, Y, R, gap, L):
+    """Unscaled field (B_x, B_y) of the six-magnet ring at offsets (X, Y) from
+    the pipe axis (see six_magnet_field)."""
+    X = np.asarray(X, dtype=float)
+    Y = np.asarray(Y, dtype=float)
+    Bx = np.zeros_like(X)
+    By = np.zeros_like(X)
+    for k in range(6):
+        th = k * math.pi / 3.0
+        nxk, nyk = math.cos(th), math.sin(th)  # outward normal of magnet k
+        txk, tyk = -nyk, nxk                    # along its face
+        zp = np.maximum((R + gap) - (X * nxk + Y * nyk), 0.5)
+        yp = X * txk + Y * tyk
+        b_t = 2.0 * (np.arctan((yp - L) / zp) - np.arctan((yp + L) / zp))
+        b_n = np.log(((yp + L) ** 2 + zp ** 2) / ((yp - L) ** 2 + zp ** 2))
+        sgn = -1.0 if k % 2 else 1.0
+        # z' points inward, along -normal
+        Bx += sgn * (b_t * txk - b_n * nxk)
+        By += sgn * (b_t * tyk - b_n * nyk)
+    return Bx, By

@@ -407,6 +407,48 @@ def test_time_resolved_update_stability_bound():
         assert (2 * tmax - 1) * (2 * w0 - 1) - 2 * (tmax - 1) == pytest.approx(-1.0, abs=1e-15)
 
 
+# -------------------------------------------------------- applied field kinds
+
+def test_six_magnet_field_is_a_potential_field_with_hexagonal_symmetry():
+    # The Biot-Savart field of the slab magnets (Sec. VI) is divergence- and
+    # curl-free inside the pipe, and the ring of six magnets with alternating
+    # poles maps to minus itself under a rotation by 60 degrees.
+    R, gap = 20.0, 2.0
+    L = R / 6
+    rng = np.random.default_rng(1)
+    r = R * np.sqrt(rng.uniform(0, 0.9, 200))
+    th = rng.uniform(0, 2 * np.pi, 200)
+    X, Y = r * np.cos(th), r * np.sin(th)
+    e = 1e-4
+    f = lambda X, Y: np.array(W.magnet_ring_at(X, Y, R, gap, L))  # noqa: E731
+    B = f(X, Y)
+    dx = (f(X + e, Y) - f(X - e, Y)) / (2 * e)
+    dy = (f(X, Y + e) - f(X, Y - e)) / (2 * e)
+    scale = np.hypot(*B).max() / R
+    assert np.abs(dx[0] + dy[1]).max() < 1e-7 * scale
+    assert np.abs(dx[1] - dy[0]).max() < 1e-7 * scale
+    c, s = math.cos(math.pi / 3), math.sin(math.pi / 3)
+    Br = f(c * X - s * Y, s * X + c * Y)
+    np.testing.assert_allclose(Br[0], -(c * B[0] - s * B[1]), atol=1e-12)
+    np.testing.assert_allclose(Br[1], -(s * B[0] + c * B[1]), atol=1e-12)
+    F = W.six_magnet_field(48, 48, 2 * R)
+    assert F.shape == (3, 48, 48) and np.all(F[2] == 0.0)
+
+
+def test_field_kind_with_a_uniform_array_is_the_uniform_field():
+    # b0_kind = 'field' with the array (1, 0, 0) everywhere gives bitwise the
+    # run with the uniform field B0 along x.
+    kw = dict(nx=14, ny=12, nz=5, diameter=9.0, perturb=0.05, n_mag=15)
+    a = oracle.Oracle(W.small_pipe(precision="fp64", **kw))
+    field = np.zeros((3, 12, 14))
+    field[0] = 1.0
+    b = oracle.Oracle(W.small_pipe(precision="fp64", b0_kind="field", b0_field=field, **kw))
+    a.step(3)
+    b.step(3)
+    for x, y in zip(a.state(), b.state()):
+        np.testing.assert_array_equal(x, y)
+
+
 # --------------------------------------------------- converged physical flows
 
 @pytest.fixture(scope="module")
