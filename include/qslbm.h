@@ -59,6 +59,8 @@ extern "C" {
 
 #define QSLBM_B0_UNIFORM 0 /* B^ext = B0 * b0_dir                              */
 #define QSLBM_B0_TANH 1    /* B^ext = B0 * 0.5 (1 + tanh((z - zc)/w)) * b0_dir  */
+#define QSLBM_B0_FIELD 2   /* B^ext = B0 * b0_field(x, y): a z-invariant in-plane
+                              field, e.g. of magnets around the pipe (Sec. VI)   */
 
 #define QSLBM_FP32 0
 #define QSLBM_FP64 1
@@ -97,7 +99,7 @@ typedef struct qslbm_params {
     double marker_spacing;  /* Lagrangian marker spacing; default 1.0              */
     double Re, Ha, Rm;      /* L = D/2; Ha = B0 L / sqrt(eta nu)                   */
     double U0;              /* velocity scale; 0 = min(0.05, Re/(6L), Re L/(2Ha^2)) */
-    int32_t b0_kind;        /* QSLBM_B0_UNIFORM | QSLBM_B0_TANH                    */
+    int32_t b0_kind;        /* QSLBM_B0_UNIFORM | QSLBM_B0_TANH | QSLBM_B0_FIELD    */
     double b0_dir[3];       /* unit direction of B^ext; default (1, 0, 0)          */
     double ramp_center;     /* zc of the tanh ramp                                 */
     double ramp_width;      /* w of the tanh ramp                                  */
@@ -123,6 +125,8 @@ typedef struct qslbm_params {
                                relaxation times and forcing rescaled; forces and
                                resistivity per step over gamma; 1 (default; 0 also
                                means 1); the body-force period is in physical time */
+    const double* b0_field; /* QSLBM_B0_FIELD: [3][ny][nx] binary64, read (copied) by
+                               qslbm_create only; NULL otherwise                 */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 

@@ -17,12 +17,12 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUDGET, ENOTFOUND, EARCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
 CHANNEL, PIPE, PERIODIC = 0, 1, 2
-B0_UNIFORM, B0_TANH = 0, 1
+B0_UNIFORM, B0_TANH, B0_FIELD = 0, 1, 2
 FP32, FP64 = 0, 1
 SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT, SWEEP_SPLIT = 0, 1, 2, 3
 SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT, "split": SWEEP_SPLIT}
 GEOMETRY = {"channel": CHANNEL, "pipe": PIPE, "none": PERIODIC, "periodic": PERIODIC}
-B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH}
+B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH, "field": B0_FIELD}
 PRECISION = {"fp32": FP32, "fp64": FP64}
 
 
@@ -36,7 +36,7 @@ class qslbm_params(C.Structure):
         ("n_mag", C.c_int32), ("n_mag_cap", C.c_int32), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
         ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double),
-        ("mag_scheme", C.c_int32), ("gamma", C.c_double), ("stream", C.c_void_p),
+        ("mag_scheme", C.c_int32), ("gamma", C.c_double), ("b0_field", C.c_void_p), ("stream", C.c_void_p),
     ]
 
 
@@ -204,6 +204,10 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.alpha = float(p.get("alpha", 1.0))
     q.mag_scheme = int(p.get("mag_scheme", 0))
     q.gamma = float(p.get("gamma", 1.0))
+    f = p.get("b0_field")
+    if f is not None:  # read by qslbm_create; the array only has to outlive that call
+        q._field = np.ascontiguousarray(f, dtype=np.float64)
+        q.b0_field = q._field.ctypes.data
     q.stream = stream
     return q
 

@@ -123,7 +123,8 @@ int validate(const qslbm_params& p) {
     if (p.geometry < QSLBM_CHANNEL || p.geometry > QSLBM_PERIODIC) return QSLBM_EINVAL;
     if (!(p.diameter > 0) || !(p.Re > 0) || !(p.Rm > 0) || !(p.Ha >= 0)) return QSLBM_EINVAL;
     if (!(p.marker_spacing > 0)) return QSLBM_EINVAL;
-    if (p.b0_kind != QSLBM_B0_UNIFORM && p.b0_kind != QSLBM_B0_TANH) return QSLBM_EINVAL;
+    if (p.b0_kind != QSLBM_B0_UNIFORM && p.b0_kind != QSLBM_B0_TANH && p.b0_kind != QSLBM_B0_FIELD) return QSLBM_EINVAL;
+    if (p.b0_kind == QSLBM_B0_FIELD && !p.b0_field) return QSLBM_EINVAL;
     if (p.b0_kind == QSLBM_B0_TANH && !(p.ramp_width > 0)) return QSLBM_EINVAL;
     if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
     if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
@@ -453,7 +454,7 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         s.w1 = 1.0 / 6.0;
     }
     s.kappa = 1.0 / (s.units.c_mag * s.units.cm2);
-    for (int a = 0; a < 3; ++a) s.be[a] = s.units.B0 * s.p.b0_dir[a];
+    for (int a = 0; a < 3; ++a) s.be[a] = s.p.b0_kind == QSLBM_B0_FIELD ? 0.0 : s.units.B0 * s.p.b0_dir[a];
     if ((rc = build_markers(s))) {
         delete h;
         return rc;
@@ -492,6 +493,13 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         }
         if ((rc = upload_real(s, &s.bext_z, s.bext_host))) goto fail;
     }
+    if (s.p.b0_kind == QSLBM_B0_FIELD) {
+        const size_t P = (size_t)s.nx * s.ny;
+        std::vector<double> f(3 * P);
+        for (size_t i = 0; i < 3 * P; ++i) f[i] = s.units.B0 * s.p.b0_field[i];
+        if ((rc = upload_real(s, &s.bext_xy, f))) goto fail;
+    }
+    s.p.b0_field = nullptr;  // the caller's array is not kept
     if ((rc = upload_ib(s))) goto fail;
     if (s.p.sweep_kernel == QSLBM_SWEEP_AUTO || s.p.sweep_kernel == QSLBM_SWEEP_RESIDENT) {
         cudaError_t e = ops(s).plan_resident(s);

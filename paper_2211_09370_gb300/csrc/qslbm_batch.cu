@@ -286,6 +286,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     sweep_weights(s, D.sc.w0, D.sc.w1, D.sc.kappa);
     for (int a = 0; a < 3; ++a) D.sc.be[a] = (T)s.be[a];
     D.sc.bext_z = (const T*)s.bext_z;
+    D.sc.bext_xy = (const T*)s.bext_xy;
     D.sc.strict_qs = s.p.strict_qs;
     D.sc.sq = s.p.strict_qs ? T(0) : T(1);
     D.fc.F0 = s.units.F0;
@@ -294,6 +295,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     D.fc.axis = s.axis;
     for (int a = 0; a < 3; ++a) D.fc.be[a] = (T)s.be[a];
     D.fc.bext_z = (const T*)s.bext_z;
+    D.fc.bext_xy = (const T*)s.bext_xy;
     D.flc.tau = (T)s.units.tau;
     D.flc.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
     D.flc.ig = (T)s.ig;

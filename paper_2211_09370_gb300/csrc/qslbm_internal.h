@@ -55,6 +55,7 @@ struct State {
     double omega = 0;                  // 2 pi / period
     void *drho[2] = {nullptr, nullptr}, *u[2] = {nullptr, nullptr}, *b[2] = {nullptr, nullptr};
     void *F = nullptr, *usnap = nullptr, *bext_z = nullptr;
+    void* bext_xy = nullptr;  // [3][nx ny] B0 times the in-plane applied field (QSLBM_B0_FIELD)
     long long* tdev = nullptr;
     double *partial = nullptr, *obs_dev = nullptr, *staging = nullptr;
     int nblocks_obs = 0;

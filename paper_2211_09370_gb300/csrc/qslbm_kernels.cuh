@@ -71,6 +71,7 @@ struct SweepCoef {
     const T* bext_z;  // [3 * nz] B^ext per plane for the ramp, or nullptr
     int strict_qs;
     T sq;          // weight of b in the flux's B: 1, or 0 for the strict QS flux
+    const T* bext_xy;  // [3][nx ny] in-plane applied field (QSLBM_B0_FIELD), or nullptr
 };
 
 // Coefficients of the flow update (Sec. III.E, V.A).
@@ -87,6 +88,7 @@ struct ForceCoef {
     int axis;               // direction of the body force
     T be[3];
     const T* bext_z;
+    const T* bext_xy;  // [3][nx ny] in-plane applied field, or nullptr
 };
 
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
@@ -103,6 +105,16 @@ __device__ __forceinline__ void bext_at(const T* bext_z, const T* be, int z, T o
         out[0] = be[0];
         out[1] = be[1];
         out[2] = be[2];
+    }
+}
+
+// Adds the in-plane applied field of node p (QSLBM_B0_FIELD) to a plane's value.
+template <typename T>
+__device__ __forceinline__ void bext_add_xy(const T* bxy, int P, int p, T out[3]) {
+    if (bxy) {
+        out[0] += bxy[p];
+        out[1] += bxy[P + p];
+        out[2] += bxy[2 * P + p];
     }
 }
 
@@ -204,9 +216,11 @@ __device__ __forceinline__ void sweep_node(const T* __restrict__ bin, const T* _
         for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
         const T uq[3] = {u0[q], u1[q], u2[q]};
         const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
+        T Bx[3] = {bez[0], bez[1], bez[2]};
+        bext_add_xy(c.bext_xy, nx * ny, d < 4 ? q - base : p, Bx);
         T B[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
+        for (int a = 0; a < 3; ++a) B[a] = Bx[a] + c.sq * bq[a];
         // x - e_beta enters with +, x + e_beta with -
         flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
     }
@@ -371,10 +385,13 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
         if constexpr (EMF) {
             T be[3];
             bext_at(c.bext_z, c.be, zm, be);
+            bext_add_xy(c.bext_xy, P, p, be);
             node_emf(prv, be, c.sq);
             bext_at(c.bext_z, c.be, z0, be);
+            bext_add_xy(c.bext_xy, P, p, be);
             node_emf(cur, be, c.sq);
             bext_at(c.bext_z, c.be, zn, be);
+            bext_add_xy(c.bext_xy, P, p, be);
             node_emf(nxt, be, c.sq);
         }
     }
@@ -396,6 +413,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             if constexpr (EMF) {
                 T be[3];
                 bext_at(c.bext_z, c.be, z, be);
+                bext_add_xy(c.bext_xy, P, hp, be);
                 node_emf(r, be, c.sq);
             }
 #pragma unroll
@@ -446,9 +464,15 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
                     const T* bez = (d < 4) ? be_c : (d == 4 ? be_m : be_p);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
+                    T Bx[3] = {bez[0], bez[1], bez[2]};
+                    if (c.bext_xy) {
+                        const int xq = d == 0 ? wrap_dec(xc, nx) : d == 1 ? wrap_inc(xc, nx) : xc;
+                        const int yq = d == 2 ? wrap_dec(yc, ny) : d == 3 ? wrap_inc(yc, ny) : yc;
+                        bext_add_xy(c.bext_xy, P, yq * nx + xq, Bx);
+                    }
                     T B[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) B[a] = bez[a] + c.sq * bq[a];
+                    for (int a = 0; a < 3; ++a) B[a] = Bx[a] + c.sq * bq[a];
                     flux_acc(uq, B, d >> 1, (d & 1) ? T(-1) : T(1), diff);
                 }
 #pragma unroll
@@ -465,6 +489,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             if constexpr (EMF) {
                 T be[3];
                 bext_at(c.bext_z, c.be, za, be);
+                bext_add_xy(c.bext_xy, P, p, be);
                 node_emf(ahd, be, c.sq);
             }
 #pragma unroll
@@ -524,11 +549,11 @@ __device__ __forceinline__ void pair_halo(int hid, int x0, int y0, int nx, int n
     gp = gy * nx + gx;
 }
 
-__device__ __forceinline__ void pair_emf(float2 r[6], const float be[3], float sq) {
+__device__ __forceinline__ void pair_emf(float2 r[6], const float beA[3], const float beB[3], float sq) {
     float a[6] = {r[0].x, r[1].x, r[2].x, r[3].x, r[4].x, r[5].x};
     float b[6] = {r[0].y, r[1].y, r[2].y, r[3].y, r[4].y, r[5].y};
-    node_emf(a, be, sq);
-    node_emf(b, be, sq);
+    node_emf(a, beA, sq);
+    node_emf(b, beB, sq);
 #pragma unroll
     for (int v = 0; v < 6; ++v) r[v] = make_float2(a[v], b[v]);
 }
@@ -562,6 +587,15 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
             for (int v = 0; v < 6; ++v) h[v] = make_float2(src[v][zz * P + hp], 0.f);
         }
     };
+    // (b, u) -> (b, e) of the nodes pp and pp + 1 of plane zz
+    auto emf2 = [&](float2 r[6], int zz, int pp) {
+        float be[3];
+        bext_at(c.bext_z, c.be, zz, be);
+        float bA[3] = {be[0], be[1], be[2]}, bB[3] = {be[0], be[1], be[2]};
+        bext_add_xy(c.bext_xy, P, pp, bA);
+        bext_add_xy(c.bext_xy, P, pp + 1 < P ? pp + 1 : pp, bB);
+        pair_emf(r, bA, bB, c.sq);
+    };
     float2 prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
     {
         const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
@@ -572,13 +606,9 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
             nxt[v] = ld2(src[v] + zn * P + p);
         }
         load_halo(z0, hcur);
-        float be[3];
-        bext_at(c.bext_z, c.be, zm, be);
-        pair_emf(prv, be, c.sq);
-        bext_at(c.bext_z, c.be, z0, be);
-        pair_emf(cur, be, c.sq);
-        bext_at(c.bext_z, c.be, zn, be);
-        pair_emf(nxt, be, c.sq);
+        emf2(prv, zm, p);
+        emf2(cur, z0, p);
+        emf2(nxt, zn, p);
     }
     const float w0 = c.w0, w1 = c.w1, w1k = c.w1 * c.kappa;
     const int r = ty + 1, cc = 2 + 2 * tx;
@@ -595,9 +625,7 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
 #pragma unroll
         for (int v = 0; v < 6; ++v) *reinterpret_cast<float2*>(&t[v][r][cc]) = cur[v];
         if (hkind != 0) {
-            float be[3];
-            bext_at(c.bext_z, c.be, z, be);
-            pair_emf(hcur, be, c.sq);
+            emf2(hcur, z, hp);  // a single halo node uses .x only
             if (hkind == 1) {
 #pragma unroll
                 for (int v = 0; v < 6; ++v) *reinterpret_cast<float2*>(&t[v][hrow][hcol]) = hcur[v];
@@ -648,9 +676,7 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
             hcur[v] = hnxt[v];
         }
         if (z + 1 < z1) {
-            float be[3];
-            bext_at(c.bext_z, c.be, za, be);
-            pair_emf(ahd, be, c.sq);
+            emf2(ahd, za, p);
 #pragma unroll
             for (int v = 0; v < 6; ++v) nxt[v] = ahd[v];
         }
@@ -858,6 +884,7 @@ __device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restric
     const T J[3] = {db[1][2] - db[2][1], db[2][0] - db[0][2], db[0][1] - db[1][0]};
     T Be[3];
     bext_at(c.bext_z, c.be, z, Be);
+    bext_add_xy(c.bext_xy, nx * ny, y * nx + x, Be);
     const T B[3] = {Be[0] + b[k], Be[1] + b[k + n], Be[2] + b[k + 2 * n]};
     T L[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
     L[c.axis] += fb;
@@ -1067,6 +1094,7 @@ struct ObsCoef {
     double cx, cy, rin;  // region: distance from the centre <= rin
     T be[3];
     const T* bext_z;
+    const T* bext_xy;  // [3][nx ny] in-plane applied field, or nullptr
 };
 
 template <typename T, int DIM>
@@ -1116,6 +1144,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         }
         T Be_t[3];
         bext_at(c.bext_z, c.be, z, Be_t);
+        bext_add_xy(c.bext_xy, nx * ny, y * nx + x, Be_t);
         const double Be[3] = {(double)Be_t[0], (double)Be_t[1], (double)Be_t[2]};
         const double B[3] = {Be[0] + bk[0], Be[1] + bk[1], Be[2] + bk[2]};
         acc[1] += 0.5 * rho * (uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
@@ -1164,6 +1193,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
                 T Bep_t[3], Bem_t[3];
                 bext_at(c.bext_z, c.be, zpp, Bep_t);
                 bext_at(c.bext_z, c.be, zmm, Bem_t);
+                bext_add_xy(c.bext_xy, nx * ny, kp - zpp * nx * ny, Bep_t);
+                bext_add_xy(c.bext_xy, nx * ny, km - zmm * nx * ny, Bem_t);
                 L Bp[3], Bm[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {

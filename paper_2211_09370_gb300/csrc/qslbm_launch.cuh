@@ -58,6 +58,7 @@ struct Launch {
         sweep_weights(s, c.w0, c.w1, c.kappa);
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
         c.bext_z = static_cast<const T*>(s.bext_z);
+        c.bext_xy = static_cast<const T*>(s.bext_xy);
         c.strict_qs = s.p.strict_qs;
         c.sq = s.p.strict_qs ? T(0) : T(1);
         const IBView<T> v = view(s, true);
@@ -238,6 +239,7 @@ struct Launch {
         s.resident = false;
         const long long P = (long long)s.nx * s.ny;
         if (P > (long long)kResidentMaxPlane) return cudaSuccess;
+        if (s.bext_xy) return cudaSuccess;  // an in-plane applied field takes the split path
         int dev = 0, optin = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
@@ -278,6 +280,7 @@ struct Launch {
         fc.axis = s.axis;
         for (int a = 0; a < 3; ++a) fc.be[a] = (T)s.be[a];
         fc.bext_z = static_cast<const T*>(s.bext_z);
+        fc.bext_xy = static_cast<const T*>(s.bext_xy);
         FlowCoef<T> c;
         c.tau = (T)s.units.tau;
         c.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
@@ -313,6 +316,7 @@ struct Launch {
         c.rin = s.R - 2.0;
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
         c.bext_z = static_cast<const T*>(s.bext_z);
+        c.bext_xy = static_cast<const T*>(s.bext_xy);
         const T* dr = (const T*)s.drho[s.fcur];
         const T* u = (const T*)s.u[s.fcur];
         const T* b = (const T*)s.b[s.bcur];

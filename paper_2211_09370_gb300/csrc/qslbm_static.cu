@@ -60,6 +60,7 @@ void launch(const qslbm::State& s, const void* drho, const void* u, const void* 
     c.rin = s.R - 2.0;
     for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
     c.bext_z = static_cast<const T*>(s.bext_z);
+    c.bext_xy = static_cast<const T*>(s.bext_xy);
     const qslbm::Geo g{s.nx, s.ny, s.nz, s.n};
     const int blocks = s.nz;
     double* partial = scratch;

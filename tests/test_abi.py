@@ -44,7 +44,7 @@ def test_struct_layouts_match_header_sizes():
     dict(force_amp=0.2, force_period=0.0), dict(precision=5), dict(n_mag=-3), dict(perturb=-1.0),
     dict(alpha=0.7), dict(alpha=1.5), dict(alpha=-1.0),
     dict(mag_scheme=2), dict(mag_scheme=1),  # the second: tau_m far above 7/6 at Rm = 1e-3
-    dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), dict(gamma=-1.0),
+    dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), dict(gamma=-1.0), dict(b0_kind="field"),
 ])
 def test_invalid_parameters_rejected_before_device(bad):
     p = W.small_pipe(**bad)

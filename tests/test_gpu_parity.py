@@ -202,6 +202,39 @@ def test_rescaled_time_step_parity(name, precision, kernel):
     check_fields(got, want, precision, name)
 
 
+def _magnet_case(**kw):
+    nx, ny, D = 26, 24, 18.0
+    return W.small_pipe(nx=nx, ny=ny, nz=8, diameter=D, U0=0.05, Re=60.0, Ha=15.0, Rm=5e-3, perturb=0.0,
+                        n_mag=40, b0_kind="field", b0_field=W.six_magnet_field(nx, ny, D), **kw)
+
+
+@pytest.mark.parametrize("kernel", ["planes", "split"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_six_magnet_field_parity(precision, kernel):
+    # the six-magnet applied field of Sec. VI as a z-invariant in-plane field
+    p = _magnet_case(precision=precision, sweep_kernel=kernel)
+    got, want, o = run_both(p, 30)
+    check_fields(got, want, precision, "six magnets")
+    with Solver(p) as s:
+        assert s.units["sweep_kernel"] in ("planes", "split")
+
+
+def test_six_magnet_field_observables_and_auto_kernel_fp64():
+    p = _magnet_case(precision="fp64")
+    o = oracle.Oracle(p)
+    with Solver(p) as s:
+        assert s.units["sweep_kernel"] == "split"  # the resident kernel takes uniform / per-plane fields only
+        s.step(10)
+        s.observables()
+        o.step(10)
+        o.observables()
+        s.step(5)
+        o.step(5)
+        g, w = s.observables(), o.observables()
+    for k in ("E_k", "E_m", "pump", "visc", "joule", "qs_residual", "steady_residual"):
+        assert g[k] == pytest.approx(w[k], rel=1e-9, abs=1e-300), k
+
+
 def test_observables_match_oracle_fp64():
     p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
     o = oracle.Oracle(p)
