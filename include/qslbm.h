@@ -270,8 +270,7 @@ int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_
  * from a CUDA graph, and the node-parallel sweep's block size and persistent
  * grid are chosen by timing candidates on the batch at creation.  Each
  * instance follows the same arithmetic as a handle created alone with
- * QSLBM_SWEEP_PLANES when its planes have at most 2048 nodes (those are swept
- * and corrected in one launch, one CTA per plane), QSLBM_SWEEP_SPLIT otherwise. */
+ * QSLBM_SWEEP_SPLIT. */
 typedef struct qslbm_batch qslbm_batch;
 
 typedef struct qslbm_batch_info_t {

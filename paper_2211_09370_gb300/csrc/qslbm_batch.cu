@@ -122,41 +122,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_batch_ib_staged(const InstDesc
                                      sdelta + 3 * max_ring);
 }
 
-// Sweep and IB on b in one launch for instances with small planes
-// (kBatchFusedPlane nodes at most): one CTA per (instance, plane) in the prefix
-// table `fpfirst`, the same per-node arithmetic as k_sweep_ib (the single
-// instance's QSLBM_SWEEP_PLANES kernel).  For such planes the marching tiles
-// would be mostly halo and two launches per sweep mostly latency.
-template <typename T>
-__global__ void __launch_bounds__(kPlaneThreads) k_batch_sweep_ib(const InstDesc<T>* __restrict__ d,
-                                                                  const int* __restrict__ fpfirst, int kact,
-                                                                  int s) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sdelta = reinterpret_cast<T*>(smem_raw);
-    const int i = find_inst(fpfirst, kact, blockIdx.x);
-    const InstDesc<T>& D = d[i];
-    const int z = blockIdx.x - fpfirst[i];
-    const int nx = D.g.nx, ny = D.g.ny, nz = D.g.nz;
-    const long long n = D.g.n, P = (long long)nx * ny, base = (long long)z * P;
-    const int par = (D.bpar + s) & 1;
-    const T* bin = D.b[par];
-    T* bout = D.b[par ^ 1];
-    const T* u = D.u[D.fpar];
-    const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
-    T be_c[3], be_m[3], be_p[3];
-    bext_at(D.sc.bext_z, D.sc.be, z, be_c);
-    bext_at(D.sc.bext_z, D.sc.be, zm, be_m);
-    bext_at(D.sc.bext_z, D.sc.be, zp, be_p);
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        T o[3];
-        sweep_node<T, 3>(bin, u, n, nx, ny, base, (long long)zm * P, (long long)zp * P, p, D.sc, be_c, be_m, be_p, o);
-        bout[base + p] = o[0];
-        bout[base + p + n] = o[1];
-        bout[base + p + 2 * n] = o[2];
-    }
-    ib_plane<T>(D.ibm, bout, bout + n, bout + 2 * n, base, D.ibm.zinv ? 0 : z, sdelta);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kNodeThreads) k_batch_ib(const InstDesc<T>* __restrict__ d,
                                                            const int* __restrict__ pfirst, int kact, int s) {
@@ -231,11 +196,9 @@ struct qslbm_batch {
     void* desc = nullptr;                // InstDesc<T>[K]
     int* first = nullptr;                // node-block prefix [K + 1]
     int* pfirst = nullptr;               // plane prefix [K + 1]
-    int* fpfirst = nullptr;              // planes of the instances swept by k_batch_sweep_ib [K + 1]
-    int* lpfirst = nullptr;              // planes of the marching instances [K + 1]
     int* mfirst = nullptr;               // marker prefix [K + 1]
     int* sfirst = nullptr;               // shell-node prefix [K + 1]
-    std::vector<int> h_first, h_pfirst, h_mfirst, h_sfirst, h_fpfirst, h_lpfirst;
+    std::vector<int> h_first, h_pfirst, h_mfirst, h_sfirst;
     std::vector<int> active;             // active[s] = instances with N_mag > s
     int max_nmag = 0;
     int capacity = 0;                    // instances the device tables can hold
@@ -323,11 +286,6 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     return D;
 }
 
-// Instances whose planes are small enough for one CTA to sweep a plane and
-// apply its IB in one launch (k_batch_sweep_ib).
-constexpr long long kBatchFusedPlane = 2048;
-inline bool fused_plane(const State& s) { return (long long)s.nx * s.ny <= kBatchFusedPlane; }
-
 template <typename T>
 void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st) {
     const int kact = B.active[s];
@@ -336,17 +294,11 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
     (void)threads;
-    // small-plane instances: sweep + IB in one launch
-    if (B.h_fpfirst[kact] > 0)
-        qslbm::k_batch_sweep_ib<T><<<B.h_fpfirst[kact], qslbm::kPlaneThreads, B.ib_smem, st>>>(d, B.fpfirst, kact,
-                                                                                                  s);
-    // the others: marching sweep, then the IB corrector
-    if (total == 0) return;
     qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
     if (nm > 0 && B.ib_staged_smem > 0) {
-        qslbm::k_batch_ib_staged<T><<<B.h_lpfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
-            d, B.lpfirst, kact, s, B.max_ring);
+        qslbm::k_batch_ib_staged<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
+            d, B.pfirst, kact, s, B.max_ring);
     } else if (nm > 0) {
         qslbm::k_batch_ib_markers<T><<<(nm + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
                                         st>>>(d, B.mfirst, kact, s);
@@ -374,8 +326,6 @@ int build_tables(qslbm_batch& B, int threads) {
     B.h_pfirst.assign(K + 1, 0);
     B.h_mfirst.assign(K + 1, 0);
     B.h_sfirst.assign(K + 1, 0);
-    B.h_fpfirst.assign(K + 1, 0);
-    B.h_lpfirst.assign(K + 1, 0);
     size_t ring = 1, shell = 1;
     {
         // z planes per work item of the marching sweep: 16, halved while the
@@ -388,7 +338,6 @@ int build_tables(qslbm_batch& B, int threads) {
             long long w = 0;
             for (int k = 0; k < K; ++k) {
                 const State& s = qslbm::handle_state_mut(B.members[k]);
-                if (fused_plane(s)) continue;
                 w += (long long)((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
                      ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) * ((s.nz + chunk - 1) / chunk);
             }
@@ -400,18 +349,14 @@ int build_tables(qslbm_batch& B, int threads) {
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
-        const bool fused = fused_plane(s);
-        const int tiles = fused ? 0
-                                : ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
-                                      ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
-                                      ((s.nz + B.chunk - 1) / B.chunk);
+        const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
+                          ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
+                          ((s.nz + B.chunk - 1) / B.chunk);
         h[k].bpp = tiles;
         B.h_first[k + 1] = B.h_first[k] + tiles;
         B.h_pfirst[k + 1] = B.h_pfirst[k] + s.nz;
-        B.h_fpfirst[k + 1] = B.h_fpfirst[k] + (fused ? s.nz : 0);
-        B.h_lpfirst[k + 1] = B.h_lpfirst[k] + (fused ? 0 : s.nz);
-        B.h_mfirst[k + 1] = B.h_mfirst[k] + (fused ? 0 : s.ib.nm);
-        B.h_sfirst[k + 1] = B.h_sfirst[k] + (fused ? 0 : s.ib.ns);
+        B.h_mfirst[k + 1] = B.h_mfirst[k] + s.ib.nm;
+        B.h_sfirst[k + 1] = B.h_sfirst[k] + s.ib.ns;
         ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
         shell = std::max(shell, (size_t)std::max(1, s.ib.max_shell));
     }
@@ -436,19 +381,15 @@ int build_tables(qslbm_batch& B, int threads) {
         if (B.pfirst) cudaFree(B.pfirst);
         if (B.mfirst) cudaFree(B.mfirst);
         if (B.sfirst) cudaFree(B.sfirst);
-        if (B.fpfirst) cudaFree(B.fpfirst);
-        if (B.lpfirst) cudaFree(B.lpfirst);
         B.desc = nullptr;
-        B.first = B.pfirst = B.mfirst = B.sfirst = B.fpfirst = B.lpfirst = nullptr;
+        B.first = B.pfirst = B.mfirst = B.sfirst = nullptr;
         const int cap = std::max(K, 2 * B.capacity);
         BCHK(cudaMalloc(&B.desc, sizeof(qslbm::InstDesc<T>) * cap));
         BCHK(cudaMalloc((void**)&B.first, sizeof(int) * (cap + 1)));
         BCHK(cudaMalloc((void**)&B.pfirst, sizeof(int) * (cap + 1)));
         BCHK(cudaMalloc((void**)&B.mfirst, sizeof(int) * (cap + 1)));
         BCHK(cudaMalloc((void**)&B.sfirst, sizeof(int) * (cap + 1)));
-        BCHK(cudaMalloc((void**)&B.fpfirst, sizeof(int) * (cap + 1)));
-        BCHK(cudaMalloc((void**)&B.lpfirst, sizeof(int) * (cap + 1)));
-        B.device_bytes = (long long)(sizeof(qslbm::InstDesc<T>) * cap + 6 * sizeof(int) * (cap + 1));
+        B.device_bytes = (long long)(sizeof(qslbm::InstDesc<T>) * cap + 4 * sizeof(int) * (cap + 1));
         B.capacity = cap;
     }
     BCHK(cudaMemcpyAsync(B.desc, h.data(), sizeof(qslbm::InstDesc<T>) * K, cudaMemcpyHostToDevice, B.stream));
@@ -456,8 +397,6 @@ int build_tables(qslbm_batch& B, int threads) {
     BCHK(cudaMemcpyAsync(B.pfirst, B.h_pfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.mfirst, B.h_mfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.sfirst, B.h_sfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
-    BCHK(cudaMemcpyAsync(B.fpfirst, B.h_fpfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
-    BCHK(cudaMemcpyAsync(B.lpfirst, B.h_lpfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaStreamSynchronize(B.stream));
     return QSLBM_OK;
 }
@@ -542,8 +481,6 @@ void destroy_batch(qslbm_batch* B) {
     if (B->pfirst) cudaFree(B->pfirst);
     if (B->mfirst) cudaFree(B->mfirst);
     if (B->sfirst) cudaFree(B->sfirst);
-    if (B->fpfirst) cudaFree(B->fpfirst);
-    if (B->lpfirst) cudaFree(B->lpfirst);
     if (B->owns_members)
         for (qslbm_handle* h : B->members) qslbm_destroy(h);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);

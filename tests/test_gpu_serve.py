@@ -11,13 +11,6 @@ pytestmark = pytest.mark.gpu
 GB = 1 << 30
 
 
-
-def alone_kernel(p):
-    # a batched instance runs the planes kernel's arithmetic when its planes
-    # have at most 2048 nodes, the split kernel's otherwise
-    return "planes" if p["nx"] * p["ny"] <= 2048 else "split"
-
-
 def requests():
     return [
         W.small_pipe(nx=20, ny=20, nz=16, diameter=14.0, Re=20.0, Ha=30.0, Rm=1e-3, perturb=0.0,
@@ -64,7 +57,7 @@ def test_served_results_equal_alone_runs():
         assert r["status"] in (OK, ETIMEOUT), r
         if r["status"] == OK:
             assert r["obs"]["steady_residual"] < 1e-4
-        with Solver(dict(p, sweep_kernel=alone_kernel(p))) as s:
+        with Solver(dict(p, sweep_kernel="split")) as s:
             s.step(r["steps"])
             want = s.state()
         for a, b in zip(fields[i], want):
