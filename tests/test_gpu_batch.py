@@ -25,13 +25,16 @@ def uneven(precision, n=5):
         W.small_pipe(nx=21, ny=23, nz=11, diameter=15.0, Re=50.0, Ha=0.0, Rm=0.2, force_amp=0.2,
                      force_period=7.0, precision=precision, seed=4),
         W.small_pipe(nx=20, ny=20, nz=7, diameter=14.0, Rm=1.0, n_mag=9, precision=precision, seed=5),
+        # the six-magnet in-plane applied field (Sec. VI)
+        W.small_pipe(nx=22, ny=22, nz=6, diameter=16.0, Ha=12.0, Rm=5e-3, n_mag=30, b0_kind="field",
+                     b0_field=W.six_magnet_field(22, 22, 16.0), precision=precision, seed=6),
     ]
     return ps[:n]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_batch_members_match_single_instances(precision):
-    ps = uneven(precision)
+    ps = uneven(precision, n=6)
     steps = 6
     with Batch(ps) as B:
         info = B.info()
