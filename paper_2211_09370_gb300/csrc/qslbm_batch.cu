@@ -62,7 +62,8 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, i
 // Persistent z-marching sweep over every active instance's tiles: work item w
 // is (instance, tile x, tile y, z chunk of `chunk` planes) in the prefix table
 // `first`.
-template <typename T>
+// XY: some instance has an in-plane applied field (QSLBM_B0_FIELD)
+template <typename T, bool XY>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
                                                                     const int* __restrict__ first, int kact, int s,
                                                                     int chunk) {
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDe
         const int r = local - bz * tiles_x * tiles_y;
         const int by = r / tiles_x, bx = r - by * tiles_x;
         const int par = (D.bpar + s) & 1;
-        march_tile<T>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, chunk, tile);
+        march_tile<T, XY>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, chunk, tile);
         __syncthreads();
     }
 }
@@ -208,6 +209,7 @@ struct qslbm_batch {
     size_t ib_staged_smem = 0;  // shared memory of k_batch_ib_staged, 0 when it does not fit
     int max_ring = 1;           // largest ring of the batch (layout of that shared memory)
     int chunk = 16;             // z planes per work item of the marching sweep
+    bool has_field = false;     // some member has an in-plane applied field
     int threads = 256, grid = 0;         // autotuned sweep launch
     cudaGraphExec_t graph = nullptr;
     long long steps = 0;
@@ -294,7 +296,10 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
     (void)threads;
-    qslbm::k_batch_sweep<T><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
+    if (B.has_field)
+        qslbm::k_batch_sweep<T, true><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
+    else
+        qslbm::k_batch_sweep<T, false><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
     if (nm > 0 && B.ib_staged_smem > 0) {
         qslbm::k_batch_ib_staged<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
@@ -346,9 +351,11 @@ int build_tables(qslbm_batch& B, int threads) {
         B.chunk = qslbm::kMarchChunk;
         while (B.chunk > 2 && items(B.chunk) < 8LL * sms) B.chunk /= 2;
     }
+    B.has_field = false;
     for (int k = 0; k < K; ++k) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
+        if (s.bext_xy) B.has_field = true;
         const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
                           ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
                           ((s.nz + B.chunk - 1) / B.chunk);

@@ -352,7 +352,7 @@ using MarchTile = T[6][kMarchTY + 2][kMarchTX + 2];
 // every neighbour's flux is formed as in sweep_node, with the same
 // expressions and neighbour order, so that it rounds like the other FP64 sweep
 // kernels.  The column's plane z + 2 is loaded one plane ahead of its use.
-template <typename T>
+template <typename T, bool XY = true>
 __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
                                            const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
                                            int chunk, MarchTile<T>& tile) {
@@ -385,13 +385,13 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
         if constexpr (EMF) {
             T be[3];
             bext_at(c.bext_z, c.be, zm, be);
-            bext_add_xy(c.bext_xy, P, p, be);
+            if constexpr (XY) bext_add_xy(c.bext_xy, P, p, be);
             node_emf(prv, be, c.sq);
             bext_at(c.bext_z, c.be, z0, be);
-            bext_add_xy(c.bext_xy, P, p, be);
+            if constexpr (XY) bext_add_xy(c.bext_xy, P, p, be);
             node_emf(cur, be, c.sq);
             bext_at(c.bext_z, c.be, zn, be);
-            bext_add_xy(c.bext_xy, P, p, be);
+            if constexpr (XY) bext_add_xy(c.bext_xy, P, p, be);
             node_emf(nxt, be, c.sq);
         }
     }
@@ -413,7 +413,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             if constexpr (EMF) {
                 T be[3];
                 bext_at(c.bext_z, c.be, z, be);
-                bext_add_xy(c.bext_xy, P, hp, be);
+                if constexpr (XY) bext_add_xy(c.bext_xy, P, hp, be);
                 node_emf(r, be, c.sq);
             }
 #pragma unroll
@@ -465,10 +465,12 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
 #pragma unroll
                     for (int a = 0; a < 3; ++a) acc[a] += c.w1 * bq[a];
                     T Bx[3] = {bez[0], bez[1], bez[2]};
-                    if (c.bext_xy) {
-                        const int xq = d == 0 ? wrap_dec(xc, nx) : d == 1 ? wrap_inc(xc, nx) : xc;
-                        const int yq = d == 2 ? wrap_dec(yc, ny) : d == 3 ? wrap_inc(yc, ny) : yc;
-                        bext_add_xy(c.bext_xy, P, yq * nx + xq, Bx);
+                    if constexpr (XY) {
+                        if (c.bext_xy) {
+                            const int xq = d == 0 ? wrap_dec(xc, nx) : d == 1 ? wrap_inc(xc, nx) : xc;
+                            const int yq = d == 2 ? wrap_dec(yc, ny) : d == 3 ? wrap_inc(yc, ny) : yc;
+                            bext_add_xy(c.bext_xy, P, yq * nx + xq, Bx);
+                        }
                     }
                     T B[3];
 #pragma unroll
@@ -489,7 +491,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
             if constexpr (EMF) {
                 T be[3];
                 bext_at(c.bext_z, c.be, za, be);
-                bext_add_xy(c.bext_xy, P, p, be);
+                if constexpr (XY) bext_add_xy(c.bext_xy, P, p, be);
                 node_emf(ahd, be, c.sq);
             }
 #pragma unroll
@@ -498,12 +500,13 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     }
 }
 
-template <typename T>
+// XY: the domain has an in-plane applied field (QSLBM_B0_FIELD)
+template <typename T, bool XY>
 __global__ void __launch_bounds__(kMarchTX* kMarchTY) k_sweep_march(Geo g, const T* __restrict__ bin,
                                                                     T* __restrict__ bout, const T* __restrict__ u,
                                                                     SweepCoef<T> c, int chunk) {
     __shared__ MarchTile<T> tile;
-    march_tile<T>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, chunk, tile);
+    march_tile<T, XY>(g, bin, bout, u, c, blockIdx.x, blockIdx.y, blockIdx.z, chunk, tile);
 }
 
 // FP32 z-marching sweep on x-adjacent node pairs (nx even): a CTA of 256
@@ -558,7 +561,7 @@ __device__ __forceinline__ void pair_emf(float2 r[6], const float beA[3], const 
     for (int v = 0; v < 6; ++v) r[v] = make_float2(a[v], b[v]);
 }
 
-template <typename F>
+template <typename F, bool XY>
 __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const F* __restrict__ bin,
                                                                    F* __restrict__ bout, const F* __restrict__ u,
                                                                    SweepCoef<F> c, int chunk) {
@@ -591,10 +594,14 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
     auto emf2 = [&](float2 r[6], int zz, int pp) {
         float be[3];
         bext_at(c.bext_z, c.be, zz, be);
-        float bA[3] = {be[0], be[1], be[2]}, bB[3] = {be[0], be[1], be[2]};
-        bext_add_xy(c.bext_xy, P, pp, bA);
-        bext_add_xy(c.bext_xy, P, pp + 1 < P ? pp + 1 : pp, bB);
-        pair_emf(r, bA, bB, c.sq);
+        if constexpr (XY) {
+            float bA[3] = {be[0], be[1], be[2]}, bB[3] = {be[0], be[1], be[2]};
+            bext_add_xy(c.bext_xy, P, pp, bA);
+            bext_add_xy(c.bext_xy, P, pp + 1 < P ? pp + 1 : pp, bB);
+            pair_emf(r, bA, bB, c.sq);
+        } else {
+            pair_emf(r, be, be, c.sq);
+        }
     };
     float2 prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
     {

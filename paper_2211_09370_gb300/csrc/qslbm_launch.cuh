@@ -81,10 +81,19 @@ struct Launch {
                 if (pair_march(s)) {
                     const dim3 pgrid((unsigned)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)),
                                      (unsigned)((s.ny + kPairTY - 1) / kPairTY), (unsigned)((s.nz + chunk - 1) / chunk));
-                    k_sweep_march_pair<float><<<pgrid, kPairThreads, 0, st>>>(geo(s), (const float*)bin, (float*)bout,
-                                                                       (const float*)u, fcoef(c), chunk);
+                    if (s.bext_xy)
+                        k_sweep_march_pair<float, true><<<pgrid, kPairThreads, 0, st>>>(
+                            geo(s), (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
+                    else
+                        k_sweep_march_pair<float, false><<<pgrid, kPairThreads, 0, st>>>(
+                            geo(s), (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
                 } else if (s.dim == 3)
-                    k_sweep_march<T><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
+                {
+                    if (s.bext_xy)
+                        k_sweep_march<T, true><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
+                    else
+                        k_sweep_march<T, false><<<mgrid, kMarchTX * kMarchTY, 0, st>>>(geo(s), bin, bout, u, c, chunk);
+                }
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
                 if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
@@ -208,8 +217,14 @@ struct Launch {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const bool pair = pair_march(s);
         if (e == cudaSuccess)
-            e = pair ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march_pair<float>, kPairThreads, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T>, kMarchTX * kMarchTY, 0);
+            e = pair ? (s.bext_xy ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march_pair<float, true>,
+                                                                                  kPairThreads, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                        &per_sm, k_sweep_march_pair<float, false>, kPairThreads, 0))
+                     : (s.bext_xy ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T, true>,
+                                                                                  kMarchTX * kMarchTY, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_march<T, false>,
+                                                                                  kMarchTX * kMarchTY, 0));
         if (e != cudaSuccess) return e;
         const long long tiles =
             pair ? (long long)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)) * ((s.ny + kPairTY - 1) / kPairTY)
