@@ -121,8 +121,10 @@ struct LocalIB {
 
 // Explicit IB corrector on a plane held in shared memory (Sec. V.D, V.F):
 // delta_j = s_j (0 - D f*) for every marker first, then f += D^T delta.
+// With pub set, each corrected shell value is also written to pub (three
+// components P apart), by the thread that corrected it.
 template <typename T, int THREADS>
-__device__ __forceinline__ void ib_local(const LocalIB<T>& t, T* f0, T* f1, T* f2, T* sdelta) {
+__device__ __forceinline__ void ib_local(const LocalIB<T>& t, T* f0, T* f1, T* f2, T* sdelta, T* pub, int P) {
     if (t.R == 0) return;
     __syncthreads();
     for (int m = threadIdx.x; m < t.R; m += THREADS) {
@@ -151,9 +153,15 @@ __device__ __forceinline__ void ib_local(const LocalIB<T>& t, T* f0, T* f1, T* f
             c2 += w * sdelta[3 * l + 2];
         }
         const int q = t.shell[i];
-        f0[q] += c0;
-        f1[q] += c1;
-        f2[q] += c2;
+        const T v0 = f0[q] + c0, v1 = f1[q] + c1, v2 = f2[q] + c2;
+        f0[q] = v0;
+        f1[q] = v1;
+        f2[q] = v2;
+        if (pub) {
+            __stcg(pub + q, v0);
+            __stcg(pub + P + q, v1);
+            __stcg(pub + 2 * P + q, v2);
+        }
     }
 }
 
@@ -378,7 +386,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 }
             }
         }
-        __syncthreads();  // every read of the old plane is done
+        // every read of the old plane is done (after a wait, its barrier did that)
+        if (!(DIM == 3 && s > 0)) __syncthreads();
 #pragma unroll
         for (int k = 0; k < NPAIR; ++k) {
             const int p0 = 2 * (tid + k * kResidentThreads);
@@ -462,7 +471,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 }
             }
         }
-        __syncthreads();  // every read of the old plane is done
+        // every read of the old plane is done (after a wait, its barrier did that)
+        if (!(DIM == 3 && s > 0)) __syncthreads();
 #pragma unroll
         for (int k = 0; k < kResidentMaxNpt; ++k) {
             const int p = tid + k * kResidentThreads;
@@ -477,19 +487,11 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             }
         }
         }
-        ib_local<T, kResidentThreads>(lib, sb, sb + P, sb + 2 * P, sdelta);
-        __syncthreads();
-        if (publish) {
-            for (int i = tid; i < lib.S; i += kResidentThreads) {
-                const int q = lib.shell[i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) __stcg(xout + a * P + q, sb[a * P + q]);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                st_release_u32(&sync->flags[z], epoch + (unsigned int)s + 1u);
-            }
+        ib_local<T, kResidentThreads>(lib, sb, sb + P, sb + 2 * P, sdelta, publish ? xout : nullptr, P);
+        __syncthreads();  // the plane is final in shared memory and in xout
+        if (publish && tid == 0) {
+            __threadfence();
+            st_release_u32(&sync->flags[z], epoch + (unsigned int)s + 1u);
         }
     }
     for (int p = tid; p < P; p += kResidentThreads) {
