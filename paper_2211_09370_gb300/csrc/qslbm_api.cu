@@ -387,6 +387,28 @@ int upload_ib(State& s) {
     d.max_shell = h.max_shell;
     d.max_nnz = h.max_nnz;
     d.zinv = ib_tables_z_invariant(s, q9, w9) ? 1 : 0;
+    {
+        // each shell node's markers and weights in CSR order, padded to a
+        // multiple of four entries (plane 0's nodes alone when every plane
+        // carries plane 0's tables)
+        const int nsp = d.zinv ? h.shell_off[1] : (int)h.shell_xy.size();
+        int kmax = 0;
+        for (int i = 0; i < nsp; ++i) kmax = std::max(kmax, h.csr_off[i + 1] - h.csr_off[i]);
+        const int K = (kmax + 3) / 4 * 4;
+        d.pad_k = 0;
+        if (K > 0 && K <= qslbm::kMaxPadK) {
+            std::vector<int> pm((size_t)nsp * K, 0);
+            std::vector<double> pw((size_t)nsp * K, 0.0);
+            for (int i = 0; i < nsp; ++i)
+                for (int e = h.csr_off[i]; e < h.csr_off[i + 1]; ++e) {
+                    pm[(size_t)i * K + (e - h.csr_off[i])] = h.csr_m[e];
+                    pw[(size_t)i * K + (e - h.csr_off[i])] = h.csr_w[e];
+                }
+            if ((rc = upload(s, (void**)&d.pad_m, pm))) return rc;
+            if ((rc = upload_real(s, &d.pad_w, pw))) return rc;
+            d.pad_k = K;
+        }
+    }
     return QSLBM_OK;
 }
 

@@ -109,18 +109,17 @@ __global__ void __launch_bounds__(kNodeThreads) k_batch_ib_shell(const InstDesc<
 // The staged IB corrector over every active instance: one CTA per
 // (instance, plane) in the plane prefix table; shared memory for the largest
 // ring and shell of the batch.
-template <typename T>
-__global__ void __launch_bounds__(kNodeThreads) k_batch_ib_staged(const InstDesc<T>* __restrict__ d,
+template <typename T, int U>
+__global__ void __launch_bounds__(kNodeThreads, (kIbStagedMinBlocks<T, U>)) k_batch_ib_staged(const InstDesc<T>* __restrict__ d,
                                                                   const int* __restrict__ pfirst, int kact, int s,
-                                                                  int max_ring) {
+                                                                  int max_ring, int max_shell) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sdelta = reinterpret_cast<T*>(smem_raw);
     const int i = find_inst(pfirst, kact, blockIdx.x);
     const InstDesc<T>& D = d[i];
     const int z = blockIdx.x - pfirst[i];
     T* f = D.b[((D.bpar + s) & 1) ^ 1];
-    ib_staged_plane<T, kNodeThreads>(D.ibm, f, (int)D.g.n, z * D.g.nx * D.g.ny, D.ibm.zinv ? 0 : z, sdelta,
-                                     sdelta + 3 * max_ring);
+    ib_staged_plane<T, kNodeThreads, U>(D.ibm, f, (int)D.g.n, z * D.g.nx * D.g.ny, D.ibm.zinv ? 0 : z, max_ring,
+                                     max_shell, smem_raw);
 }
 
 template <typename T>
@@ -208,6 +207,7 @@ struct qslbm_batch {
     size_t ib_smem = 0;
     size_t ib_staged_smem = 0;  // shared memory of k_batch_ib_staged, 0 when it does not fit
     int max_ring = 1;           // largest ring of the batch (layout of that shared memory)
+    int max_shell = 1;          // largest shell of the batch
     int chunk = 16;             // z planes per work item of the marching sweep
     bool has_field = false;     // some member has an in-plane applied field
     int threads = 256, grid = 0;         // autotuned sweep launch
@@ -284,6 +284,9 @@ qslbm::InstDesc<T> make_desc(const State& s) {
         v.ns = s.ib.ns;
         v.zinv = s.ib.zinv;
         v.mk_slot = s.ib.mk_slot;
+        v.pad_m = s.ib.pad_m;
+        v.pad_w = (const T*)s.ib.pad_w;
+        v.pad_k = s.ib.pad_k;
     }
     return D;
 }
@@ -302,8 +305,13 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
         qslbm::k_batch_sweep<T, false><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
     if (nm > 0 && B.ib_staged_smem > 0) {
-        qslbm::k_batch_ib_staged<T><<<B.h_pfirst[kact], qslbm::kNodeThreads, B.ib_staged_smem, st>>>(
-            d, B.pfirst, kact, s, B.max_ring);
+        const int np = B.h_pfirst[kact], R = B.max_ring, S = B.max_shell;
+        const size_t sm = B.ib_staged_smem;
+        switch (qslbm::ib_staged_unroll(S)) {
+            case 1: qslbm::k_batch_ib_staged<T, 1><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
+            case 2: qslbm::k_batch_ib_staged<T, 2><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
+            default: qslbm::k_batch_ib_staged<T, 5><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
+        }
     } else if (nm > 0) {
         qslbm::k_batch_ib_markers<T><<<(nm + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
                                         st>>>(d, B.mfirst, kact, s);
@@ -332,6 +340,7 @@ int build_tables(qslbm_batch& B, int threads) {
     B.h_mfirst.assign(K + 1, 0);
     B.h_sfirst.assign(K + 1, 0);
     size_t ring = 1, shell = 1;
+    bool padded = true;
     {
         // z planes per work item of the marching sweep: 16, halved while the
         // batch would give fewer than 8 work items per SM (small instances:
@@ -366,19 +375,24 @@ int build_tables(qslbm_batch& B, int threads) {
         B.h_sfirst[k + 1] = B.h_sfirst[k] + s.ib.ns;
         ring = std::max(ring, (size_t)std::max(1, s.ib.max_ring));
         shell = std::max(shell, (size_t)std::max(1, s.ib.max_shell));
+        if (s.ib.nm > 0 && s.ib.pad_k == 0) padded = false;
     }
     B.ib_smem = 3 * ring * sizeof(T);
     // the staged IB corrector, when the largest plane's ring and shell fit
+    // and every member's shell nodes have padded marker lists
     B.max_ring = (int)ring;
+    B.max_shell = (int)shell;
     B.ib_staged_smem = 0;
-    {
-        const size_t smem = 3 * (ring + shell) * sizeof(T);
+    if (padded) {
+        const size_t smem = qslbm::ib_staged_smem_bytes<T>((int)ring, (int)shell);
         int dev = 0, optin = 0;
         BCHK(cudaGetDevice(&dev));
         BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         if (smem <= (size_t)optin) {
-            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+            const int U = qslbm::ib_staged_unroll((int)shell);
+            BCHK(cudaFuncSetAttribute(U == 1 ? qslbm::k_batch_ib_staged<T, 1>
+                                             : (U == 2 ? qslbm::k_batch_ib_staged<T, 2> : qslbm::k_batch_ib_staged<T, 5>),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             B.ib_staged_smem = smem;
         }
     }

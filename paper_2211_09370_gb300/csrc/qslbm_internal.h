@@ -25,7 +25,14 @@ struct DeviceIB {
     int nm = 0, ns = 0, nnz = 0, max_ring = 0, max_shell = 0, max_nnz = 0;
     int zinv = 0;  // 1: every z plane carries plane 0's ring and shell tables
     int* mk_slot = nullptr;  // [9 nm] shell-list position of each support node
+    int* pad_m = nullptr;    // [nsp pad_k] padded marker lists of the shell nodes
+    void* pad_w = nullptr;   // [nsp pad_k] and their weights
+    int pad_k = 0;           // list length, a multiple of 4 (0: none)
 };
+
+// Longest padded marker list of a shell node (longer lists: the staged IB
+// corrector is not used).
+constexpr int kMaxPadK = 16;
 
 // Host copy of the marker geometry and IB weights (binary64).
 struct HostIB {

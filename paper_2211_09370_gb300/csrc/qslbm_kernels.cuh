@@ -55,6 +55,9 @@ struct IBView {
     T* delta;              // [3 * nm]: delta_j of the two-phase corrector
     const int* mk_slot;    // [9 * nm]: position of each support node in its plane's shell list
                            //           (0 where the weight is zero)
+    const int* pad_m;      // [ns_pad * pad_k]: each shell node's markers (ring-relative, CSR order)
+    const T* pad_w;        //   and weights, padded with (0, 0.0) to pad_k entries
+    int pad_k;             // a multiple of 4 (0: no padded lists; the staged corrector is not used)
     int nm, ns;
     int zinv;              // 1: every plane has plane 0's ring and shell tables (straight pipe)
 };
@@ -753,70 +756,162 @@ __global__ void __launch_bounds__(kNodeThreads) k_ib_planes(Geo g, T* f, IBView<
     ib_plane<T>(ib, f, f + n, f + 2 * n, base, ib.zinv ? 0 : (int)blockIdx.x, sdelta);
 }
 
+// Shared memory of the staged IB corrector for a plane of R markers and S
+// shell nodes: 3 R deltas, 3 S staged values, the markers' 9 R weights and R
+// scalings, then 9 R shell slots (int).
+template <typename T>
+__host__ __device__ inline size_t ib_staged_smem_bytes(int max_ring, int max_shell) {
+    return (size_t)(13 * max_ring + 3 * max_shell) * sizeof(T) + (size_t)9 * max_ring * sizeof(int);
+}
+
+// Shell nodes a thread of the staged corrector loads at once (U), chosen for
+// the largest shell so that one batch of loads covers it, and the CTAs kept
+// resident per SM at that U (bounds the registers): with U = 5 in FP32, four
+// cover a plane per CTA of a 512-plane domain in one wave.
+inline int ib_staged_unroll(int max_shell) {
+    return max_shell <= kNodeThreads ? 1 : (max_shell <= 2 * kNodeThreads ? 2 : 5);
+}
+template <typename T, int U>
+constexpr int kIbStagedMinBlocks = (sizeof(T) == 4 ? 8 : 4) / (U == 1 ? 1 : 2);
+
+// Four consecutive weights of a padded marker list (16-byte aligned rows).
+__device__ __forceinline__ void ld4(const float* p, float (&w)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&w)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+
 // The IB corrector with the plane's shell nodes staged in shared memory, on
-// plane `base` of f (three components n apart): the shell values are read
-// from memory once (independent loads), the markers interpolate from the
-// staged copy through mk_slot, and every shell node is written once.  Same
-// sums in the same order as ib_plane.  tz: the plane whose tables apply;
-// sdelta holds 3 R values, sf 3 S.  Called by every thread of the CTA.
-template <typename T, int THREADS>
-__device__ __forceinline__ void ib_staged_plane(const IBView<T>& ib, T* f, int n, int base, int tz, T* sdelta,
-                                                T* sf) {
+// plane `base` of f (three components n apart).  Three phases, each one
+// round trip to memory: (A) the shell values and the markers' tables are
+// read with independent loads into shared memory; (B) each marker
+// interpolates from the staged copy through mk_slot; (C) each shell node adds
+// the spread of its markers' deltas, read from its padded marker list
+// (pad_k entries, weight 0 past its own), and is written once.  Same sums in
+// the same order as ib_plane (the padding adds exact zeros).  tz: the plane
+// whose tables apply; smem as ib_staged_smem_bytes.  Called by every thread
+// of the CTA.
+template <typename T, int THREADS, int U>
+__device__ __forceinline__ void ib_staged_plane(const IBView<T>& ib, T* f, int n, int base, int tz, int max_ring,
+                                                int max_shell, unsigned char* smem) {
     const int m0 = ib.ring_off[tz], R = ib.ring_off[tz + 1] - m0;
     if (R == 0) return;  // uniform across the CTA
     const int s0 = ib.shell_off[tz], S = ib.shell_off[tz + 1] - s0;
+    T* sdelta = reinterpret_cast<T*>(smem);  // [3 R]
+    T* sf = sdelta + 3 * max_ring;           // [3 S]
+    T* tw = sf + 3 * max_shell;              // [9 R]
+    T* tsc = tw + 9 * max_ring;              // [R]
+    int* tslot = reinterpret_cast<int*>(tsc + max_ring);  // [9 R]
     T* f0 = f + base;
     T* f1 = f0 + n;
     T* f2 = f1 + n;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < S; i += THREADS) {
-        const int q = ib.shell_xy[s0 + i];
-        sf[i] = f0[q];
-        sf[S + i] = f1[q];
-        sf[2 * S + i] = f2[q];
+    const int tid = threadIdx.x;
+    // (A) shell values (in-plane index, then the value) and marker tables
+    for (int i0 = 0; i0 < S; i0 += U * THREADS) {
+        int q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * THREADS + tid;
+            q[u] = i < S ? __ldg(ib.shell_xy + s0 + i) : 0;
+        }
+        T v[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * THREADS + tid < S) {
+                v[u][0] = f0[q[u]];
+                v[u][1] = f1[q[u]];
+                v[u][2] = f2[q[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * THREADS + tid;
+            if (i < S) {
+                sf[i] = v[u][0];
+                sf[S + i] = v[u][1];
+                sf[2 * S + i] = v[u][2];
+            }
+        }
     }
+    for (int e = tid; e < 9 * R; e += THREADS) {
+        tw[e] = __ldg(ib.mk_w + 9 * m0 + e);
+        tslot[e] = __ldg(ib.mk_slot + 9 * m0 + e);
+    }
+    for (int m = tid; m < R; m += THREADS) tsc[m] = __ldg(ib.mk_s + m0 + m);
     __syncthreads();
-    for (int m = threadIdx.x; m < R; m += THREADS) {
+    // (B) delta_j = -s_j D f* at every marker
+    for (int m = tid; m < R; m += THREADS) {
         T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const T w = ib.mk_w[9 * (m0 + m) + j];
-            const int q = ib.mk_slot[9 * (m0 + m) + j];
+            const T w = tw[9 * m + j];
+            const int q = tslot[9 * m + j];
             a0 += w * sf[q];
             a1 += w * sf[S + q];
             a2 += w * sf[2 * S + q];
         }
-        const T s = ib.mk_s[m0 + m];
-        sdelta[3 * m + 0] = -s * a0;
-        sdelta[3 * m + 1] = -s * a1;
-        sdelta[3 * m + 2] = -s * a2;
+        const T sm = tsc[m];
+        sdelta[3 * m + 0] = -sm * a0;
+        sdelta[3 * m + 1] = -sm * a1;
+        sdelta[3 * m + 2] = -sm * a2;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < S; i += THREADS) {
-        T c0 = T(0), c1 = T(0), c2 = T(0);
-        const int e0 = ib.csr_off[s0 + i], e1 = ib.csr_off[s0 + i + 1];
-        for (int e = e0; e < e1; ++e) {
-            const T w = ib.csr_w[e];
-            const int l = ib.csr_m[e];
-            c0 += w * sdelta[3 * l + 0];
-            c1 += w * sdelta[3 * l + 1];
-            c2 += w * sdelta[3 * l + 2];
+    // (C) f += D^T delta on the shell, four list entries per load
+    const int K = ib.pad_k;
+    for (int i0 = 0; i0 < S; i0 += U * THREADS) {
+        T c[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u][0] = c[u][1] = c[u][2] = T(0);
+        for (int k0 = 0; k0 < K; k0 += 4) {
+            int4 mm[U];
+            T ww[U][4];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * THREADS + tid;
+                if (i < S) {
+                    const long long r = (long long)(s0 + i) * K + k0;
+                    mm[u] = __ldg(reinterpret_cast<const int4*>(ib.pad_m + r));
+                    ld4(ib.pad_w + r, ww[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (i0 + u * THREADS + tid < S) {
+                    const int l[4] = {mm[u].x, mm[u].y, mm[u].z, mm[u].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        c[u][0] += ww[u][e] * sdelta[3 * l[e] + 0];
+                        c[u][1] += ww[u][e] * sdelta[3 * l[e] + 1];
+                        c[u][2] += ww[u][e] * sdelta[3 * l[e] + 2];
+                    }
+                }
+            }
         }
-        const int q = ib.shell_xy[s0 + i];
-        f0[q] = sf[i] + c0;
-        f1[q] = sf[S + i] + c1;
-        f2[q] = sf[2 * S + i] + c2;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * THREADS + tid;
+            if (i < S) {
+                const int q = __ldg(ib.shell_xy + s0 + i);
+                f0[q] = sf[i] + c[u][0];
+                f1[q] = sf[S + i] + c[u][1];
+                f2[q] = sf[2 * S + i] + c[u][2];
+            }
+        }
     }
 }
 
-// The staged corrector as a launch of its own, one CTA per plane.  Shared
-// memory: 3 max_ring deltas, then 3 max_shell staged values.
-template <typename T>
-__global__ void __launch_bounds__(kNodeThreads) k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring) {
+// The staged corrector as a launch of its own, one CTA per plane; shared
+// memory ib_staged_smem_bytes(max_ring, max_shell).
+template <typename T, int U>
+__global__ void __launch_bounds__(kNodeThreads, (kIbStagedMinBlocks<T, U>))
+    k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring, int max_shell) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sdelta = reinterpret_cast<T*>(smem_raw);
     const int z = blockIdx.x;
-    ib_staged_plane<T, kNodeThreads>(ib, f, (int)g.n, z * g.nx * g.ny, ib.zinv ? 0 : z, sdelta, sdelta + 3 * max_ring);
+    ib_staged_plane<T, kNodeThreads, U>(ib, f, (int)g.n, z * g.nx * g.ny, ib.zinv ? 0 : z, max_ring, max_shell,
+                                     smem_raw);
 }
 
 // ---------------------------------------------------------------------------

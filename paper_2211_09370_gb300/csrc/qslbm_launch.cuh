@@ -33,6 +33,9 @@ struct Launch {
         v.ns = s.ib.ns;
         v.zinv = s.ib.zinv;
         v.mk_slot = s.ib.mk_slot;
+        v.pad_m = s.ib.pad_m;
+        v.pad_w = static_cast<const T*>(s.ib.pad_w);
+        v.pad_k = s.ib.pad_k;
         return v;
     }
 
@@ -97,7 +100,13 @@ struct Launch {
                 else
                     k_sweep_nodes<T, 2><<<grid, kNodeThreads, 0, st>>>(geo(s), bin, bout, u, c);
                 if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
-                    k_ib_staged<T><<<s.nz, kNodeThreads, s.ib_staged_smem, st>>>(geo(s), bout, v, s.ib.max_ring);
+                    const int R = s.ib.max_ring, S = s.ib.max_shell;
+                    const size_t sm = s.ib_staged_smem;
+                    switch (ib_staged_unroll(S)) {
+                        case 1: k_ib_staged<T, 1><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
+                        case 2: k_ib_staged<T, 2><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
+                        default: k_ib_staged<T, 5><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
+                    }
                 } else if (s.ib.nm > 0) {
                     k_ib_markers<T><<<(s.ib.nm + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
                     k_ib_shell<T><<<(s.ib.ns + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
@@ -235,14 +244,17 @@ struct Launch {
         chunk = std::max<long long>(chunk, 4);  // keep the z halo overhead small
         s.march_chunk = (int)std::min<long long>(chunk, s.nz);
         // the staged IB corrector, when the plane's shell fits shared memory
+        // and the shell nodes' marker lists are padded
         s.ib_staged_smem = 0;
-        if (s.ib.nm > 0) {
-            const size_t smem = (size_t)3 * (s.ib.max_ring + s.ib.max_shell) * sizeof(T);
+        if (s.ib.nm > 0 && s.ib.pad_k > 0) {
+            const size_t smem = ib_staged_smem_bytes<T>(s.ib.max_ring, s.ib.max_shell);
             int max_optin = 0;
             e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
             if (e != cudaSuccess) return e;
             if (smem <= (size_t)max_optin) {
-                e = cudaFuncSetAttribute(k_ib_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                const int U = ib_staged_unroll(s.ib.max_shell);
+                e = cudaFuncSetAttribute(U == 1 ? k_ib_staged<T, 1> : (U == 2 ? k_ib_staged<T, 2> : k_ib_staged<T, 5>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 s.ib_staged_smem = smem;
             }
