@@ -209,6 +209,7 @@ struct qslbm_batch {
     int max_ring = 1;           // largest ring of the batch (layout of that shared memory)
     int max_shell = 1;          // largest shell of the batch
     int chunk = 16;             // z planes per work item of the marching sweep
+    int sms = 1;                // SMs of the device
     bool has_field = false;     // some member has an in-plane applied field
     int threads = 256, grid = 0;         // autotuned sweep launch
     cudaGraphExec_t graph = nullptr;
@@ -307,7 +308,7 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     if (nm > 0 && B.ib_staged_smem > 0) {
         const int np = B.h_pfirst[kact], R = B.max_ring, S = B.max_shell;
         const size_t sm = B.ib_staged_smem;
-        switch (qslbm::ib_staged_unroll(S)) {
+        switch (qslbm::ib_staged_unroll(S, np, B.sms)) {
             case 1: qslbm::k_batch_ib_staged<T, 1><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
             case 2: qslbm::k_batch_ib_staged<T, 2><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
             default: qslbm::k_batch_ib_staged<T, 5><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
@@ -357,6 +358,7 @@ int build_tables(qslbm_batch& B, int threads) {
             }
             return w;
         };
+        B.sms = sms;
         B.chunk = qslbm::kMarchChunk;
         while (B.chunk > 2 && items(B.chunk) < 8LL * sms) B.chunk /= 2;
     }
@@ -389,10 +391,13 @@ int build_tables(qslbm_batch& B, int threads) {
         BCHK(cudaGetDevice(&dev));
         BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         if (smem <= (size_t)optin) {
-            const int U = qslbm::ib_staged_unroll((int)shell);
-            BCHK(cudaFuncSetAttribute(U == 1 ? qslbm::k_batch_ib_staged<T, 1>
-                                             : (U == 2 ? qslbm::k_batch_ib_staged<T, 2> : qslbm::k_batch_ib_staged<T, 5>),
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            // the launch picks U per active set (ib_staged_unroll)
+            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
             B.ib_staged_smem = smem;
         }
     }

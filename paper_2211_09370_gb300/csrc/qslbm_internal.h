@@ -81,6 +81,7 @@ struct State {
     bool launch_error = false;  // a cudaLaunchKernelEx call failed
     int march_chunk = 16;       // z planes per CTA of the marching sweep (one wave)
     size_t ib_staged_smem = 0;  // shared memory of k_ib_staged, 0 when it does not fit
+    int ib_staged_u = 1;        // its shell nodes per thread per batch of loads (1, 2 or 5)
     bool resident_uhalo = false;
     size_t resident_smem = 0;
     void* xbuf = nullptr;   // [2][nz][3][P] plane exchange

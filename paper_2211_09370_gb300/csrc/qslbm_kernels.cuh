@@ -764,11 +764,14 @@ __host__ __device__ inline size_t ib_staged_smem_bytes(int max_ring, int max_she
     return (size_t)(13 * max_ring + 3 * max_shell) * sizeof(T) + (size_t)9 * max_ring * sizeof(int);
 }
 
-// Shell nodes a thread of the staged corrector loads at once (U), chosen for
-// the largest shell so that one batch of loads covers it, and the CTAs kept
-// resident per SM at that U (bounds the registers): with U = 5 in FP32, four
-// cover a plane per CTA of a 512-plane domain in one wave.
-inline int ib_staged_unroll(int max_shell) {
+// Shell nodes a thread of the staged corrector loads at once (U), and the CTAs
+// kept resident per SM at that U (bounds the registers).  When the launch's
+// planes fit one wave at four CTAs per SM, U is chosen for the largest shell
+// so that one batch of loads covers it (with U = 5 in FP32, four CTAs per SM
+// cover a plane per CTA of a 512-plane domain); with more planes than that,
+// U = 1 keeps eight CTAs per SM in flight.
+inline int ib_staged_unroll(int max_shell, long long planes, int sms) {
+    if (planes > 4LL * sms) return 1;
     return max_shell <= kNodeThreads ? 1 : (max_shell <= 2 * kNodeThreads ? 2 : 5);
 }
 template <typename T, int U>

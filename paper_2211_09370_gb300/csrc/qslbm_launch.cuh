@@ -102,7 +102,7 @@ struct Launch {
                 if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
                     const int R = s.ib.max_ring, S = s.ib.max_shell;
                     const size_t sm = s.ib_staged_smem;
-                    switch (ib_staged_unroll(S)) {
+                    switch (s.ib_staged_u) {
                         case 1: k_ib_staged<T, 1><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
                         case 2: k_ib_staged<T, 2><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
                         default: k_ib_staged<T, 5><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
@@ -252,7 +252,8 @@ struct Launch {
             e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
             if (e != cudaSuccess) return e;
             if (smem <= (size_t)max_optin) {
-                const int U = ib_staged_unroll(s.ib.max_shell);
+                s.ib_staged_u = ib_staged_unroll(s.ib.max_shell, s.nz, sms);
+                const int U = s.ib_staged_u;
                 e = cudaFuncSetAttribute(U == 1 ? k_ib_staged<T, 1> : (U == 2 ? k_ib_staged<T, 2> : k_ib_staged<T, 5>),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
