@@ -38,7 +38,7 @@ class _Params(C.Structure):
         ("ramp_width", C.c_double), ("force_amp", C.c_double), ("force_period", C.c_double),
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
-        ("mag_scheme", C.c_int), ("gamma", C.c_double), ("b0_field", C.c_void_p),
+        ("mag_scheme", C.c_int), ("gamma", C.c_double), ("b0_field", C.c_void_p), ("flow_q", C.c_int),
     ]
 
 
@@ -90,8 +90,10 @@ def lib():
         L.orc_kernel1d.argtypes = [C.c_double]
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_splitmix64.argtypes = [C.c_uint64]
-        L.orc_gzs_terms.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, dp, C.POINTER(C.c_int),
+        L.orc_gzs_terms.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.POINTER(C.c_int),
                                     C.POINTER(C.c_int)]
+        L.orc_flow_lattice.restype = C.c_int
+        L.orc_flow_lattice.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp]
         _lib = L
     return _lib
 
@@ -134,6 +136,7 @@ def make_params(p: dict) -> _Params:
     q.alpha = float(p.get("alpha", 1.0))
     q.mag_scheme = int(p.get("mag_scheme", 0))
     q.gamma = float(p.get("gamma", 1.0))
+    q.flow_q = int(p.get("flow_q", 0))
     f = p.get("b0_field")
     if f is not None:  # copied by orc_create; the array only has to outlive the call
         q._field = np.ascontiguousarray(f, dtype=np.float64)
@@ -232,14 +235,23 @@ def splitmix64(x: int) -> int:
     return int(lib().orc_splitmix64(int(x) & ((1 << 64) - 1)))
 
 
-def gzs_terms(dim: int, tau: float, u, F, gamma: float = 1.0):
+def gzs_terms(dim: int, tau: float, u, F, gamma: float = 1.0, flow_q: int = 0):
     """GZS forcing terms F_i for every flow-lattice direction (with the time
-    step rescaled by gamma); returns (F_i, c_i)."""
+    step rescaled by gamma; flow_q = 27 for the D3Q27 lattice); returns
+    (F_i, c_i)."""
     u = np.asarray(u, dtype=np.float64)
     F = np.asarray(F, dtype=np.float64)
-    Fi = np.zeros(19)
-    c = np.zeros(57, dtype=np.int32)
+    Fi = np.zeros(27)
+    c = np.zeros(81, dtype=np.int32)
     q = C.c_int(0)
-    lib().orc_gzs_terms(int(dim), float(tau), float(gamma), _ptr(u), _ptr(F), _ptr(Fi), C.byref(q),
+    lib().orc_gzs_terms(int(dim), int(flow_q), float(tau), float(gamma), _ptr(u), _ptr(F), _ptr(Fi), C.byref(q),
                         c.ctypes.data_as(C.POINTER(C.c_int)))
-    return Fi[: q.value], c.reshape(19, 3)[: q.value]
+    return Fi[: q.value], c.reshape(27, 3)[: q.value]
+
+
+def flow_lattice(dim: int, flow_q: int = 0):
+    """The oracle's flow lattice: (c_i [q, 3], w_i [q])."""
+    c = np.zeros(81, dtype=np.int32)
+    w = np.zeros(27)
+    q = lib().orc_flow_lattice(int(dim), int(flow_q), c.ctypes.data_as(C.POINTER(C.c_int)), _ptr(w))
+    return c.reshape(27, 3)[:q].copy(), w[:q].copy()

@@ -84,6 +84,12 @@
  *      (gamma c_m^2); time-resolved: tau_m = eta/(gamma c_m^2) + 1/2) with the
  *      flux over gamma, so that the quasi-static fixed point does not depend
  *      on gamma.  lambda and lambda_m use nu/gamma and eta/gamma.
+ *   R17 3-D flow lattice: D3Q19 unless flow_q = 27, which selects the paper's own
+ *      D3Q27 (Sec. III.A, Table I: rest 8/27, six axis 2/27, twelve edge 1/54,
+ *      eight corner 1/216; c_s^2 = 1/3).  Every sum over the flow lattice (the
+ *      equilibria of the density and momentum updates, the GZS terms and their
+ *      correction, the isotropic differences of the Lorentz force, the
+ *      diagnostics' Laplacian) runs over the chosen lattice.
  */
 #include <math.h>
 #include <stdint.h>
@@ -114,6 +120,7 @@ typedef struct orc_params {
     int mag_scheme; /* 0: quasi-static sweeps (tau_m = 1); 1: one update per step (R14) */
     double gamma;   /* time-step rescaling (Sec. V.I); 0 means 1 */
     const double* b0_field; /* ORC_B0_FIELD: [3][ny][nx], copied at creation */
+    int flow_q;     /* 3-D flow lattice: 19 (also 0) or 27 (R17) */
 } orc_params;
 
 typedef struct orc_derived {
@@ -124,8 +131,8 @@ typedef struct orc_derived {
 
 typedef struct lattice {
     int q;
-    int c[19][3];
-    double w[19];
+    int c[27][3];
+    double w[27];
 } lattice;
 
 typedef struct orc {
@@ -177,7 +184,29 @@ static void make_lattices(orc* o) {
         static const int c7[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0},
                                      {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
         static const double w7[7] = {1.0 / 4, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8};
-        set_lattice(&o->flow, 19, c19, w19);
+        if (o->p.flow_q == 27) {
+            /* Table I: the D3Q19 set plus the eight corners (+-1, +-1, +-1) */
+            int c27[27][3];
+            double w27[27];
+            for (int i = 0; i < 19; ++i)
+                for (int a = 0; a < 3; ++a) c27[i][a] = c19[i][a];
+            int i = 19;
+            for (int sz = 1; sz >= -1; sz -= 2)
+                for (int sy = 1; sy >= -1; sy -= 2)
+                    for (int sx = 1; sx >= -1; sx -= 2) {
+                        c27[i][0] = sx;
+                        c27[i][1] = sy;
+                        c27[i][2] = sz;
+                        ++i;
+                    }
+            w27[0] = 8.0 / 27;
+            for (i = 1; i <= 6; ++i) w27[i] = 2.0 / 27;
+            for (i = 7; i < 19; ++i) w27[i] = 1.0 / 54;
+            for (i = 19; i < 27; ++i) w27[i] = 1.0 / 216;
+            set_lattice(&o->flow, 27, c27, w27);
+        } else {
+            set_lattice(&o->flow, 19, c19, w19);
+        }
         set_lattice(&o->field, 7, c7, w7);
     }
 }
@@ -239,6 +268,8 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     memset(d, 0, sizeof(*d));
     d->cs2 = 1.0 / 3.0;
     d->cm2 = (p->dim == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
+    if (p->dim == 3 && !(p->flow_q == 0 || p->flow_q == 19 || p->flow_q == 27)) return -1;
+    if (p->dim == 2 && !(p->flow_q == 0 || p->flow_q == 9)) return -1;
     double R = 0.5 * p->diameter;
     if (!(R > 0)) return -1;
     d->R = R;
@@ -600,11 +631,12 @@ static double gzs(const orc* o, int i, long y) {
 }
 
 /* Same forcing term for caller-given u and F (used to pin its moments). */
-void orc_gzs_terms(int dim, double tau, double gamma, const double* u, const double* F, double* Fi, int* q_out,
-                   int* c_out) {
+void orc_gzs_terms(int dim, int flow_q, double tau, double gamma, const double* u, const double* F, double* Fi,
+                   int* q_out, int* c_out) {
     orc tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.p.dim = dim;
+    tmp.p.flow_q = flow_q;
     make_lattices(&tmp);
     const double cs2 = 1.0 / 3.0;
     for (int i = 0; i < tmp.flow.q; ++i) {
@@ -620,6 +652,21 @@ void orc_gzs_terms(int dim, double tau, double gamma, const double* u, const dou
         Fi[i] = (1.0 - 1.0 / (2.0 * tau)) * tmp.flow.w[i] * ((cF * ig - uF * ig2) / cs2 + cu * cF * ig2 / (cs2 * cs2));
     }
     *q_out = tmp.flow.q;
+}
+
+/* The flow lattice of (dim, flow_q): q velocities c[3 q] and weights w[q]
+ * (Sec. III.A; Table I for flow_q = 27).  Returns q. */
+int orc_flow_lattice(int dim, int flow_q, int* c_out, double* w_out) {
+    orc tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.p.dim = dim;
+    tmp.p.flow_q = flow_q;
+    make_lattices(&tmp);
+    for (int i = 0; i < tmp.flow.q; ++i) {
+        for (int a = 0; a < 3; ++a) c_out[3 * i + a] = tmp.flow.c[i][a];
+        w_out[i] = tmp.flow.w[i];
+    }
+    return tmp.flow.q;
 }
 
 /* Single-step flow update with the discrete-effect correction (Sec. III.E Eq.

@@ -154,11 +154,44 @@ def test_explicit_ib_close_to_implicit_on_curved_wall():
     assert after < 0.5 * before
 
 
+# ------------------------------------------------------------ flow lattices
+
+def test_d3q27_lattice_is_the_papers_table():
+    # Sec. III.A, Table I: per speed class |c|^2 the number of velocities and
+    # their weight; every velocity is distinct and in {-1, 0, 1}^3.
+    c, w = oracle.flow_lattice(3, 27)
+    assert len(set(map(tuple, c))) == 27
+    assert set(np.unique(c)) <= {-1, 0, 1}
+    sq = (c * c).sum(axis=1)
+    for k, num, a, b in _golden_lines("d3q27_table1.txt"):
+        sel = sq == int(k)
+        assert sel.sum() == int(num)
+        np.testing.assert_array_equal(w[sel], int(a) / int(b))
+
+
+@pytest.mark.parametrize("dim,flow_q,q", [(2, 0, 9), (3, 0, 19), (3, 27, 27)])
+def test_flow_lattice_moment_identities(dim, flow_q, q):
+    # What the single-step scheme needs of its lattice (Sec. III.A):
+    # sum w = 1, odd moments zero, sum w c_a c_b = c_s^2 delta_ab and the
+    # fourth moment c_s^4 (delta_ab delta_cd + delta_ac delta_bd + delta_ad
+    # delta_bc), with c_s^2 = 1/3.
+    c, w = oracle.flow_lattice(dim, flow_q)
+    assert len(w) == q
+    c = c[:, :dim].astype(float)
+    d = np.eye(dim)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(np.einsum("i,ia->a", w, c), 0.0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, c, c), d / 3, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0.0, atol=1e-16)
+    four = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), four, atol=1e-16)
+
+
 # ------------------------------------------------------------ forcing moments
 
 @pytest.mark.parametrize("gamma", [1.0, 2.5])
-@pytest.mark.parametrize("dim", [2, 3])
-def test_gzs_moments(dim, gamma):
+@pytest.mark.parametrize("dim,flow_q", [(2, 0), (3, 0), (3, 27)])
+def test_gzs_moments(dim, flow_q, gamma):
     # Sec. V.A: sum F_i = 0, sum c_i F_i = (1-1/2tau) F,
     # sum c_i c_i F_i = (1-1/2tau)(u F + F u), exactly on the lattice.  With the
     # time step rescaled (Sec. V.I) the first moment is (1-1/2tau) F/gamma and
@@ -170,7 +203,7 @@ def test_gzs_moments(dim, gamma):
         F = rng.uniform(-1e-3, 1e-3, 3)
         if dim == 2:
             u[2] = F[2] = 0.0
-        Fi, c = oracle.gzs_terms(dim, tau, u, F, gamma)
+        Fi, c = oracle.gzs_terms(dim, tau, u, F, gamma, flow_q)
         k = 1 - 1 / (2 * tau)
         assert abs(Fi.sum()) < 1e-18
         np.testing.assert_allclose(c.T @ Fi, k * F / gamma, rtol=1e-12, atol=1e-19)
@@ -210,12 +243,14 @@ def test_channel_shear_mode_decays_at_discrete_rate(gamma):
     np.testing.assert_allclose(uu[1], 0.0, atol=1e-15)
 
 
+@pytest.mark.parametrize("flow_q", [0, 27])
 @pytest.mark.parametrize("gamma", [1.0, 3.0])
-def test_uniform_flow_gains_exactly_the_body_force(gamma):
+def test_uniform_flow_gains_exactly_the_body_force(gamma, flow_q):
     # Uniform fields in a periodic box: every neighbour equilibrium equals the
     # local one, the discrete-effect correction vanishes and rho u gains F per
     # step (Sec. V.A update), F/gamma with the rescaled time step; rho stays one.
-    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0, gamma=gamma)
+    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0, gamma=gamma,
+                     flow_q=flow_q)
     o = oracle.Oracle(p)
     d = o.derived()
     u0 = np.array([0.01, -0.02, 0.005])
@@ -229,8 +264,13 @@ def test_uniform_flow_gains_exactly_the_body_force(gamma):
     np.testing.assert_allclose(rho, 1.0, atol=1e-14)
 
 
-def test_3d_shear_wave_exact_at_rest():
-    p = W.small_pipe(nx=8, ny=6, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0)
+@pytest.mark.parametrize("flow_q", [0, 27])
+def test_3d_shear_wave_exact_at_rest(flow_q):
+    # A shear wave u_z(x) in a periodic box: the update reduces to
+    # u <- u + nu lap_h u + F with lap_h the 3-point Laplacian along x (both
+    # lattices put weight c_s^2/2 on each x neighbour class), so the mode
+    # decays by exactly 1 - 4 nu sin^2(pi/8) per step.
+    p = W.small_pipe(nx=8, ny=6, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0, flow_q=flow_q)
     o = oracle.Oracle(p)
     d = o.derived()
     x = np.arange(8, dtype=float)
@@ -246,10 +286,11 @@ def test_3d_shear_wave_exact_at_rest():
     np.testing.assert_allclose(uu[2], np.broadcast_to(want, (4, 6, 8)), rtol=0, atol=1e-15)
 
 
-def test_mass_conserved_to_roundoff():
+@pytest.mark.parametrize("flow_q", [0, 27])
+def test_mass_conserved_to_roundoff(flow_q):
     # Sec. III.C density update: the coefficients 3/2 - 1 + 1/2 sum to one over
     # a periodic box and the IB corrects velocity only.
-    o = oracle.Oracle(W.small_pipe(nx=16, ny=16, nz=6, diameter=10.0, n_mag=20, perturb=0.05))
+    o = oracle.Oracle(W.small_pipe(nx=16, ny=16, nz=6, diameter=10.0, n_mag=20, perturb=0.05, flow_q=flow_q))
     o.step(15)
     ob = o.observables()
     assert abs(ob["mass_drift"]) < 1e-13
