@@ -44,6 +44,9 @@ WORKLOADS = {
     # 203 = ceil(270 * 3/4) sweeps damp as much as 270 plain ones
     "pipe64a": ("pipe_64x64x128 as above with the accelerated sweep, alpha = 3/4, N_mag = 203",
                 lambda rank: W.pipe_64x64x128(seed=2211 + rank, alpha=0.75, n_mag=203)),
+    # the same pipe on the paper's own D3Q27 flow lattice (Sec. III.A, Table I)
+    "pipe64q27": ("pipe_64x64x128 as above with the D3Q27 flow lattice",
+                  lambda rank: W.pipe_64x64x128(seed=2211 + rank, flow_q=27)),
     # the non-uniform-field pipe (above L2): measurement of the HBM-bound path
     "ramp96": ("pipe_ramp_96x96x512 D3Q19+D3Q7 D=88 tanh-ramped B0 Ha_max=50 Re=500 Rm=1e-2 N_mag=270 "
                "pulsating force (20k-step workload, per step)",

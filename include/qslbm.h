@@ -91,7 +91,7 @@ extern "C" {
  * Sec. IV: pipe, insulating walls, pressure gradient; Sec. VI: non-uniform
  * applied field).  qslbm_params_init fills the defaults noted here. */
 typedef struct qslbm_params {
-    int32_t dim;            /* 2 (D2Q9 + D2Q5) or 3 (D3Q19 + D3Q7); default 3      */
+    int32_t dim;            /* 2 (D2Q9 + D2Q5) or 3 (D3Q19 or D3Q27 + D3Q7); default 3 */
     int32_t nx, ny, nz;     /* periodic box in lattice nodes; 2-D uses nz = 1      */
     int32_t geometry;       /* QSLBM_CHANNEL | QSLBM_PIPE | QSLBM_PERIODIC         */
     double diameter;        /* pipe diameter / wall distance D, lattice units      */
@@ -127,6 +127,8 @@ typedef struct qslbm_params {
                                means 1); the body-force period is in physical time */
     const double* b0_field; /* QSLBM_B0_FIELD: [3][ny][nx] binary64, read (copied) by
                                qslbm_create only; NULL otherwise                 */
+    int32_t flow_q;         /* 3-D flow lattice: 19 (D3Q19; default, 0 also) or 27
+                               (D3Q27 of Sec. III.A, Table I); 2-D: 0 or 9        */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 
@@ -140,6 +142,7 @@ typedef struct qslbm_units {
     int64_t shell_nodes;  /* nodes inside the support of some wall marker */
     int32_t sweep_kernel; /* the QSLBM_SWEEP_* kernel in use (never AUTO)        */
     double tau_m;         /* relaxation time of the magnetic update (1 for QS)  */
+    int32_t flow_q;       /* velocities of the flow lattice: 9, 19 or 27        */
 } qslbm_units;
 
 /* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2

@@ -97,6 +97,7 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     u.F0 = (p.geometry == QSLBM_CHANNEL ? 2.0 : 4.0) * u.nu * U0 / (u.R * u.R);
     u.c_mag = 2.0 * u.eta / (g * u.cm2);
     u.tau_m = 1.0;
+    u.flow_q = p.dim == 2 ? 9 : (p.flow_q == 27 ? 27 : 19);
     int n = p.n_mag > 0 ? p.n_mag : ceil_rel(u.c_mag);
     if (p.n_mag <= 0 && p.n_mag_cap > 0) n = std::min(n, p.n_mag_cap);
     u.n_mag = std::max(n, 1);
@@ -131,6 +132,8 @@ int validate(const qslbm_params& p) {
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
     if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_SPLIT) return QSLBM_EINVAL;
     if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
+    if (p.dim == 3 && p.flow_q != 0 && p.flow_q != 19 && p.flow_q != 27) return QSLBM_EINVAL;
+    if (p.dim == 2 && p.flow_q != 0 && p.flow_q != 9) return QSLBM_EINVAL;
     {
         // accelerated sweep: the checkerboard gain (2 w_0 - 2 + alpha)/alpha
         // stays >= -1 only for alpha >= 1 - w_0 (w_0 = 1/4 on D3Q7, 1/3 on D2Q5)

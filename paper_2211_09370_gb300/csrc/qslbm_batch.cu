@@ -33,6 +33,7 @@ template <typename T>
 struct InstDesc {
     Geo g;
     int n_mag;
+    int flow_q;      // 19 or 27: the instance's 3-D flow lattice
     int bpar, fpar;  // parity of b and of (drho, u) at the start of the current step
     int bpp;         // node blocks per plane
     T* b[2];
@@ -147,7 +148,10 @@ __global__ void __launch_bounds__(kNodeThreads) k_batch_force(const InstDesc<T>*
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         const int y = p / nx;
         const int x = p - y * nx;
-        force_node<T, 3>(b, D.F, D.g.n, nx, ny, D.g.nz, x, y, z, (long long)z * P + p, D.fc, fb);
+        if (D.flow_q == 27)  // uniform across the CTA (one instance plane)
+            force_node<T, 3, 27>(b, D.F, D.g.n, nx, ny, D.g.nz, x, y, z, (long long)z * P + p, D.fc, fb);
+        else
+            force_node<T, 3>(b, D.F, D.g.n, nx, ny, D.g.nz, x, y, z, (long long)z * P + p, D.fc, fb);
     }
 }
 
@@ -168,7 +172,10 @@ __global__ void __launch_bounds__(kPlaneThreads) k_batch_flow(InstDesc<T>* __res
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         const int y = p / nx;
         const int x = p - y * nx;
-        flow_node<T, 3>(dr, u, D.F, dro, uo, n, nx, ny, nz, x, y, z, base + p, D.flc);
+        if (D.flow_q == 27)
+            flow_node<T, 3, 27>(dr, u, D.F, dro, uo, n, nx, ny, nz, x, y, z, base + p, D.flc);
+        else
+            flow_node<T, 3>(dr, u, D.F, dro, uo, n, nx, ny, nz, x, y, z, base + p, D.flc);
     }
     ib_plane<T>(D.ibu, uo, uo + n, uo + 2 * n, base, D.ibu.zinv ? 0 : z, sdelta);
     if (z == 0 && threadIdx.x == 0) *D.tdev += 1;
@@ -239,6 +246,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     std::memset(&D, 0, sizeof(D));
     D.g = qslbm::Geo{s.nx, s.ny, s.nz, s.n};
     D.n_mag = s.units.n_mag;
+    D.flow_q = s.units.flow_q;
     D.bpar = s.bcur;
     D.fpar = s.fcur;
     D.bpp = (s.nx * s.ny + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads;

@@ -918,24 +918,17 @@ __global__ void __launch_bounds__(kNodeThreads, (kIbStagedMinBlocks<T, U>))
 }
 
 // ---------------------------------------------------------------------------
-// Lattice tables for the flow update.
+// Lattice tables for the flow update: D2Q9, D3Q19, and the paper's own D3Q27
+// (Sec. III.A, Table I).  Q is the number of velocities; the 3-D tables list
+// the rest velocity, the 6 axis, the 12 edge (D3Q19 ends here) and the 8
+// corner velocities.
 template <int DIM>
-struct FlowLattice;
-
-template <>
-struct FlowLattice<3> {
-    static constexpr int Q = 19;
-};
-template <>
-struct FlowLattice<2> {
-    static constexpr int Q = 9;
-};
+constexpr int kDefaultFlowQ = DIM == 3 ? 19 : 9;
 
 __device__ __forceinline__ void flow_dir3(int j, int& cx, int& cy, int& cz) {
-    // D3Q19 non-rest directions 1..18: 6 axis then 12 edge directions
-    const int tx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-    const int ty[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-    const int tz[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    const int tx[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    const int ty[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+    const int tz[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, 1, -1, -1, -1, -1};
     cx = tx[j];
     cy = ty[j];
     cz = tz[j];
@@ -947,10 +940,19 @@ __device__ __forceinline__ void flow_dir2(int j, int& cx, int& cy, int& cz) {
     cy = ty[j];
     cz = 0;
 }
+template <int Q>
+__device__ __forceinline__ void flow_dir(int j, int& cx, int& cy, int& cz) {
+    if constexpr (Q == 9)
+        flow_dir2(j, cx, cy, cz);
+    else
+        flow_dir3(j, cx, cy, cz);
+}
 
-template <int DIM>
+template <int Q>
 __device__ __forceinline__ double flow_w(int j) {
-    if (DIM == 3) return j == 0 ? 1.0 / 3.0 : (j <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    static_assert(Q == 9 || Q == 19 || Q == 27, "flow lattices: D2Q9, D3Q19, D3Q27");
+    if (Q == 27) return j == 0 ? 8.0 / 27.0 : (j <= 6 ? 2.0 / 27.0 : (j <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
+    if (Q == 19) return j == 0 ? 1.0 / 3.0 : (j <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
     return j == 0 ? 4.0 / 9.0 : (j <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
@@ -958,7 +960,7 @@ __device__ __forceinline__ double flow_w(int j) {
 // Force: J = curl b by isotropic differences on the flow lattice
 // (d_beta phi = 3 sum_i w_i c_i,beta phi(x + c_i)), F = F_body(t) e_axis +
 // J x (B^ext + b).  One thread per node.
-template <typename T, int DIM>
+template <typename T, int DIM, int Q = kDefaultFlowQ<DIM>>
 __device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restrict__ F, long long n, int nx, int ny,
                                            int nz, int x, int y, int z, long long k, const ForceCoef<T>& c,
                                            T fb) {
@@ -970,14 +972,11 @@ __device__ __forceinline__ void force_node(const T* __restrict__ b, T* __restric
 #pragma unroll
         for (int a = 0; a < 3; ++a) db[be][a] = T(0);
 #pragma unroll
-    for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+    for (int j = 1; j < Q; ++j) {
         int cx, cy, cz;
-        if (DIM == 3)
-            flow_dir3(j, cx, cy, cz);
-        else
-            flow_dir2(j, cx, cy, cz);
+        flow_dir<Q>(j, cx, cy, cz);
         const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
-        const T w = (T)(3.0 * flow_w<DIM>(j));
+        const T w = (T)(3.0 * flow_w<Q>(j));
         const T bq[3] = {b[q], b1[q], b2[q]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -1004,7 +1003,7 @@ __device__ __forceinline__ T body_force_at(const ForceCoef<T>& c, long long t) {
     return (T)fb_d;
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int Q = kDefaultFlowQ<DIM>>
 __global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T* __restrict__ F,
                                                ForceCoef<T> c, const long long* __restrict__ tstep) {
     const long long n = g.n;
@@ -1015,7 +1014,7 @@ __global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T
         const int x = (int)(k % nx);
         const int y = (int)((k / nx) % ny);
         const int z = (int)(k / ((long long)nx * ny));
-        force_node<T, DIM>(b, F, n, nx, ny, nz, x, y, z, k, c, fb);
+        force_node<T, DIM, Q>(b, F, n, nx, ny, nz, x, y, z, k, c, fb);
     }
 }
 
@@ -1030,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_force(Geo g, const T* __restrict__ b, T
 // q_i = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u, and the GZS terms
 // F_j + F_jbar = (1 - 1/2tau) w_j (-6 u.F + 18 (c_j.u)(c_j.F)).  This uses
 // sum_i f_i^eq(x) = rho and sum_i c_i f_i^eq(x) = rho u, exact on the lattice.
-template <typename T, int DIM>
+template <typename T, int DIM, int Q = kDefaultFlowQ<DIM>>
 __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* __restrict__ u,
                                           const T* __restrict__ F, T* __restrict__ drho_out, T* uout, long long n,
                                           int nx, int ny, int nz, int x, int y, int z, long long k,
@@ -1044,17 +1043,14 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
     const T ux0 = u[k], uy0 = u[k + n], uz0 = u[k + 2 * n];
     const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
     const T q0 = T(-1.5) * uu0 * c.ig;
-    const T w0 = (T)flow_w<DIM>(0);
+    const T w0 = (T)flow_w<Q>(0);
     T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
     T m[3] = {T(0), T(0), T(0)};
     T corr[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+    for (int j = 1; j < Q; ++j) {
         int cx, cy, cz;
-        if (DIM == 3)
-            flow_dir3(j, cx, cy, cz);
-        else
-            flow_dir2(j, cx, cy, cz);
+        flow_dir<Q>(j, cx, cy, cz);
         const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
         const T dr = drho[q];
         const T uq[3] = {u[q], u1[q], u2[q]};
@@ -1063,7 +1059,7 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
         const T uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
         const T cF = (T)cx * Fq[0] + (T)cy * Fq[1] + (T)cz * Fq[2];
         const T uF = uq[0] * Fq[0] + uq[1] * Fq[1] + uq[2] * Fq[2];
-        const T w = (T)flow_w<DIM>(j);
+        const T w = (T)flow_w<Q>(j);
         const T sq = (T(4.5) * a * a - T(1.5) * uu) * c.ig;
         const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
         const T fj = w * (dr + qp + dr * qp);
@@ -1097,7 +1093,7 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
     }
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int Q = kDefaultFlowQ<DIM>>
 __global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __restrict__ drho,
                                                            const T* __restrict__ u, const T* __restrict__ F,
                                                            T* __restrict__ drho_out, T* uout, FlowCoef<T> c,
@@ -1112,7 +1108,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_flow_ib(Geo g, const T* __res
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         const int y = p / nx;
         const int x = p - y * nx;
-        flow_node<T, DIM>(drho, u, F, drho_out, uout, n, nx, ny, nz, x, y, z, base + p, c);
+        flow_node<T, DIM, Q>(drho, u, F, drho_out, uout, n, nx, ny, nz, x, y, z, base + p, c);
     }
     ib_plane<T>(ib, uout, uout + n, uout + 2 * n, base, ib.zinv ? 0 : z, sdelta);
     if (blockIdx.x == 0 && threadIdx.x == 0) *tstep += 1;
@@ -1202,7 +1198,7 @@ struct ObsCoef {
     const T* bext_xy;  // [3][nx ny] in-plane applied field, or nullptr
 };
 
-template <typename T, int DIM>
+template <typename T, int DIM, int Q = kDefaultFlowQ<DIM>>
 __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __restrict__ drho,
                                                             const T* __restrict__ u, const T* __restrict__ b,
                                                             const T* __restrict__ usnap, ObsCoef<T> c,
@@ -1259,14 +1255,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_observe(Geo g, const T* __re
         L lap[3] = {L(0), L(0), L(0)};
         L db[3][3] = {{L(0), L(0), L(0)}, {L(0), L(0), L(0)}, {L(0), L(0), L(0)}};
 #pragma unroll
-        for (int j = 1; j < FlowLattice<DIM>::Q; ++j) {
+        for (int j = 1; j < Q; ++j) {
             int cx, cy, cz;
-            if (DIM == 3)
-                flow_dir3(j, cx, cy, cz);
-            else
-                flow_dir2(j, cx, cy, cz);
+            flow_dir<Q>(j, cx, cy, cz);
             const int q = (wrapi(z + cz, nz) * ny + wrapi(y + cy, ny)) * nx + wrapi(x + cx, nx);
-            const L w = (L)flow_w<DIM>(j);
+            const L w = (L)flow_w<Q>(j);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 lap[a] += w * ((L)u[q + a * n] - (L)ut[a]);

@@ -321,7 +321,10 @@ struct Launch {
         T* dro = (T*)s.drho[1 - s.fcur];
         T* uo = (T*)s.u[1 - s.fcur];
         T* F = (T*)s.F;
-        if (s.dim == 3) {
+        if (s.dim == 3 && s.units.flow_q == 27) {
+            k_force<T, 3, 27><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), b, F, fc, s.tdev);
+            k_flow_ib<T, 3, 27><<<s.nz, kPlaneThreads, ib_smem(s), st>>>(geo(s), dr, u, F, dro, uo, c, v, s.tdev);
+        } else if (s.dim == 3) {
             k_force<T, 3><<<grid_for(s.n, 256), 256, 0, st>>>(geo(s), b, F, fc, s.tdev);
             k_flow_ib<T, 3><<<s.nz, kPlaneThreads, ib_smem(s), st>>>(geo(s), dr, u, F, dro, uo, c, v, s.tdev);
         } else {
@@ -348,7 +351,10 @@ struct Launch {
         const T* dr = (const T*)s.drho[s.fcur];
         const T* u = (const T*)s.u[s.fcur];
         const T* b = (const T*)s.b[s.bcur];
-        if (s.dim == 3)
+        if (s.dim == 3 && s.units.flow_q == 27)
+            k_observe<T, 3, 27><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
+                                                                        s.partial);
+        else if (s.dim == 3)
             k_observe<T, 3><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
                                                                     s.partial);
         else

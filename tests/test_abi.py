@@ -45,6 +45,7 @@ def test_struct_layouts_match_header_sizes():
     dict(alpha=0.7), dict(alpha=1.5), dict(alpha=-1.0),
     dict(mag_scheme=2), dict(mag_scheme=1),  # the second: tau_m far above 7/6 at Rm = 1e-3
     dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), dict(gamma=-1.0), dict(b0_kind="field"),
+    dict(flow_q=15), dict(flow_q=9), dict(dim=2, nz=1, flow_q=27),
 ])
 def test_invalid_parameters_rejected_before_device(bad):
     p = W.small_pipe(**bad)

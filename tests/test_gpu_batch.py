@@ -28,13 +28,16 @@ def uneven(precision, n=5):
         # the six-magnet in-plane applied field (Sec. VI)
         W.small_pipe(nx=22, ny=22, nz=6, diameter=16.0, Ha=12.0, Rm=5e-3, n_mag=30, b0_kind="field",
                      b0_field=W.six_magnet_field(22, 22, 16.0), precision=precision, seed=6),
+        # the paper's D3Q27 flow lattice (Sec. III.A, Table I)
+        W.small_pipe(nx=24, ny=20, nz=8, diameter=15.0, Ha=15.0, Rm=2e-2, n_mag=40, flow_q=27,
+                     precision=precision, seed=7),
     ]
     return ps[:n]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_batch_members_match_single_instances(precision):
-    ps = uneven(precision, n=6)
+    ps = uneven(precision, n=7)
     steps = 6
     with Batch(ps) as B:
         info = B.info()
@@ -62,6 +65,17 @@ def test_batch_member_matches_oracle_fp64():
     _, ou, ob = o.state()
     assert rel(u, ou) <= 1e-12 and rel(b, ob) <= 1e-12
     assert obs["step"] == 4
+
+
+def test_batch_d3q27_member_matches_oracle_fp64():
+    ps = uneven("fp64", 7)
+    with Batch([ps[0], ps[6]]) as B:
+        B.step(4)
+        _, u, b = B.member(1).state()
+    o = oracle.Oracle(ps[6])
+    o.step(4)
+    _, ou, ob = o.state()
+    assert rel(u, ou) <= 1e-12 and rel(b, ob) <= 1e-12
 
 
 def test_batch_steps_in_chunks_equal_one_call():

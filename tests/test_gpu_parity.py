@@ -235,8 +235,39 @@ def test_six_magnet_field_observables_and_auto_kernel_fp64():
         assert g[k] == pytest.approx(w[k], rel=1e-9, abs=1e-300), k
 
 
-def test_observables_match_oracle_fp64():
-    p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0)
+# the paper's own D3Q27 flow lattice (Sec. III.A, Table I): the 3-D cases
+# above on it, every sweep kernel, both precisions
+Q27_CASES = {k: (dict(p, flow_q=27), steps, t0) for k, (p, steps, t0) in FP64_CASES.items() if p["dim"] == 3}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(Q27_CASES))
+def test_d3q27_parity(name, precision, kernel):
+    p, steps, t0 = Q27_CASES[name]
+    p = dict(p, precision=precision, sweep_kernel=kernel)
+    with Solver(p) as s:
+        assert s.units["flow_q"] == 27
+    got, want, _ = run_both(p, steps, t0=t0)
+    check_fields(got, want, precision, name + " D3Q27")
+
+
+def test_d3q27_differs_from_d3q19():
+    # the lattice choice reaches the result: the same case on the two lattices
+    # differs far beyond the FP64 bound
+    p, steps, t0 = FP64_CASES["smooth_pipe_long"]
+    outs = []
+    for q in (0, 27):
+        with Solver(dict(p, precision="fp64", flow_q=q)) as s:
+            s.step(steps)
+            outs.append(s.state()[1])
+    assert rel(outs[1], outs[0]) > 1e-6
+
+
+@pytest.mark.parametrize("flow_q", [0, 27])
+def test_observables_match_oracle_fp64(flow_q):
+    p = W.small_pipe(nx=26, ny=26, nz=8, diameter=18.0, precision="fp64", Ha=10.0, Rm=1e-2, perturb=0.0,
+                     flow_q=flow_q)
     o = oracle.Oracle(p)
     with Solver(p) as s:
         s.step(10)
