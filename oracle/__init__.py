@@ -27,6 +27,7 @@ _lib = None
 
 GEOMETRY = {"channel": 0, "pipe": 1, "none": 2}
 B0_KIND = {"uniform": 0, "tanh": 1, "field": 2}
+FLOW_SCHEME = {"single_step": 0, "macroscopic": 1}
 
 
 class _Params(C.Structure):
@@ -39,13 +40,14 @@ class _Params(C.Structure):
         ("n_mag", C.c_int), ("n_mag_cap", C.c_int), ("nu_ref", C.c_double), ("eta_ref", C.c_double),
         ("seed", C.c_uint64), ("perturb", C.c_double), ("strict_qs", C.c_int), ("alpha", C.c_double),
         ("mag_scheme", C.c_int), ("gamma", C.c_double), ("b0_field", C.c_void_p), ("flow_q", C.c_int),
+        ("flow_scheme", C.c_int),
     ]
 
 
 class _Derived(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
-    _fields_ += [("n_mag", C.c_int), ("n_markers", C.c_int), ("tau_m", C.c_double)]
+    _fields_ += [("n_mag", C.c_int), ("n_markers", C.c_int), ("tau_m", C.c_double), ("gamma", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -137,6 +139,7 @@ def make_params(p: dict) -> _Params:
     q.mag_scheme = int(p.get("mag_scheme", 0))
     q.gamma = float(p.get("gamma", 1.0))
     q.flow_q = int(p.get("flow_q", 0))
+    q.flow_scheme = FLOW_SCHEME[p.get("flow_scheme", "single_step")]
     f = p.get("b0_field")
     if f is not None:  # copied by orc_create; the array only has to outlive the call
         q._field = np.ascontiguousarray(f, dtype=np.float64)

@@ -30,10 +30,10 @@
  *               c = 6 eta (c_s^2 = c^2/3), N_mag = ceil(1/dt)
  *   Sec. IV     Eq. "Energy balance equations", Eq. "variable force"
  *   Sec. V.H    Eq. "Error l2 decay" (QS residual)
- *   Sec. III.E  Eq. "single-step algorithm for MHD de rosis": the magnetic
+ *   Sec. III.D  Eq. "single-step algorithm for MHD de rosis": the magnetic
  *               update for any tau_m (mag_scheme = 1: one update per flow step,
  *               the induction equation advanced in time, not quasi-static)
- *   Sec. V.I    rescaled time step dt/gamma (Eq. "adaptative time step delta t",
+ *   Sec. VII    rescaled time step dt/gamma (Eq. "adaptative time step delta t",
  *               "adaptative time step lattice velocities", "rescaled relaxation
  *               time"): second-order f^eq terms and the g^eq flux over gamma,
  *               tau = nu/(gamma c_s^2) + 1/2, the GZS terms with gamma
@@ -90,6 +90,18 @@
  *      equilibria of the density and momentum updates, the GZS terms and their
  *      correction, the isotropic differences of the Lorentz force, the
  *      diagnostics' Laplacian) runs over the chosen lattice.
+ *   R18 Macroscopic flow scheme for tau >= 1 (flow_scheme = 1; Sec. V.G
+ *      "Stability improvements for high values of viscosity and resistivity",
+ *      Eqs. "densities MAC", "momentum Mac"): tau = 1 at particle speed
+ *      c = 6 nu (dx = 1, dt = 1/c).  In the rescaled-time-step form of R15 this
+ *      is gamma = 6 nu, which makes tau = nu/(gamma c_s^2) + 1/2 = 1; rho is
+ *      sum_i f_i^eq(x - c_i) and rho u is sum_i c_i f_i^eq(x - c_i), the
+ *      single-step momentum update at tau = 1.  The paper gives no forcing for
+ *      this scheme: the single-step GZS terms and correction at tau = 1 are
+ *      used, with the force per step over gamma as in R15, and the magnetic
+ *      algorithm runs with the same time step.  It needs 6 nu >= 1 (tau >= 1
+ *      in the single-step scheme at gamma = 1), and the automatic U0 then
+ *      drops its tau <= 1 bound.
  */
 #include <math.h>
 #include <stdint.h>
@@ -118,15 +130,17 @@ typedef struct orc_params {
     int strict_qs;
     double alpha; /* accelerated sweep (Sec. V.H); 0 means 1, the plain sweep */
     int mag_scheme; /* 0: quasi-static sweeps (tau_m = 1); 1: one update per step (R14) */
-    double gamma;   /* time-step rescaling (Sec. V.I); 0 means 1 */
+    double gamma;   /* time-step rescaling (Sec. VII); 0 means 1 */
     const double* b0_field; /* ORC_B0_FIELD: [3][ny][nx], copied at creation */
     int flow_q;     /* 3-D flow lattice: 19 (also 0) or 27 (R17) */
+    int flow_scheme; /* 0: single-step; 1: macroscopic scheme for tau >= 1 (R18) */
 } orc_params;
 
 typedef struct orc_derived {
     double R, U0, nu, tau, eta, B0, F0, c_mag, lambda, lambda_m, cs2, cm2;
     int n_mag, n_markers;
     double tau_m; /* relaxation time of the magnetic update: 1, or R14 */
+    double gamma; /* time-step rescaling in use (R15; 6 nu for R18) */
 } orc_derived;
 
 typedef struct lattice {
@@ -273,11 +287,12 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     double R = 0.5 * p->diameter;
     if (!(R > 0)) return -1;
     d->R = R;
+    if (p->flow_scheme != 0 && p->flow_scheme != 1) return -1;
     double U0 = p->U0;
     if (!(U0 > 0)) {
         U0 = 0.05;
         double tau_cap = p->Re * d->cs2 / (2.0 * R);
-        if (tau_cap < U0) U0 = tau_cap;
+        if (tau_cap < U0 && p->flow_scheme == 0) U0 = tau_cap; /* R18: no tau bound */
         if (p->Ha > 0) {
             double lor_cap = p->Re * R / (2.0 * p->Ha * p->Ha);
             if (lor_cap < U0) U0 = lor_cap;
@@ -285,7 +300,12 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     }
     d->U0 = U0;
     d->nu = U0 * R / p->Re;                 /* Re = U0 L / nu  (Sec. II)        */
-    const double g = p->gamma > 0 ? p->gamma : 1.0;
+    double g = p->gamma > 0 ? p->gamma : 1.0;
+    if (p->flow_scheme == 1) { /* R18: c = 6 nu, tau = 1 */
+        if (g != 1.0 || !(6.0 * d->nu >= 1.0 - 1e-12)) return -1;
+        g = 6.0 * d->nu;
+    }
+    d->gamma = g;
     d->tau = d->nu / (g * d->cs2) + 0.5;    /* nu = gamma c_s^2 (tau - 1/2)    */
     d->eta = U0 * R / p->Rm;                /* Rm = U0 L / eta                  */
     d->B0 = p->Ha * sqrt(d->eta * d->nu) / R; /* Ha = B0 L / sqrt(eta nu)       */
@@ -508,7 +528,7 @@ static double geq(const orc* o, int i, int a, long y) {
 /* One sweep of the tau_m = 1 scheme (Sec. V.G, Eq. "Single step algoritm for
  * magnetic field"): b_alpha(x) <- sum_i g^eq_{i alpha}(x - e_i); with the
  * accelerated equilibria of Sec. V.H the sum is multiplied by 1/alpha.  With
- * mag_scheme = 1 the update of Sec. III.E for any tau_m:
+ * mag_scheme = 1 the update of Sec. III.D for any tau_m:
  * b_alpha(x) <- sum_i { g_i(x - e_i) + (tau_m - 1) [g_i(x + e_i) - 2 g_i(x) + g_i(x - e_i)] }. */
 static void sweep(orc* o) {
     long n = o->n;
@@ -624,7 +644,7 @@ static double gzs(const orc* o, int i, long y) {
         uF += o->u[a][y] * o->F[a][y];
     }
     ciF = cF;
-    /* rescaled (Sec. V.I): [(c_i - u/gamma)/(gamma c_s^2) + (c_i . u) c_i/(gamma^2 c_s^4)] . F */
+    /* rescaled (Sec. VII): [(c_i - u/gamma)/(gamma c_s^2) + (c_i . u) c_i/(gamma^2 c_s^4)] . F */
     const double ig = o->ig, ig2 = o->ig * o->ig;
     return (1.0 - 1.0 / (2.0 * o->d.tau)) * o->flow.w[i] *
            ((ciF * ig - uF * ig2) / cs2 + cu * cF * ig2 / (cs2 * cs2));
@@ -685,7 +705,10 @@ static void flow_update(orc* o) {
             long km = node(o, x - c[0], y - c[1], z - c[2]);
             long kp = node(o, x + c[0], y + c[1], z + c[2]);
             double fm = feq(o, i, km), f0 = feq(o, i, k), fp = feq(o, i, kp);
-            rho += 1.5 * fm - f0 + 0.5 * fp;
+            if (o->p.flow_scheme == 1)
+                rho += fm; /* R18: Eq. "densities MAC" */
+            else
+                rho += 1.5 * fm - f0 + 0.5 * fp;
             double mom = fm + (tau - 1.0) * (fp - 2.0 * f0 + fm);
             double corr = -0.5 * tau * (gzs(o, i, kp) - gzs(o, i, km));
             for (int a = 0; a < 3; ++a) m[a] += c[a] * mom + c[a] * corr;
@@ -733,11 +756,12 @@ orc* orc_create(const orc_params* p) {
     if (o->p.dim == 2) o->p.nz = 1;
     if (o->p.alpha == 0.0) o->p.alpha = 1.0;
     if (!(o->p.gamma > 0.0)) o->p.gamma = 1.0;
-    o->ig = 1.0 / o->p.gamma;
     if (orc_derive(&o->p, &o->d) != 0) {
         free(o);
         return NULL;
     }
+    o->p.gamma = o->d.gamma; /* R18 sets it from nu */
+    o->ig = 1.0 / o->p.gamma;
     make_lattices(o);
     if (o->p.b0_kind == ORC_B0_FIELD) {
         long P = (long)o->p.nx * o->p.ny;

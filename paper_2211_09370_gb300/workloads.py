@@ -10,7 +10,8 @@ marker_spacing, Re, Ha, Rm, U0 (0 = automatic), b0_kind ('uniform' | 'tanh' |
 'field'), b0_dir, ramp_center, ramp_width, b0_field ([3][ny][nx] for 'field'), force_amp, force_period, n_mag (0 = automatic),
 n_mag_cap (0 = no cap), nu_ref, eta_ref, precision ('fp32' | 'fp64'), seed,
 perturb, steps (horizon of the workload), flow_q (3-D flow lattice: 0 or 19 for
-D3Q19, 27 for the paper's D3Q27).
+D3Q19, 27 for the paper's D3Q27), flow_scheme ('single_step' | 'macroscopic',
+the tau >= 1 scheme).
 """
 from __future__ import annotations
 
@@ -26,7 +27,7 @@ def _base(**kw):
     p = dict(dim=3, geometry="pipe", center=NAN2, marker_spacing=1.0, U0=0.0, b0_kind="uniform",
              b0_dir=(1.0, 0.0, 0.0), ramp_center=0.0, ramp_width=1.0, force_amp=0.0, force_period=0.0,
              n_mag=0, n_mag_cap=270, nu_ref=0.0, eta_ref=0.0, precision="fp32", seed=0, perturb=0.0,
-             strict_qs=0, flow_q=0)
+             strict_qs=0, flow_q=0, flow_scheme="single_step")
     p.update(kw)
     return p
 

@@ -153,7 +153,7 @@ def test_accelerated_sweep_parity_2d_channel():
 
 
 TIME_CASES = {
-    # time-resolved magnetic update (Sec. III.E, one per flow step), tau_m 0.9 and 0.7
+    # time-resolved magnetic update (Sec. III.D, one per flow step), tau_m 0.9 and 0.7
     "pipe_ramp": (dict(nx=24, ny=22, nz=10, diameter=16.0, U0=0.05, Re=50.0, Ha=10.0, Rm=4.0, b0_kind="tanh",
                        ramp_center=5.0, ramp_width=2.0, perturb=0.0, mag_scheme=1), 60),
     "pipe_odd": (dict(nx=21, ny=19, nz=6, diameter=14.0, U0=0.05, Re=30.0, Ha=8.0, Rm=7.0, perturb=0.0,
@@ -181,7 +181,7 @@ def test_time_resolved_update_parity_2d_channel():
 
 
 GAMMA_CASES = {
-    # time step rescaled by gamma (Sec. V.I): quasi-static sweeps, gamma = 2
+    # time step rescaled by gamma (Sec. VII): quasi-static sweeps, gamma = 2
     "qs_ramp": (dict(nx=24, ny=22, nz=10, diameter=16.0, U0=0.05, Re=50.0, Ha=20.0, Rm=0.05, b0_kind="tanh",
                      ramp_center=5.0, ramp_width=2.0, perturb=0.0, n_mag=30, force_amp=0.2, force_period=40.0,
                      gamma=2.0), 40),

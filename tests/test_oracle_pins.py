@@ -194,7 +194,7 @@ def test_flow_lattice_moment_identities(dim, flow_q, q):
 def test_gzs_moments(dim, flow_q, gamma):
     # Sec. V.A: sum F_i = 0, sum c_i F_i = (1-1/2tau) F,
     # sum c_i c_i F_i = (1-1/2tau)(u F + F u), exactly on the lattice.  With the
-    # time step rescaled (Sec. V.I) the first moment is (1-1/2tau) F/gamma and
+    # time step rescaled (Sec. VII) the first moment is (1-1/2tau) F/gamma and
     # the second (1-1/2tau)(u F + F u)/gamma^2.
     rng = np.random.default_rng(7 + dim)
     for _ in range(20):
@@ -220,7 +220,7 @@ def test_channel_shear_mode_decays_at_discrete_rate(gamma):
     # unidirectional u_x(y) the update reduces to u <- u + nu lap_h u + F, so
     # the parabola F y (31 - y)/(2 nu) is steady and the mode sin(pi y/31)
     # decays by exactly 1 - 4 nu sin^2(pi/62) per step.  With the time step
-    # rescaled by gamma (Sec. V.I) a step carries nu/gamma and F/gamma: the
+    # rescaled by gamma (Sec. VII) a step carries nu/gamma and F/gamma: the
     # same parabola, the mode decaying by 1 - 4 (nu/gamma) sin^2(pi/62).
     p = W.hartmann_channel_2d(Ha=0.0, n_mag=1, gamma=gamma)
     o = oracle.Oracle(p)
@@ -284,6 +284,97 @@ def test_3d_shear_wave_exact_at_rest(flow_q):
     g = (1 - 4 * d["nu"] * math.sin(math.pi / 8) ** 2) ** n
     want = n * d["F0"] + eps * g * np.sin(2 * np.pi * x / 8)
     np.testing.assert_allclose(uu[2], np.broadcast_to(want, (4, 6, 8)), rtol=0, atol=1e-15)
+
+
+def _mac(**kw):
+    return dict(flow_scheme="macroscopic", **kw)
+
+
+def test_macroscopic_scheme_mapping():
+    # Sec. V.G: tau = 1 at particle speed c = 6 nu, i.e. the time step 1/(6 nu);
+    # the automatic U0 drops its tau <= 1 bound; below 6 nu = 1 it is refused
+    p = W.small_pipe(nx=136, ny=136, nz=8, diameter=128.0, Re=10.0, Ha=0.0)
+    d1, d2 = oracle.derive(p), oracle.derive(dict(p, **_mac()))
+    assert d1["tau"] == pytest.approx(1.0, abs=1e-15) and d1["U0"] < 0.05
+    assert d2["U0"] == 0.05 and d2["gamma"] == pytest.approx(6 * d2["nu"], rel=1e-15)
+    assert d2["tau"] == pytest.approx(1.0, abs=1e-15)
+    with pytest.raises(ValueError):
+        oracle.derive(dict(p, Re=1000.0, **_mac()))  # 6 nu < 1
+    with pytest.raises(ValueError):
+        oracle.derive(dict(p, gamma=2.0, **_mac()))  # the scheme sets the time step itself
+
+
+def test_macroscopic_channel_shear_mode_decays_at_discrete_rate():
+    # Ha = 0 channel on the macroscopic scheme: a unidirectional u_x(y) keeps
+    # rho = 1 exactly (every neighbour class of the density sum balances), so
+    # the update is u <- u + (nu/gamma) lap_h u + F/gamma with gamma = 6 nu:
+    # the parabola F y (31 - y)/(2 nu) is steady and sin(pi y/31) decays by
+    # 1 - (2/3) sin^2(pi/62) per step.
+    p = W.hartmann_channel_2d(Ha=0.0, n_mag=1, U0=0.05, Re=2.0, **_mac())
+    o = oracle.Oracle(p)
+    d = o.derived()
+    nu, F = d["nu"], d["F0"]
+    assert d["gamma"] == pytest.approx(6 * nu, rel=1e-15)
+    y = np.arange(32, dtype=float)
+    parab = F * y * (31 - y) / (2 * nu)
+    eps = 1e-3
+    u = np.zeros((3, 1, 32, 64))
+    u[0, 0] = (parab + eps * np.sin(np.pi * y / 31))[:, None]
+    o.set_state(rho=np.ones((1, 32, 64)), u=u, b=np.zeros_like(u), t=0)
+    n = 60
+    o.step(n)
+    rho, uu, _ = o.state()
+    g = (1 - 4 / 6 * math.sin(math.pi / 62) ** 2) ** n
+    want = parab + eps * g * np.sin(np.pi * y / 31)
+    np.testing.assert_allclose(uu[0, 0], np.broadcast_to(want[:, None], (32, 64)), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("flow_q", [0, 27])
+@pytest.mark.parametrize("scheme", ["single_step", "macroscopic"])
+def test_density_wave_follows_the_linear_update(scheme, flow_q):
+    # A small density wave along x in a periodic box, u = 0 at the start.  To
+    # first order f_i^eq = w_i (rho + 3 c_i.j), and both lattices put weight
+    # 2/3 on c_x = 0 and 1/6 on each of c_x = +-1, so per Fourier mode k:
+    #   macroscopic (Sec. V.G: rho = sum f^eq(x - c), j = sum c f^eq(x - c))
+    #     rho' = (2 + cos k)/3 rho - i sin k j,   j' = -(i/3) sin k rho + cos k j;
+    #   single-step density (Sec. III.E: 3/2 f^eq(x - c) - f^eq(x) + 1/2 f^eq(x + c))
+    #     rho' = (1 + 2 cos k)/3 rho - i sin k j, the same j' at tau = 1.
+    # The two schemes differ at O(1); the body force adds only a uniform u_z.
+    kw = dict(nx=16, ny=4, nz=4, geometry="none", diameter=100.0, U0=0.01, Re=1.0, Ha=0.0, n_mag=1,
+              perturb=0.0, flow_q=flow_q)
+    if scheme == "macroscopic":
+        kw.update(_mac())
+    else:
+        kw.update(Re=3.0)  # nu = 1/6: tau = 1 on the single-step scheme as well
+    o = oracle.Oracle(W.small_pipe(**kw))
+    assert o.derived()["tau"] == pytest.approx(1.0, abs=1e-14)
+    eps = 1e-6
+    k = 2 * np.pi / 16
+    x = np.arange(16, dtype=float)
+    rho0 = np.broadcast_to(1 + eps * np.cos(k * x), (4, 4, 16)).copy()
+    o.set_state(rho=rho0, u=np.zeros((3, 4, 4, 16)), b=np.zeros((3, 4, 4, 16)), t=0)
+    n = 12
+    o.step(n)
+    rho, u, _ = o.state()
+    if scheme == "macroscopic":
+        M = np.array([[(2 + np.cos(k)) / 3, -1j * np.sin(k)], [-1j / 3 * np.sin(k), np.cos(k)]])
+    else:
+        M = np.array([[(1 + 2 * np.cos(k)) / 3, -1j * np.sin(k)], [-1j / 3 * np.sin(k), np.cos(k)]])
+    v = np.linalg.matrix_power(M, n) @ np.array([eps, 0.0])
+    want_rho = 1 + np.real(v[0] * np.exp(1j * k * x))
+    want_u = np.real(v[1] * np.exp(1j * k * x))
+    np.testing.assert_allclose(rho[0, 0], want_rho, rtol=0, atol=1e-3 * eps)
+    np.testing.assert_allclose(u[0, 0, 0], want_u, rtol=0, atol=1e-3 * eps)
+
+
+def test_mass_conserved_on_the_macroscopic_scheme():
+    # sum_x sum_i f_i^eq(x - c_i) = sum_x rho over a periodic box
+    p = W.small_pipe(nx=16, ny=16, nz=6, diameter=10.0, n_mag=20, perturb=0.05, U0=0.05, Re=1.0, **_mac())
+    o = oracle.Oracle(p)
+    o.step(15)
+    ob = o.observables()
+    assert abs(ob["mass_drift"]) < 1e-13 and ob["nan_flag"] == 0
 
 
 @pytest.mark.parametrize("flow_q", [0, 27])
@@ -393,7 +484,7 @@ def test_accelerated_sweep_stability_bound():
 
 
 def _full_update_case(dim, **kw):
-    # mag_scheme = 1 (Sec. III.E update for any tau_m, one per flow step);
+    # mag_scheme = 1 (Sec. III.D update for any tau_m, one per flow step);
     # U0 = 0.05, R = 5: eta = 0.25 / Rm, tau_m = eta / c_m^2 + 1/2
     if dim == 3:
         p = W.small_pipe(nx=12, ny=4, nz=4, geometry="none", diameter=10.0, U0=0.05, Rm=3.0, Ha=0.0,
