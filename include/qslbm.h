@@ -81,8 +81,17 @@ extern "C" {
 #define QSLBM_SWEEP_RESIDENT 2
 #define QSLBM_SWEEP_SPLIT 3
 
+/* Flow schemes.  SINGLE_STEP: the single-step update (Sec. III.E, V.A), tau < 1.
+ * MACROSCOPIC: the tau = 1 scheme at particle speed c = 6 nu for tau >= 1
+ * (Sec. V.G Eqs. "densities MAC", "momentum Mac"): the time step is rescaled
+ * by gamma = 6 nu (Sec. VII form), rho and rho u come from the neighbours'
+ * equilibria, the force enters as in the single-step scheme at tau = 1; needs
+ * 6 nu >= 1 and gamma = 0 or 1; the automatic U0 drops its tau <= 1 bound. */
+#define QSLBM_FLOW_SINGLE_STEP 0
+#define QSLBM_FLOW_MACROSCOPIC 1
+
 #define QSLBM_MAG_QS 0   /* quasi-static: N_mag tau_m = 1 sweeps per flow step  */
-#define QSLBM_MAG_TIME 1 /* time-resolved: one update of Sec. III.E Eq. "single-
+#define QSLBM_MAG_TIME 1 /* time-resolved: one update of Sec. III.D Eq. "single-
                             step algorithm for MHD de rosis" per flow step, with
                             tau_m = eta/c_m^2 + 1/2 (lattice speed 1); needs
                             1/2 < tau_m <= 7/6 (3-D) or 5/4 (2-D) and alpha = 1 */
@@ -121,7 +130,7 @@ typedef struct qslbm_params {
                                1 (default; 0 also means 1) is the plain sweep; stable
                                for 1 - w_0 <= alpha <= 1 (3/4 in 3-D, 2/3 in 2-D) */
     int32_t mag_scheme;     /* QSLBM_MAG_QS (default) | QSLBM_MAG_TIME             */
-    double gamma;           /* time step rescaled to dt/gamma (Sec. V.I): equilibria,
+    double gamma;           /* time step rescaled to dt/gamma (Sec. VII): equilibria,
                                relaxation times and forcing rescaled; forces and
                                resistivity per step over gamma; 1 (default; 0 also
                                means 1); the body-force period is in physical time */
@@ -129,6 +138,7 @@ typedef struct qslbm_params {
                                qslbm_create only; NULL otherwise                 */
     int32_t flow_q;         /* 3-D flow lattice: 19 (D3Q19; default, 0 also) or 27
                                (D3Q27 of Sec. III.A, Table I); 2-D: 0 or 9        */
+    int32_t flow_scheme;    /* QSLBM_FLOW_SINGLE_STEP (default) | QSLBM_FLOW_MACROSCOPIC */
     void* stream;           /* cudaStream_t to queue work on, or NULL              */
 } qslbm_params;
 
@@ -143,6 +153,8 @@ typedef struct qslbm_units {
     int32_t sweep_kernel; /* the QSLBM_SWEEP_* kernel in use (never AUTO)        */
     double tau_m;         /* relaxation time of the magnetic update (1 for QS)  */
     int32_t flow_q;       /* velocities of the flow lattice: 9, 19 or 27        */
+    double gamma;         /* time-step rescaling in use (6 nu on the macroscopic
+                             scheme)                                            */
 } qslbm_units;
 
 /* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2

@@ -307,6 +307,7 @@ int orc_derive(const orc_params* p, orc_derived* d) {
     }
     d->gamma = g;
     d->tau = d->nu / (g * d->cs2) + 0.5;    /* nu = gamma c_s^2 (tau - 1/2)    */
+    if (p->flow_scheme == 1) d->tau = 1.0;  /* R18: the scheme is tau = 1      */
     d->eta = U0 * R / p->Rm;                /* Rm = U0 L / eta                  */
     d->B0 = p->Ha * sqrt(d->eta * d->nu) / R; /* Ha = B0 L / sqrt(eta nu)       */
     if (p->geometry == ORC_CHANNEL)

@@ -37,7 +37,7 @@ class qslbm_params(C.Structure):
         ("precision", C.c_int32), ("strict_qs", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
         ("init_kind", C.c_int32), ("sweep_kernel", C.c_int32), ("alpha", C.c_double),
         ("mag_scheme", C.c_int32), ("gamma", C.c_double), ("b0_field", C.c_void_p), ("flow_q", C.c_int32),
-        ("stream", C.c_void_p),
+        ("flow_scheme", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -46,7 +46,7 @@ class qslbm_units(C.Structure):
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
     _fields_ += [("n_mag", C.c_int32), ("n_markers", C.c_int32), ("nodes", C.c_int64), ("device_bytes", C.c_int64),
                 ("shell_nodes", C.c_int64), ("sweep_kernel", C.c_int32), ("tau_m", C.c_double),
-                ("flow_q", C.c_int32)]
+                ("flow_q", C.c_int32), ("gamma", C.c_double)]
 
 
 class qslbm_obs(C.Structure):
@@ -207,6 +207,7 @@ def make_params(p: dict, stream: int | None = None) -> qslbm_params:
     q.mag_scheme = int(p.get("mag_scheme", 0))
     q.gamma = float(p.get("gamma", 1.0))
     q.flow_q = int(p.get("flow_q", 0))
+    q.flow_scheme = {"single_step": 0, "macroscopic": 1}[p.get("flow_scheme", "single_step")]
     f = p.get("b0_field")
     if f is not None:  # read by qslbm_create; the array only has to outlive that call
         q._field = np.ascontiguousarray(f, dtype=np.float64)

@@ -85,13 +85,15 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     double U0 = p.U0;
     if (!(U0 > 0)) {
         U0 = 0.05;
-        U0 = std::min(U0, p.Re * u.cs2 / (2.0 * u.R));
+        if (p.flow_scheme != QSLBM_FLOW_MACROSCOPIC) U0 = std::min(U0, p.Re * u.cs2 / (2.0 * u.R));
         if (p.Ha > 0) U0 = std::min(U0, p.Re * u.R / (2.0 * p.Ha * p.Ha));
     }
     u.U0 = U0;
     u.nu = U0 * u.R / p.Re;
-    const double g = p.gamma > 0 ? p.gamma : 1.0;  // time step dt/gamma (Sec. V.I)
-    u.tau = u.nu / (g * u.cs2) + 0.5;
+    // time step dt/gamma (Sec. VII); the macroscopic scheme's c = 6 nu (Sec. V.G)
+    const double g = p.flow_scheme == QSLBM_FLOW_MACROSCOPIC ? 6.0 * u.nu : (p.gamma > 0 ? p.gamma : 1.0);
+    u.gamma = g;
+    u.tau = p.flow_scheme == QSLBM_FLOW_MACROSCOPIC ? 1.0 : u.nu / (g * u.cs2) + 0.5;
     u.eta = U0 * u.R / p.Rm;
     u.B0 = p.Ha * std::sqrt(u.eta * u.nu) / u.R;
     u.F0 = (p.geometry == QSLBM_CHANNEL ? 2.0 : 4.0) * u.nu * U0 / (u.R * u.R);
@@ -134,6 +136,16 @@ int validate(const qslbm_params& p) {
     if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
     if (p.dim == 3 && p.flow_q != 0 && p.flow_q != 19 && p.flow_q != 27) return QSLBM_EINVAL;
     if (p.dim == 2 && p.flow_q != 0 && p.flow_q != 9) return QSLBM_EINVAL;
+    if (p.flow_scheme != QSLBM_FLOW_SINGLE_STEP && p.flow_scheme != QSLBM_FLOW_MACROSCOPIC) return QSLBM_EINVAL;
+    if (p.flow_scheme == QSLBM_FLOW_MACROSCOPIC) {
+        if (!(p.gamma == 0.0 || p.gamma == 1.0)) return QSLBM_EINVAL;  // the scheme sets the time step
+        qslbm_units u;
+        map_units(p, u);
+        if (!(6.0 * u.nu >= 1.0 - 1e-12)) {
+            g_last_error = "macroscopic flow scheme: 6 nu = " + std::to_string(6.0 * u.nu) + " < 1 (tau < 1)";
+            return QSLBM_EINVAL;
+        }
+    }
     {
         // accelerated sweep: the checkerboard gain (2 w_0 - 2 + alpha)/alpha
         // stays >= -1 only for alpha >= 1 - w_0 (w_0 = 1/4 on D3Q7, 1/3 on D2Q5)
@@ -466,7 +478,7 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
     s.cy = std::isnan(s.p.center[1]) ? 0.5 * (s.ny - 1) : s.p.center[1];
     s.R = s.units.R;
     s.axis = s.dim == 3 ? 2 : 0;
-    s.ig = 1.0 / (s.p.gamma > 0 ? s.p.gamma : 1.0);
+    s.ig = 1.0 / s.units.gamma;
     // the modulation runs on physical time t/gamma
     s.omega = s.p.force_amp != 0.0 ? 2.0 * M_PI / s.p.force_period * s.ig : 0.0;
     if (s.dim == 3) {

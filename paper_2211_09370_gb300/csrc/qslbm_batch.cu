@@ -272,6 +272,7 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     D.fc.bext_xy = (const T*)s.bext_xy;
     D.flc.tau = (T)s.units.tau;
     D.flc.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+    D.flc.mac = s.p.flow_scheme == QSLBM_FLOW_MACROSCOPIC;
     D.flc.ig = (T)s.ig;
     D.flc.ig2 = (T)(s.ig * s.ig);
     for (int m = 0; m < 2; ++m) {

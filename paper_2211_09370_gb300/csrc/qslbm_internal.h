@@ -96,19 +96,19 @@ struct State {
 // covering three forms of the same sum:
 //   - the tau_m = 1 sweep (Sec. V.G): w_0, w_axis, 1/(c c_m^2);
 //   - the accelerated sweep (Sec. V.H): (w_0 - 1 + alpha)/alpha, w_axis/alpha;
-//   - the time-resolved update for any tau_m (Sec. III.E, de Rosis form), whose
+//   - the time-resolved update for any tau_m (Sec. III.D, de Rosis form), whose
 //     sum_i {g_i(x - e_i) + (tau_m - 1)[g_i(x + e_i) - 2 g_i(x) + g_i(x - e_i)]}
 //     is (2 tau_m - 1) times the plain neighbour sum of b, plus the plain flux
 //     sum, minus 2 (tau_m - 1) b, since the flux terms of g_i(x + e_i) are
 //     those of g_i(x - e_i) with the sign reversed and sum_i g_i(x) = b.
-// With the time step rescaled by gamma (Sec. V.I) the flux carries 1/gamma.
+// With the time step rescaled by gamma (Sec. VII) the flux carries 1/gamma.
 // At alpha = 1, tau_m = 1 and gamma = 1 every weight is exactly the plain one.
 template <typename T>
 inline void sweep_weights(const State& s, T& w0, T& w1, T& kappa) {
     const double tm = s.units.tau_m, a = s.alpha;
     w0 = (T)(((2.0 * tm - 1.0) * s.w0 - 2.0 * (tm - 1.0) + (a - 1.0)) / a);
     w1 = (T)((2.0 * tm - 1.0) * s.w1 / a);
-    kappa = (T)(s.kappa / (2.0 * tm - 1.0) * s.ig);  // flux over gamma (Sec. V.I)
+    kappa = (T)(s.kappa / (2.0 * tm - 1.0) * s.ig);  // flux over gamma (Sec. VII)
 }
 
 // Kernel launchers, one table per storage precision.

@@ -82,7 +82,8 @@ template <typename T>
 struct FlowCoef {
     T tau;        // relaxation time
     T kforce;     // 1 - 1/(2 tau)
-    T ig, ig2;    // 1/gamma, 1/gamma^2 (time step rescaled, Sec. V.I; 1 by default)
+    T ig, ig2;    // 1/gamma, 1/gamma^2 (time step rescaled, Sec. VII; 1 by default)
+    int mac;      // 1: density of the macroscopic scheme, sum_i f_i^eq(x - c_i) (Sec. V.G)
 };
 
 template <typename T>
@@ -1044,7 +1045,9 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
     const T uu0 = ux0 * ux0 + uy0 * uy0 + uz0 * uz0;
     const T q0 = T(-1.5) * uu0 * c.ig;
     const T w0 = (T)flow_w<Q>(0);
-    T rho_acc = T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
+    // single-step density (Sec. III.E) or the macroscopic scheme's (Sec. V.G);
+    // c.mac is uniform across the launch
+    T rho_acc = c.mac ? w0 * (dr0 + q0 + dr0 * q0) : T(2) * w0 * (dr0 + q0 + dr0 * q0) - dr0;
     T m[3] = {T(0), T(0), T(0)};
     T corr[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -1064,7 +1067,10 @@ __device__ __forceinline__ void flow_node(const T* __restrict__ drho, const T* _
         const T qp = T(3) * a + sq, qm = T(-3) * a + sq;
         const T fj = w * (dr + qp + dr * qp);
         const T fjb = w * (dr + qm + dr * qm);
-        rho_acc += T(0.5) * fj + T(1.5) * fjb;
+        if (c.mac)
+            rho_acc += fjb;  // f^eq of direction -c_j at x + c_j
+        else
+            rho_acc += T(0.5) * fj + T(1.5) * fjb;
         const T mom = tm1 * fj - tau * fjb;
         const T fs = c.kforce * w * (T(-6) * uF + T(18) * a * cF) * c.ig2;
         if (cx) {

@@ -312,6 +312,7 @@ struct Launch {
         FlowCoef<T> c;
         c.tau = (T)s.units.tau;
         c.kforce = (T)(1.0 - 1.0 / (2.0 * s.units.tau));
+        c.mac = s.p.flow_scheme == QSLBM_FLOW_MACROSCOPIC;
         c.ig = (T)s.ig;
         c.ig2 = (T)(s.ig * s.ig);
         const IBView<T> v = view(s, false);

@@ -46,6 +46,8 @@ def test_struct_layouts_match_header_sizes():
     dict(mag_scheme=2), dict(mag_scheme=1),  # the second: tau_m far above 7/6 at Rm = 1e-3
     dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), dict(gamma=-1.0), dict(b0_kind="field"),
     dict(flow_q=15), dict(flow_q=9), dict(dim=2, nz=1, flow_q=27),
+    dict(flow_scheme="macroscopic"),  # Re = 100: 6 nu < 1, tau < 1
+    dict(flow_scheme="macroscopic", Re=1.0, Ha=5.0, gamma=2.0),
 ])
 def test_invalid_parameters_rejected_before_device(bad):
     p = W.small_pipe(**bad)

@@ -31,13 +31,16 @@ def uneven(precision, n=5):
         # the paper's D3Q27 flow lattice (Sec. III.A, Table I)
         W.small_pipe(nx=24, ny=20, nz=8, diameter=15.0, Ha=15.0, Rm=2e-2, n_mag=40, flow_q=27,
                      precision=precision, seed=7),
+        # the macroscopic scheme for tau >= 1 (Sec. V.G)
+        W.small_pipe(nx=20, ny=22, nz=7, diameter=15.0, Re=1.0, Ha=5.0, Rm=5e-2, n_mag=50,
+                     flow_scheme="macroscopic", precision=precision, seed=8),
     ]
     return ps[:n]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_batch_members_match_single_instances(precision):
-    ps = uneven(precision, n=7)
+    ps = uneven(precision, n=8)
     steps = 6
     with Batch(ps) as B:
         info = B.info()
@@ -67,15 +70,17 @@ def test_batch_member_matches_oracle_fp64():
     assert obs["step"] == 4
 
 
-def test_batch_d3q27_member_matches_oracle_fp64():
-    ps = uneven("fp64", 7)
-    with Batch([ps[0], ps[6]]) as B:
+@pytest.mark.parametrize("k", [6, 7])  # D3Q27; the macroscopic scheme
+def test_batch_variant_member_matches_oracle_fp64(k):
+    ps = uneven("fp64", 8)
+    with Batch([ps[0], ps[k]]) as B:
         B.step(4)
-        _, u, b = B.member(1).state()
-    o = oracle.Oracle(ps[6])
+        rho, u, b = B.member(1).state()
+    o = oracle.Oracle(ps[k])
     o.step(4)
-    _, ou, ob = o.state()
+    orho, ou, ob = o.state()
     assert rel(u, ou) <= 1e-12 and rel(b, ob) <= 1e-12
+    assert np.abs(rho - orho).max() <= 1e-12
 
 
 def test_batch_steps_in_chunks_equal_one_call():

@@ -252,6 +252,29 @@ def test_d3q27_parity(name, precision, kernel):
     check_fields(got, want, precision, name + " D3Q27")
 
 
+# the macroscopic scheme for tau >= 1 (Sec. V.G): tau = 1 at c = 6 nu, rho and
+# rho u from the neighbours' equilibria; Re = 1 puts 6 nu well above one
+MAC_CASES = {
+    "pipe": (dict(nx=29, ny=27, nz=11, diameter=19.0, Re=1.0, Ha=5.0, Rm=1e-2, perturb=0.01, seed=21), 20),
+    "ramp_pulsating_d3q27": (dict(nx=24, ny=22, nz=12, diameter=16.0, Re=0.8, Ha=6.0, Rm=2e-2, b0_kind="tanh",
+                                  ramp_center=6.0, ramp_width=2.0, force_amp=0.2, force_period=30.0,
+                                  perturb=0.01, seed=22, flow_q=27), 20),
+}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(MAC_CASES))
+def test_macroscopic_scheme_parity(name, precision, kernel):
+    kw, steps = MAC_CASES[name]
+    p = W.small_pipe(precision=precision, sweep_kernel=kernel, flow_scheme="macroscopic", **kw)
+    with Solver(p) as s:
+        u = s.units
+        assert u["tau"] == 1.0 and u["gamma"] == pytest.approx(6 * u["nu"], rel=1e-15) and u["gamma"] > 1
+    got, want, _ = run_both(p, steps)
+    check_fields(got, want, precision, name + " macroscopic")
+
+
 def test_d3q27_differs_from_d3q19():
     # the lattice choice reaches the result: the same case on the two lattices
     # differs far beyond the FP64 bound
