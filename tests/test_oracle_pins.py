@@ -627,16 +627,22 @@ def test_hartmann_steady_energy_balance(hartmann_state):
 
 
 @pytest.mark.slow
-def test_pipe_poiseuille_at_zero_hartmann():
+@pytest.mark.parametrize("variant", [{}, {"flow_q": 27}, {"flow_scheme": "macroscopic", "Re": 1.0}],
+                         ids=["d3q19", "d3q27", "macroscopic"])
+def test_pipe_poiseuille_at_zero_hartmann(variant):
     # Ha -> 0: u_z(r) = F (R^2 - r^2)/(4 nu) up to the IB wall error, which
-    # falls as the pipe is refined (first order in 1/R).
+    # falls as the pipe is refined (first order in 1/R); on either 3-D flow
+    # lattice and on the macroscopic scheme (Re = 1, tau = 1 at c = 6 nu),
+    # each run for the physical time 6 R^2/nu (gamma steps per unit).
     errs = []
     for D, box in ((16, 24), (24, 32)):
-        p = W.small_pipe(nx=box, ny=box, nz=2, diameter=float(D), Re=10.0, Ha=0.0, n_mag=1, perturb=0.0)
+        kw = dict(nx=box, ny=box, nz=2, diameter=float(D), Re=10.0, Ha=0.0, n_mag=1, perturb=0.0)
+        kw.update(variant)
+        p = W.small_pipe(**kw)
         o = oracle.Oracle(p)
         d = o.derived()
         R, nu, F = d["R"], d["nu"], d["F0"]
-        o.step(int(6 * R * R / nu))
+        o.step(int(6 * R * R / nu * d["gamma"]))
         _, u, _ = o.state()
         yy, xx = np.mgrid[0:box, 0:box]
         r = np.hypot(xx - (box - 1) / 2, yy - (box - 1) / 2)
