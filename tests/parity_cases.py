@@ -19,6 +19,24 @@ FP64_CASES = {
     "smooth_pipe_long": (W.small_pipe(nx=23, ny=21, nz=9, diameter=15.0, perturb=0.0, n_mag=60), 150, 0),
 }
 
+# the paper's own D3Q27 flow lattice (Sec. III.A, Table I): the 3-D cases above on it
+Q27_CASES = {k: (dict(p, flow_q=27), steps, t0) for k, (p, steps, t0) in FP64_CASES.items() if p["dim"] == 3}
+
+# the macroscopic scheme for tau >= 1 (Sec. V.G): tau = 1 at c = 6 nu, rho and
+# rho u from the neighbours' equilibria; Re = 1 puts 6 nu well above one
+MAC_CASES = {
+    "pipe": (dict(nx=29, ny=27, nz=11, diameter=19.0, Re=1.0, Ha=5.0, Rm=1e-2, perturb=0.01, seed=21), 20),
+    "ramp_pulsating_d3q27": (dict(nx=24, ny=22, nz=12, diameter=16.0, Re=0.8, Ha=6.0, Rm=2e-2, b0_kind="tanh",
+                                  ramp_center=6.0, ramp_width=2.0, force_amp=0.2, force_period=30.0,
+                                  perturb=0.01, seed=22, flow_q=27), 20),
+}
+
+
+def mac_case(name, **kw):
+    params, steps = MAC_CASES[name]
+    return W.small_pipe(flow_scheme="macroscopic", **params, **kw), steps
+
+
 DEGENERATE = {
     "periodic": dict(geometry="none"),
     "single_plane": dict(nz=1),

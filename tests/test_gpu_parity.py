@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_2211_09370_gb300 import workloads as W
 from paper_2211_09370_gb300._lib import EUNSTABLE, QSLBMError, Solver
-from tests.parity_cases import DEGENERATE, FP64_CASES, degenerate
+from tests.parity_cases import DEGENERATE, FP64_CASES, MAC_CASES, Q27_CASES, degenerate, mac_case
 
 pytestmark = pytest.mark.gpu
 
@@ -235,11 +235,8 @@ def test_six_magnet_field_observables_and_auto_kernel_fp64():
         assert g[k] == pytest.approx(w[k], rel=1e-9, abs=1e-300), k
 
 
-# the paper's own D3Q27 flow lattice (Sec. III.A, Table I): the 3-D cases
-# above on it, every sweep kernel, both precisions
-Q27_CASES = {k: (dict(p, flow_q=27), steps, t0) for k, (p, steps, t0) in FP64_CASES.items() if p["dim"] == 3}
-
-
+# the paper's own D3Q27 flow lattice: the 3-D cases above on it, every sweep
+# kernel, both precisions
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", sorted(Q27_CASES))
@@ -252,22 +249,12 @@ def test_d3q27_parity(name, precision, kernel):
     check_fields(got, want, precision, name + " D3Q27")
 
 
-# the macroscopic scheme for tau >= 1 (Sec. V.G): tau = 1 at c = 6 nu, rho and
-# rho u from the neighbours' equilibria; Re = 1 puts 6 nu well above one
-MAC_CASES = {
-    "pipe": (dict(nx=29, ny=27, nz=11, diameter=19.0, Re=1.0, Ha=5.0, Rm=1e-2, perturb=0.01, seed=21), 20),
-    "ramp_pulsating_d3q27": (dict(nx=24, ny=22, nz=12, diameter=16.0, Re=0.8, Ha=6.0, Rm=2e-2, b0_kind="tanh",
-                                  ramp_center=6.0, ramp_width=2.0, force_amp=0.2, force_period=30.0,
-                                  perturb=0.01, seed=22, flow_q=27), 20),
-}
-
-
+# the macroscopic scheme for tau >= 1 (Sec. V.G), every sweep kernel, both precisions
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", sorted(MAC_CASES))
 def test_macroscopic_scheme_parity(name, precision, kernel):
-    kw, steps = MAC_CASES[name]
-    p = W.small_pipe(precision=precision, sweep_kernel=kernel, flow_scheme="macroscopic", **kw)
+    p, steps = mac_case(name, precision=precision, sweep_kernel=kernel)
     with Solver(p) as s:
         u = s.units
         assert u["tau"] == 1.0 and u["gamma"] == pytest.approx(6 * u["nu"], rel=1e-15) and u["gamma"] > 1

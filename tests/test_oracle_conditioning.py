@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.parity_cases import FP64_CASES, DEGENERATE, degenerate
+from tests.parity_cases import DEGENERATE, FP64_CASES, MAC_CASES, Q27_CASES, degenerate, mac_case
 
 
 def _sensitivity(p, steps, t0):
@@ -28,6 +28,20 @@ def _sensitivity(p, steps, t0):
 def test_fp64_parity_horizon_is_well_conditioned(name):
     p, steps, t0 = FP64_CASES[name]
     su, sb = _sensitivity(dict(p, precision="fp64"), steps, t0)
+    assert su < 1e-13 and sb < 1e-13, (su, sb)
+
+
+@pytest.mark.parametrize("name", sorted(Q27_CASES))
+def test_d3q27_parity_horizon_is_well_conditioned(name):
+    p, steps, t0 = Q27_CASES[name]
+    su, sb = _sensitivity(dict(p, precision="fp64"), steps, t0)
+    assert su < 1e-13 and sb < 1e-13, (su, sb)
+
+
+@pytest.mark.parametrize("name", sorted(MAC_CASES))
+def test_macroscopic_parity_horizon_is_well_conditioned(name):
+    p, steps = mac_case(name, precision="fp64")
+    su, sb = _sensitivity(p, steps, 0)
     assert su < 1e-13 and sb < 1e-13, (su, sb)
 
 
