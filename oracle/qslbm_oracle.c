@@ -40,6 +40,9 @@
  *   Sec. V.H    "Strategies for very high values of resistivity": the sweep
  *               with the extra coefficient alpha (Eq. "magnetic field
  *               quasi-static acelerated"); alpha = 1 is the plain sweep
+ *   Sec. III.A  Table I: the D3Q27 flow lattice (flow_q = 27)
+ *   Sec. V.G    Eqs. "densities MAC", "momentum Mac": the macroscopic flow
+ *               scheme for tau >= 1 (flow_scheme = 1, R18)
  *
  * Readings where the paper is silent or garbled (each one is also listed in the
  * design notes of the repository):
