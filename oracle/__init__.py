@@ -94,6 +94,7 @@ def lib():
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_gzs_terms.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.POINTER(C.c_int),
                                     C.POINTER(C.c_int)]
+        L.orc_flow_update_with_force.argtypes = [C.c_void_p, dp]
         L.orc_flow_lattice.restype = C.c_int
         L.orc_flow_lattice.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp]
         _lib = L
@@ -194,6 +195,11 @@ class Oracle:
 
     def step(self, n: int = 1):
         lib().orc_step(self._h, int(n))
+
+    def flow_update_with_force(self, F):
+        """One flow update with a given force field F [3][nz][ny][nx] (no IB on u)."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        lib().orc_flow_update_with_force(self._h, _ptr(F))
 
     def mag_sweeps(self, n: int):
         lib().orc_mag_sweeps(self._h, int(n))

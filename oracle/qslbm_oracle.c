@@ -745,6 +745,14 @@ void orc_step(orc* o, long nsteps) {
     for (long s = 0; s < nsteps; ++s) one_step(o);
 }
 
+/* Test hook: one flow update (density, momentum with the GZS correction,
+ * plus F) with the force field F [3 n] given by the caller instead of the
+ * Lorentz and body forces, and without the IB on u; t does not advance. */
+void orc_flow_update_with_force(orc* o, const double* F) {
+    for (int a = 0; a < 3; ++a) memcpy(o->F[a], F + (long)a * o->n, (size_t)o->n * sizeof(double));
+    flow_update(o);
+}
+
 /* -------------------------------------------------------------- lifecycle */
 
 static int in_fluid(const orc* o, int x, int y, double margin) {

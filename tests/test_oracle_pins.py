@@ -286,6 +286,36 @@ def test_3d_shear_wave_exact_at_rest(flow_q):
     np.testing.assert_allclose(uu[2], np.broadcast_to(want, (4, 6, 8)), rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("flow_q", [0, 27])
+def test_discrete_effect_correction_closed_form(flow_q):
+    # Sec. V.A: with rho = 1 and a uniform u the equilibrium sums return rho u
+    # exactly, so one update gives u + F + C with the correction
+    # C = -(tau/2) sum_i c_i [F_i(x + c_i) - F_i(x - c_i)].  For F = A sin(q x) e_x
+    # the lattice's third and fourth moments give, exactly,
+    #   C_a = -tau (1 - 1/2tau) A sin(q) cos(q x) (u_a + u_x delta_ax).
+    p = W.small_pipe(nx=16, ny=4, nz=4, geometry="none", Re=10.0, Ha=0.0, n_mag=1, perturb=0.0, flow_q=flow_q)
+    o = oracle.Oracle(p)
+    tau = o.derived()["tau"]
+    assert tau > 0.6
+    u0 = np.array([0.03, -0.02, 0.05])
+    shape = (4, 4, 16)
+    u = np.stack([np.full(shape, v) for v in u0])
+    o.set_state(rho=np.ones(shape), u=u, b=np.zeros_like(u), t=0)
+    A, q = 1e-2, 2 * np.pi * 3 / 16
+    x = np.arange(16, dtype=float)
+    F = np.zeros((3,) + shape)
+    F[0] = A * np.sin(q * x)
+    o.flow_update_with_force(F)
+    rho, uu, _ = o.state()
+    k = 1 - 1 / (2 * tau)
+    for a in range(3):
+        C = -tau * k * A * np.sin(q) * np.cos(q * x) * (u0[a] + (u0[0] if a == 0 else 0.0))
+        assert np.abs(C).max() > 1e-7  # the term is far above the rounding of u + F + C
+        got = uu[a] - u0[a] - (F[0] if a == 0 else 0.0)
+        np.testing.assert_allclose(got, np.broadcast_to(C, shape), rtol=0, atol=1e-16)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-15)
+
+
 def _mac(**kw):
     return dict(flow_scheme="macroscopic", **kw)
 
