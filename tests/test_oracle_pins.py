@@ -264,6 +264,26 @@ def test_uniform_flow_gains_exactly_the_body_force(gamma, flow_q):
     np.testing.assert_allclose(rho, 1.0, atol=1e-14)
 
 
+@pytest.mark.parametrize("gamma", [1.0, 2.0])
+def test_pulsating_body_force_phase(gamma):
+    # Sec. IV Eq. "variable force": F(t) = F0 (1 + amp sin(2 pi t / T)) with t
+    # the physical time at the start of the step (t_step / gamma); a uniform
+    # flow in a periodic box gains exactly F(t)/gamma per step.
+    amp, T = 0.3, 7.0
+    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0, gamma=gamma,
+                     force_amp=amp, force_period=T)
+    o = oracle.Oracle(p)
+    F0 = o.derived()["F0"]
+    shape = (4, 5, 6)
+    o.set_state(rho=np.ones(shape), u=np.zeros((3,) + shape), b=np.zeros((3,) + shape), t=0)
+    n = 23
+    o.step(n)
+    _, uu, _ = o.state()
+    want = sum(F0 * (1 + amp * math.sin(2 * math.pi * (t / gamma) / T)) / gamma for t in range(n))
+    np.testing.assert_allclose(uu[2], want, rtol=1e-11, atol=0)
+    np.testing.assert_allclose(uu[:2], 0.0, atol=1e-18)
+
+
 @pytest.mark.parametrize("flow_q", [0, 27])
 def test_3d_shear_wave_exact_at_rest(flow_q):
     # A shear wave u_z(x) in a periodic box: the update reduces to
@@ -487,6 +507,44 @@ def test_sweep_fixed_point_is_discrete_qs_poisson_solution(alpha, sweeps, gamma)
         np.testing.assert_allclose(b[a], want, rtol=0, atol=1e-10 * np.abs(want).max() + 1e-18)
     # at the fixed point the QS residual of the observables vanishes
     assert o.observables()["qs_residual"] < 1e-9 * np.abs(u).max() * np.abs(Be).max()
+
+
+def test_sweep_fixed_point_in_a_tanh_ramped_field():
+    # Sec. VI applied field B^ext(z) = B0 (1 + tanh((z - zc)/w))/2 along b0_dir:
+    # the converged sweep solves eta lap b = D.(u B^ext - B^ext u) with the flux
+    # formed node by node (B^ext varies with z) and the central difference D of
+    # the sweep's neighbour sum; the right-hand side is formed in real space and
+    # the 7-point Laplacian inverted by FFT on the periodic box.
+    n = 12
+    zc, w = 5.0, 2.0
+    p = W.small_pipe(nx=n, ny=n, nz=n, geometry="none", diameter=10.0, Re=10.0, Ha=5.0, Rm=0.05, U0=0.05,
+                     strict_qs=1, b0_kind="tanh", ramp_center=zc, ramp_width=w, b0_dir=(0.6, 0.8, 0.0),
+                     perturb=0.0)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    t = 2 * np.pi / n
+    u = np.stack([0.02 * np.sin(t * y) * np.cos(t * z), 0.03 * np.cos(t * x + 2 * t * z),
+                  0.01 * np.sin(t * x + t * y)])
+    o.set_state(rho=np.ones((n, n, n)), u=u, b=np.zeros_like(u), t=0)
+    o.mag_sweeps(3000)
+    _, _, b = o.state()
+    ramp = d["B0"] * 0.5 * (1 + np.tanh((z - zc) / w))
+    Be = [0.6 * ramp, 0.8 * ramp, 0.0 * ramp]
+    axis = {0: 2, 1: 1, 2: 0}  # component direction -> array axis ([z][y][x])
+    k = [np.fft.fftfreq(n) * 2 * np.pi] * 3
+    kz, ky, kx = np.meshgrid(*k, indexing="ij")
+    lap = sum(2 * np.cos(kk) - 2 for kk in (kx, ky, kz))
+    lap[0, 0, 0] = 1.0
+    for a in range(3):
+        rhs = np.zeros((n, n, n))
+        for be in range(3):
+            phi = u[be] * Be[a] - u[a] * Be[be]
+            rhs += 0.5 * (np.roll(phi, -1, axis=axis[be]) - np.roll(phi, 1, axis=axis[be]))
+        bh = np.fft.fftn(rhs) / (d["eta"] * lap)
+        bh[0, 0, 0] = 0.0
+        want = np.fft.ifftn(bh).real
+        np.testing.assert_allclose(b[a], want, rtol=0, atol=1e-10 * np.abs(want).max() + 1e-18)
 
 
 def test_accelerated_sweep_stability_bound():
