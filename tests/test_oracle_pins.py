@@ -509,17 +509,20 @@ def test_sweep_fixed_point_is_discrete_qs_poisson_solution(alpha, sweeps, gamma)
     assert o.observables()["qs_residual"] < 1e-9 * np.abs(u).max() * np.abs(Be).max()
 
 
-def test_sweep_fixed_point_in_a_tanh_ramped_field():
-    # Sec. VI applied field B^ext(z) = B0 (1 + tanh((z - zc)/w))/2 along b0_dir:
-    # the converged sweep solves eta lap b = D.(u B^ext - B^ext u) with the flux
-    # formed node by node (B^ext varies with z) and the central difference D of
-    # the sweep's neighbour sum; the right-hand side is formed in real space and
-    # the 7-point Laplacian inverted by FFT on the periodic box.
+@pytest.mark.parametrize("kind", ["tanh", "field"])
+def test_sweep_fixed_point_in_a_non_uniform_field(kind):
+    # Sec. VI applied fields, B^ext(z) = B0 (1 + tanh((z - zc)/w))/2 along b0_dir
+    # or B0 times the six-magnet in-plane field: the converged sweep solves
+    # eta lap b = D.(u B^ext - B^ext u) with the flux formed node by node and
+    # the central difference D of the sweep's neighbour sum; the right-hand
+    # side is formed in real space and the 7-point Laplacian inverted by FFT on
+    # the periodic box.
     n = 12
     zc, w = 5.0, 2.0
+    field = W.six_magnet_field(n, n, 10.0)
+    kw = dict(b0_kind="tanh", ramp_center=zc, ramp_width=w) if kind == "tanh" else dict(b0_kind="field", b0_field=field)
     p = W.small_pipe(nx=n, ny=n, nz=n, geometry="none", diameter=10.0, Re=10.0, Ha=5.0, Rm=0.05, U0=0.05,
-                     strict_qs=1, b0_kind="tanh", ramp_center=zc, ramp_width=w, b0_dir=(0.6, 0.8, 0.0),
-                     perturb=0.0)
+                     strict_qs=1, b0_dir=(0.6, 0.8, 0.0), perturb=0.0, **kw)
     o = oracle.Oracle(p)
     d = o.derived()
     z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
@@ -529,8 +532,11 @@ def test_sweep_fixed_point_in_a_tanh_ramped_field():
     o.set_state(rho=np.ones((n, n, n)), u=u, b=np.zeros_like(u), t=0)
     o.mag_sweeps(3000)
     _, _, b = o.state()
-    ramp = d["B0"] * 0.5 * (1 + np.tanh((z - zc) / w))
-    Be = [0.6 * ramp, 0.8 * ramp, 0.0 * ramp]
+    if kind == "tanh":
+        ramp = d["B0"] * 0.5 * (1 + np.tanh((z - zc) / w))
+        Be = [0.6 * ramp, 0.8 * ramp, 0.0 * ramp]
+    else:
+        Be = [d["B0"] * np.broadcast_to(field[a], (n, n, n)) for a in range(3)]
     axis = {0: 2, 1: 1, 2: 0}  # component direction -> array axis ([z][y][x])
     k = [np.fft.fftfreq(n) * 2 * np.pi] * 3
     kz, ky, kx = np.meshgrid(*k, indexing="ij")
