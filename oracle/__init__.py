@@ -95,6 +95,7 @@ def lib():
         L.orc_gzs_terms.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.POINTER(C.c_int),
                                     C.POINTER(C.c_int)]
         L.orc_flow_update_with_force.argtypes = [C.c_void_p, dp]
+        L.orc_force.argtypes = [C.c_void_p, dp]
         L.orc_flow_lattice.restype = C.c_int
         L.orc_flow_lattice.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp]
         _lib = L
@@ -200,6 +201,13 @@ class Oracle:
         """One flow update with a given force field F [3][nz][ny][nx] (no IB on u)."""
         F = np.ascontiguousarray(F, dtype=np.float64)
         lib().orc_flow_update_with_force(self._h, _ptr(F))
+
+    def force(self):
+        """The force field [3][nz][ny][nx] the next flow update adds: the body
+        force plus the Lorentz force J x (B^ext + b) of the current state."""
+        F = np.empty(3 * self.n)
+        lib().orc_force(self._h, _ptr(F))
+        return F.reshape((3,) + self.shape)
 
     def mag_sweeps(self, n: int):
         lib().orc_mag_sweeps(self._h, int(n))

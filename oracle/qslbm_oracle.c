@@ -119,6 +119,11 @@
 #define ORC_B0_TANH 1
 #define ORC_B0_FIELD 2 /* B0 times a caller-given in-plane field [3][ny][nx] */
 
+/* Node loops of smaller domains run on one thread: the fork and join of a
+ * parallel region would cost more than the loop (results are the same either
+ * way, since every iteration writes its own node). */
+#define ORC_OMP_MIN_NODES 512
+
 typedef struct orc_params {
     int dim, nx, ny, nz, geometry;
     double diameter, cx, cy, marker_spacing;
@@ -539,7 +544,7 @@ static void sweep(orc* o) {
     const double inv_alpha = 1.0 / o->p.alpha;
     const double tm = o->d.tau_m;
     const int full = o->p.mag_scheme == 1;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= ORC_OMP_MIN_NODES)
     for (long k = 0; k < n; ++k) {
         int x, y, z;
         coords(o, k, &x, &y, &z);
@@ -623,7 +628,7 @@ static void compute_force(orc* o) {
     long n = o->n;
     double fb = body_force(o, o->t);
     int ax = axis(o);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= ORC_OMP_MIN_NODES)
     for (long k = 0; k < n; ++k) {
         int x, y, z;
         coords(o, k, &x, &y, &z);
@@ -699,7 +704,7 @@ int orc_flow_lattice(int dim, int flow_q, int* c_out, double* w_out) {
 static void flow_update(orc* o) {
     long n = o->n;
     const double tau = o->d.tau;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= ORC_OMP_MIN_NODES)
     for (long k = 0; k < n; ++k) {
         int x, y, z;
         coords(o, k, &x, &y, &z);
@@ -751,6 +756,14 @@ void orc_step(orc* o, long nsteps) {
 void orc_flow_update_with_force(orc* o, const double* F) {
     for (int a = 0; a < 3; ++a) memcpy(o->F[a], F + (long)a * o->n, (size_t)o->n * sizeof(double));
     flow_update(o);
+}
+
+/* Test hook: the force field F [3 n] the next flow update would add for the
+ * current state and time (body force plus the Lorentz force J x (B^ext + b)
+ * with J = curl b by isotropic differences, Sec. V.A). */
+void orc_force(orc* o, double* F) {
+    compute_force(o);
+    for (int a = 0; a < 3; ++a) memcpy(F + (long)a * o->n, o->F[a], (size_t)o->n * sizeof(double));
 }
 
 /* -------------------------------------------------------------- lifecycle */

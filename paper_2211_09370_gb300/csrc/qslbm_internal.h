@@ -117,6 +117,11 @@ struct Ops {
     void (*sweeps)(State&, int nsweeps, cudaStream_t);  // flips bcur per sweep
     void (*force_flow)(State&, cudaStream_t);           // flips fcur
     void (*observe)(State&, double fb, cudaStream_t);   // obs_dev[0..10]
+    // the same reduction over caller-held fields (drho, u, b, u_prev in the
+    // handle's layout and precision): `blocks` partial sums into partial
+    // [blocks * kObs], folded into sums[kObs]
+    void (*observe_fields)(const State&, const void* drho, const void* u, const void* b, const void* u_prev,
+                           double fb, int blocks, double* partial, double* sums, cudaStream_t);
     void (*to_f64)(State&, cudaStream_t);               // staging <- state
     void (*from_f64)(State&, int mask, cudaStream_t);   // state <- staging
     // decide whether the resident sweep kernel fits this domain; sets

@@ -335,7 +335,7 @@ struct Launch {
         s.fcur ^= 1;
     }
 
-    static void observe(State& s, double fb, cudaStream_t st) {
+    static ObsCoef<T> obs_coef(const State& s, double fb) {
         ObsCoef<T> c;
         c.eta = s.units.eta;
         c.fb = fb;
@@ -349,19 +349,28 @@ struct Launch {
         for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
         c.bext_z = static_cast<const T*>(s.bext_z);
         c.bext_xy = static_cast<const T*>(s.bext_xy);
-        const T* dr = (const T*)s.drho[s.fcur];
-        const T* u = (const T*)s.u[s.fcur];
-        const T* b = (const T*)s.b[s.bcur];
+        return c;
+    }
+
+    static void observe_fields(const State& s, const void* drho, const void* u, const void* b, const void* usnap,
+                               double fb, int blocks, double* partial, double* sums, cudaStream_t st) {
+        const ObsCoef<T> c = obs_coef(s, fb);
+        const T* dr = (const T*)drho;
+        const T* uu = (const T*)u;
+        const T* bb = (const T*)b;
+        const T* us = (const T*)usnap;
         if (s.dim == 3 && s.units.flow_q == 27)
-            k_observe<T, 3, 27><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
-                                                                        s.partial);
+            k_observe<T, 3, 27><<<blocks, kReduceThreads, 0, st>>>(geo(s), dr, uu, bb, us, c, partial);
         else if (s.dim == 3)
-            k_observe<T, 3><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
-                                                                    s.partial);
+            k_observe<T, 3><<<blocks, kReduceThreads, 0, st>>>(geo(s), dr, uu, bb, us, c, partial);
         else
-            k_observe<T, 2><<<s.nblocks_obs, kReduceThreads, 0, st>>>(geo(s), dr, u, b, (const T*)s.usnap, c,
-                                                                    s.partial);
-        k_fold<T><<<1, 32 * kObs, 0, st>>>(s.partial, s.nblocks_obs, s.obs_dev);
+            k_observe<T, 2><<<blocks, kReduceThreads, 0, st>>>(geo(s), dr, uu, bb, us, c, partial);
+        k_fold<T><<<1, 32 * kObs, 0, st>>>(partial, blocks, sums);
+    }
+
+    static void observe(State& s, double fb, cudaStream_t st) {
+        observe_fields(s, s.drho[s.fcur], s.u[s.fcur], s.b[s.bcur], s.usnap, fb, s.nblocks_obs, s.partial,
+                       s.obs_dev, st);
     }
 
     static void to_f64(State& s, cudaStream_t st) {
@@ -375,7 +384,8 @@ struct Launch {
     }
 
     static const Ops& table() {
-        static const Ops o = {&init, &sweeps, &force_flow, &observe, &to_f64, &from_f64, &plan_resident, &plan_march};
+        static const Ops o = {&init,   &sweeps,   &force_flow,    &observe,   &observe_fields,
+                              &to_f64, &from_f64, &plan_resident, &plan_march};
         return o;
     }
 };

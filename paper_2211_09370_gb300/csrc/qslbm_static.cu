@@ -16,7 +16,6 @@
 
 #include "qslbm.h"
 #include "qslbm_internal.h"
-#include "qslbm_kernels.cuh"
 
 namespace {
 
@@ -45,33 +44,16 @@ __global__ void k_static_finish(const double* sums, double mass0, double nu, lon
     out[9] = sums[10] > 0 ? 1.0 : 0.0;
 }
 
-template <typename T>
+// The reduction runs through the handle's per-precision launcher table, so the
+// diagnostics kernels exist once per precision in the library (the FP64 ones
+// compiled without contraction) and the flow lattice is chosen as in
+// qslbm_observables.
 void launch(const qslbm::State& s, const void* drho, const void* u, const void* b, const void* u_prev, double fb,
             long long dt, double* out, double* scratch, cudaStream_t st) {
-    qslbm::ObsCoef<T> c;
-    c.eta = s.units.eta;
-    c.fb = fb;
-    c.axis = s.axis;
-    c.geometry = s.p.geometry;
-    c.strict_qs = s.p.strict_qs;
-    c.dim = s.dim;
-    c.cx = s.cx;
-    c.cy = s.cy;
-    c.rin = s.R - 2.0;
-    for (int a = 0; a < 3; ++a) c.be[a] = (T)s.be[a];
-    c.bext_z = static_cast<const T*>(s.bext_z);
-    c.bext_xy = static_cast<const T*>(s.bext_xy);
-    const qslbm::Geo g{s.nx, s.ny, s.nz, s.n};
-    const int blocks = s.nz;
+    const qslbm::Ops& ops = s.p.precision == QSLBM_FP64 ? qslbm::ops_f64() : qslbm::ops_f32();
     double* partial = scratch;
     double* sums = scratch + (size_t)kStaticMaxPlanes * qslbm::kObs;
-    if (s.dim == 3)
-        qslbm::k_observe<T, 3><<<blocks, qslbm::kReduceThreads, 0, st>>>(
-            g, (const T*)drho, (const T*)u, (const T*)b, (const T*)u_prev, c, partial);
-    else
-        qslbm::k_observe<T, 2><<<blocks, qslbm::kReduceThreads, 0, st>>>(
-            g, (const T*)drho, (const T*)u, (const T*)b, (const T*)u_prev, c, partial);
-    qslbm::k_fold<T><<<1, 32 * qslbm::kObs, 0, st>>>(partial, blocks, sums);
+    ops.observe_fields(s, drho, u, b, u_prev, fb, s.nz, partial, sums, st);
     k_static_finish<<<1, 32, 0, st>>>(sums, s.mass0, s.units.nu, dt, out);
 }
 
@@ -112,7 +94,14 @@ const State& handle_state(const qslbm_handle* h);
 extern "C" int qslbm_observables_static(const qslbm_handle* h, const void* drho, const void* u, const void* b,
                                         const void* u_prev, double fb, int64_t steps_since_prev, double* out,
                                         void* stream) {
-    if (!h || !drho || !u || !b || !u_prev || !out || steps_since_prev < 0) return QSLBM_EINVAL;
+    if (!h || !drho || !u || !b || !u_prev || !out) {
+        qslbm::set_last_error("qslbm_observables_static: a handle, field or output pointer is NULL");
+        return QSLBM_EINVAL;
+    }
+    if (steps_since_prev < 0) {
+        qslbm::set_last_error("qslbm_observables_static: steps_since_prev is negative");
+        return QSLBM_EINVAL;
+    }
     const qslbm::State& s = qslbm::handle_state(h);
     if (s.nz > kStaticMaxPlanes) {
         qslbm::set_last_error("qslbm_observables_static: " + std::to_string(s.nz) + " z planes exceed the limit of " +
@@ -126,11 +115,7 @@ extern "C" int qslbm_observables_static(const qslbm_handle* h, const void* drho,
         qslbm::set_last_error(err);
         return rc;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s.p.precision == QSLBM_FP64)
-        launch<double>(s, drho, u, b, u_prev, fb, steps_since_prev, out, scratch, st);
-    else
-        launch<float>(s, drho, u, b, u_prev, fb, steps_since_prev, out, scratch, st);
+    launch(s, drho, u, b, u_prev, fb, steps_since_prev, out, scratch, static_cast<cudaStream_t>(stream));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         qslbm::set_last_error(std::string("qslbm_observables_static: ") + cudaGetErrorString(e));

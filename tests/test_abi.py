@@ -73,3 +73,12 @@ def test_bounded_wait_check_rejects_bad_limits_before_the_device():
     assert L.qslbm_check_bounded_wait(0.0, 0, C.byref(g), C.byref(w)) == _lib.EINVAL
     assert L.qslbm_check_bounded_wait(5.0, 0, C.byref(g), C.byref(w)) == _lib.EINVAL
     assert L.qslbm_check_bounded_wait(0.1, 0, None, C.byref(w)) == _lib.EINVAL
+
+
+def test_static_diagnostics_null_arguments_set_the_error_text():
+    # a NULL handle or a negative step count is refused on the host, and the
+    # reason is left in qslbm_last_error like every other refusal
+    L = _lib.load()
+    rc = L.qslbm_observables_static(None, None, None, None, None, 0.0, 0, None, None)
+    assert rc == _lib.EINVAL
+    assert b"NULL" in L.qslbm_last_error()

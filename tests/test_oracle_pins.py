@@ -745,3 +745,234 @@ def test_pipe_poiseuille_at_zero_hartmann(variant):
         errs.append(np.linalg.norm((u[2, 0] - ex)[msk]) / np.linalg.norm(ex[msk]))
     assert errs[1] < errs[0] < 8e-2, errs
     assert errs[1] < 5e-2, errs
+
+
+# ------------------------------------- Lorentz force and diagnostics, closed form
+
+def _sin_fields(shape, rng):
+    """Smooth periodic fields whose every component is a sum of one-dimensional
+    waves, one wave along each axis (the component's own axis included, which
+    its curl must ignore).  Returns the fields and, per component and axis, the
+    wave's (amplitude, wavenumber, phase)."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz, dtype=float), np.arange(ny, dtype=float), np.arange(nx, dtype=float),
+                          indexing="ij")
+    coords = (x, y, z)
+    n_axes = (nx, ny, nz)
+    waves = [[None] * 3 for _ in range(3)]
+    f = np.zeros((3,) + shape)
+    for comp in range(3):
+        for ax in range(3):
+            if n_axes[ax] == 1:
+                continue
+            amp = rng.uniform(0.5, 1.5) * (1 if rng.random() < 0.5 else -1)
+            q = 2 * np.pi * rng.integers(1, 3) / n_axes[ax]
+            ph = rng.uniform(0, 2 * np.pi)
+            waves[comp][ax] = (amp, q, ph)
+            f[comp] += amp * np.sin(q * coords[ax] + ph)
+    return f, waves, coords
+
+
+def _central_diff(waves, comp, ax, coords):
+    """(phi(x + e) - phi(x - e)) / 2 of component comp along axis ax, in closed
+    form: a wave A sin(q s + p) gives A sin(q) cos(q s + p)."""
+    w = waves[comp][ax]
+    if w is None:
+        return np.zeros_like(coords[0])
+    amp, q, ph = w
+    return amp * math.sin(q) * np.cos(q * coords[ax] + ph)
+
+
+def _second_diff(waves, comp, ax, coords):
+    """phi(x + e) + phi(x - e) - 2 phi(x) of a wave: -2 (1 - cos q) A sin(q s + p)."""
+    w = waves[comp][ax]
+    if w is None:
+        return np.zeros_like(coords[0])
+    amp, q, ph = w
+    return -2.0 * (1.0 - math.cos(q)) * amp * np.sin(q * coords[ax] + ph)
+
+
+LORENTZ_CASES = [(3, 0, (8, 10, 12)), (3, 27, (8, 10, 12)), (2, 0, (1, 14, 16))]
+
+
+def _analytic_case(dim, flow_q, shape, seed):
+    nz, ny, nx = shape
+    p = W.small_pipe(nx=nx, ny=ny, nz=nz, diameter=6.0, geometry="none", dim=dim, flow_q=flow_q, Ha=12.0,
+                     Rm=0.05, Re=40.0, b0_dir=(0.48, 0.6, 0.64), perturb=0.0, n_mag=1, precision="fp64")
+    rng = np.random.default_rng(seed)
+    b, bw, coords = _sin_fields(shape, rng)
+    u, uw, _ = _sin_fields(shape, rng)
+    b *= 1e-2
+    u = 1e-2 * (u + np.array([0.3, -0.2, 0.5]).reshape(3, 1, 1, 1))  # a mean flow: pumping is not zero
+    bw = [[None if w is None else (1e-2 * w[0], w[1], w[2]) for w in row] for row in bw]
+    uw = [[None if w is None else (1e-2 * w[0], w[1], w[2]) for w in row] for row in uw]
+    rho = 1.0 + 1e-3 * np.cos(2 * np.pi * coords[0] / nx)
+    o = oracle.Oracle(p)
+    o.set_state(rho, u, b, t=0)
+    return o, p, (rho, u, b), (uw, bw), coords
+
+
+def _curl_closed_form(bw, coords):
+    d = lambda c, a: _central_diff(bw, c, a, coords)  # noqa: E731  d_a b_c
+    return np.stack([d(2, 1) - d(1, 2), d(0, 2) - d(2, 0), d(1, 0) - d(0, 1)])
+
+
+@pytest.mark.parametrize("dim,flow_q,shape", LORENTZ_CASES, ids=["d3q19", "d3q27", "d2q9"])
+def test_lorentz_force_is_the_curl_cross_the_field(dim, flow_q, shape):
+    # Sec. V.A: F = F_body e_axis + J x (B^ext + b), J = curl b with the
+    # flow lattice's isotropic first derivative.  For a sum of one-dimensional
+    # waves that derivative is exactly the central difference (the lattice has
+    # weight 1/6 on each side of every axis), so J is known in closed form;
+    # every one of the six terms of the curl carries a wave of its own, so a
+    # wrong sign or index in any of them changes F at almost every node.
+    o, p, (rho, u, b), (uw, bw), coords = _analytic_case(dim, flow_q, shape, seed=17 + dim + flow_q)
+    d = o.derived()
+    J = _curl_closed_form(bw, coords)
+    Be = d["B0"] * np.asarray(p["b0_dir"]).reshape(3, 1, 1, 1)
+    B = Be + b
+    L = np.stack([J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]])
+    ax = 2 if dim == 3 else 0
+    L[ax] += d["F0"]
+    F = o.force()
+    err = np.abs(F - L).max() / np.abs(L).max()
+    assert err < 1e-13, err
+    # the field reaches the force: J is far from zero and B^ext dominates b
+    assert np.abs(J).max() > 1e-3 and d["B0"] > 10 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dim,flow_q,shape", LORENTZ_CASES, ids=["d3q19", "d3q27", "d2q9"])
+def test_diagnostics_of_analytic_fields(dim, flow_q, shape):
+    # Sec. IV Eq. "Energy balance equations" in the local forms the
+    # diagnostics use (every node counts: no walls):
+    #   E_k = <rho |u|^2 / 2>, E_m = <|B^ext + b|^2 / 2>, pump = <F_body u_axis>,
+    #   visc = -nu <u . lap u> with the lattice Laplacian (for one-dimensional
+    #   waves, the sum over axes of the three-point second difference),
+    #   joule = -<u . (J x B)>, and the QS residual (Sec. V.H Eq. "Error l2
+    #   decay") sqrt<|eta lap_m b - div_m(u B - B u)|^2> with the field
+    #   lattice's central differences; all against closed forms of the waves.
+    o, p, (rho, u, b), (uw, bw), coords = _analytic_case(dim, flow_q, shape, seed=29 + dim + flow_q)
+    d = o.derived()
+    Be = d["B0"] * np.asarray(p["b0_dir"]).reshape(3, 1, 1, 1)
+    B = Be + b
+    J = _curl_closed_form(bw, coords)
+    L = np.stack([J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]])
+    axes = range(3) if dim == 3 else range(2)
+    lap_u = np.stack([sum(_second_diff(uw, c, a, coords) for a in axes) for c in range(3)])
+    ax = 2 if dim == 3 else 0
+    want = {
+        "mass": rho.sum(),
+        "E_k": np.mean(0.5 * rho * (u * u).sum(0)),
+        "E_m": np.mean(0.5 * (B * B).sum(0)),
+        "pump": np.mean(d["F0"] * u[ax]),
+        "visc": -d["nu"] * np.mean((u * lap_u).sum(0)),
+        "joule": -np.mean((u * L).sum(0)),
+    }
+    # QS residual: eta * second difference of b minus the central difference
+    # of the flux Phi_{a beta} = u_beta B_a - u_a B_beta (B^ext uniform here)
+    res = np.zeros_like(b)
+    for a in range(3):
+        for be in axes:
+            sh = 2 - be  # array axis of coordinate be in [z][y][x] (after the component axis)
+            res[a] += d["eta"] * (np.roll(b[a], -1, sh) + np.roll(b[a], 1, sh) - 2 * b[a])
+            phi = u[be] * B[a] - u[a] * B[be]
+            res[a] -= 0.5 * (np.roll(phi, -1, sh) - np.roll(phi, 1, sh))
+    want["qs_residual"] = math.sqrt(np.mean((res * res).sum(0)))
+    got = o.observables()
+    for k, v in want.items():
+        assert got[k] == pytest.approx(v, rel=1e-11, abs=1e-300), (k, got[k], v)
+
+
+def test_energies_of_a_uniform_state_in_a_pipe():
+    # A uniform state: the kinetic and magnetic energies are exactly
+    # rho |u|^2 / 2 and |B^ext + b|^2 / 2 (the averages run over the pipe's
+    # interior region, which a uniform state makes irrelevant), the gradients
+    # vanish, and pumping is F_body u_z.
+    p = W.small_pipe(nx=16, ny=16, nz=4, diameter=12.0, Ha=8.0, Rm=0.02, b0_dir=(0.0, 0.6, 0.8), perturb=0.0,
+                     precision="fp64", n_mag=1)
+    o = oracle.Oracle(p)
+    d = o.derived()
+    shape = o.shape
+    rho0, u0, b0 = 1.0625, np.array([0.01, -0.02, 0.03]), np.array([2e-3, 1e-3, -4e-3])
+    o.set_state(np.full(shape, rho0), np.broadcast_to(u0.reshape(3, 1, 1, 1), (3,) + shape),
+                np.broadcast_to(b0.reshape(3, 1, 1, 1), (3,) + shape), t=0)
+    B = d["B0"] * np.array(p["b0_dir"]) + b0
+    got = o.observables()
+    assert got["E_k"] == pytest.approx(0.5 * rho0 * (u0 @ u0), rel=1e-14)
+    assert got["E_m"] == pytest.approx(0.5 * (B @ B), rel=1e-14)
+    assert got["pump"] == pytest.approx(d["F0"] * u0[2], rel=1e-14)
+    assert got["mass"] == pytest.approx(rho0 * np.prod(shape), rel=1e-14)
+    for k in ("visc", "joule", "qs_residual"):
+        assert abs(got[k]) < 1e-18, (k, got[k])
+
+
+# ------------------------------------- 3-D Hartmann channel and 3-D energy balance
+
+@pytest.fixture(scope="module")
+def hartmann_3d_state():
+    # The Hartmann channel in three dimensions (D3Q19 + D3Q7): walls normal to
+    # y on nodes y = 0 and 31, the body force along z, the applied field along
+    # y.  The flow u_z(y) induces b_z(y), so the Lorentz force reaches the flow
+    # through J_x = d b_z / d y (the 2-D channel reaches only J_z).  Four x
+    # columns and two z planes: the profile is invariant along both.
+    p = W.small_pipe(nx=4, ny=32, nz=2, geometry="channel", diameter=31.0, Re=10.0, Ha=10.0, Rm=1e-2,
+                     b0_dir=(0.0, 1.0, 0.0), n_mag=40, n_mag_cap=0, perturb=0.0, precision="fp64")
+    o = oracle.Oracle(p)
+    o.step(2500)
+    return o, p
+
+
+@pytest.mark.slow
+def test_hartmann_3d_channel_profiles_match_closed_form(hartmann_3d_state):
+    o, p = hartmann_3d_state
+    d = o.derived()
+    _, u, b = o.state()
+    a, Ha, F, B0 = d["R"], p["Ha"], d["F0"], d["B0"]
+    y = np.arange(32, dtype=float) - 15.5
+    k = Ha / a
+    u_exact = F * a * a / (d["nu"] * Ha) * (math.cosh(Ha) - np.cosh(k * y)) / math.sinh(Ha)
+    b_exact = F * a / B0 * (np.sinh(k * y) / math.sinh(Ha) - y / a)
+    uz = u[2, 0, :, 0]
+    bz = b[2, 0, :, 0]
+    # invariant along x and z; no cross-stream field, and only a trace of
+    # cross-stream velocity (the magnetic pressure -d(b_z^2/2)/dy is balanced
+    # by a density gradient, which the wall correction leaves a residue of)
+    assert np.ptp(u[2], axis=(0, 2)).max() < 1e-15 and np.ptp(b[2], axis=(0, 2)).max() < 1e-15
+    assert np.abs(u[:2]).max() < 1e-5 * np.abs(uz).max() and np.abs(b[:2]).max() < 1e-12 * np.abs(bz).max()
+    eu = np.linalg.norm(uz - u_exact) / np.linalg.norm(u_exact)
+    eb = np.linalg.norm(bz - b_exact) / np.linalg.norm(b_exact)
+    assert eu < 1.5e-2, eu
+    assert eb < 3e-2, eb
+    # the Hartmann profile is flat in the core: far below the Poiseuille peak
+    assert uz.max() < 0.5 * F * a * a / (2 * d["nu"])
+
+
+@pytest.mark.slow
+def test_hartmann_3d_channel_steady_energy_balance(hartmann_3d_state):
+    o, _ = hartmann_3d_state
+    o.observables()
+    o.step(100)
+    ob = o.observables()
+    P, V, J = ob["pump"], ob["visc"], ob["joule"]
+    assert P > 0 and V > 0 and J > 0
+    assert abs(P - V - J) / P < 2e-2
+    assert ob["steady_residual"] < 5e-6
+
+
+@pytest.mark.slow
+def test_pipe_steady_energy_balance_at_finite_hartmann():
+    # Sec. IV Eq. "Energy balance equations" in the 3-D pipe: at steady state
+    # the pumping power equals viscous plus Joule dissipation, averaged over
+    # r <= R - 2 (outside the IB support).  The field along x makes the
+    # braking force -J_y B0 along the axis, so J_y carries the Joule term; a
+    # wrong sign there would turn the brake into a pump (Joule < 0).
+    p = W.small_pipe(nx=24, ny=24, nz=2, diameter=16.0, Re=10.0, Ha=8.0, Rm=1e-2, n_mag=40, n_mag_cap=0,
+                     perturb=0.0, precision="fp64")
+    o = oracle.Oracle(p)
+    o.step(3000)
+    o.observables()
+    o.step(100)
+    ob = o.observables()
+    P, V, J = ob["pump"], ob["visc"], ob["joule"]
+    assert P > 0 and V > 0 and J > 0.1 * P, (P, V, J)
+    assert abs(P - V - J) / P < 2e-2, (P, V, J)
+    assert ob["steady_residual"] < 1e-5

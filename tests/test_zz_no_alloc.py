@@ -30,12 +30,15 @@ def _device_fields(torch, state, dtype):
             torch.tensor(b, dtype=dtype, device=dev).contiguous())
 
 
+@pytest.mark.parametrize("flow_q", [0, 27])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_static_diagnostics_match_allocating_entry(precision):
+def test_static_diagnostics_match_allocating_entry(precision, flow_q):
+    # on the default D3Q19 flow lattice and on the paper's D3Q27, whose
+    # Laplacian and isotropic gradient the viscous, Joule and Lorentz terms use
     torch = pytest.importorskip("torch")
     dtype = torch.float64 if precision == "fp64" else torch.float32
     p = W.small_pipe(nx=26, ny=24, nz=10, diameter=18.0, precision=precision, Ha=10.0, Rm=1e-2, n_mag=40,
-                     perturb=0.01)
+                     perturb=0.01, flow_q=flow_q)
     with _lib.Solver(p) as s:
         s.step(5)
         s.observables()  # the allocating entry's reference velocity is now u(t = 5)
