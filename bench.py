@@ -141,7 +141,7 @@ def replica_throughput(world: int, nodes_per_rank: int, steps: int, slowest_ms: 
     return world * nodes_per_rank * steps / (slowest_ms / 1e3) / 1e6
 
 
-KERNEL_SOURCES = ("qslbm_kernels.cuh", "qslbm_resident.cuh", "qslbm_launch.cuh")
+KERNEL_SOURCES = ("qslbm_kernels.cuh", "qslbm_resident.cuh", "qslbm_fused.cuh", "qslbm_launch.cuh")
 
 
 def kernel_source_sha() -> str:
@@ -165,6 +165,91 @@ def profiled_traffic(workload: str):
         return float(d["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+def sweep_kernel_info(solver, p):
+    """(launches per flow step, kernel description, sweeps per launch) of the
+    handle's magnetic sub-iteration kernel."""
+    k = solver.units["sweep_kernel"]
+    n_mag = solver.units["n_mag"]
+    if k == "resident":
+        return 3, "k_sweeps_resident<float,3> (all sweeps + IB on b, planes held in shared memory)", n_mag
+    if k == "fused":
+        return n_mag + 2, ("k_sweep_fused<float> (one sweep + IB on b: each CTA marches a band of rows of a z "
+                           "chunk, staged by TMA, and corrects it in shared memory)"), 1
+    if k == "split":
+        return 2 * n_mag + 2, ("k_sweep_march_pair<float> + k_ib_staged<float> (one sweep: z-marching stencil, "
+                               "then the IB corrector on b, one CTA per plane)"), 1
+    return n_mag + 2, "k_sweep_ib<float,3> (one sweep + IB on b, one z plane per CTA)", 1
+
+
+def roofline_block(solver, p, workload, sweep_ms, peak, peak_kind):
+    """Roofline of the dominant kernel (the magnetic sweep + IB on b) from its
+    CUDA-event time.  Algorithmic bytes: 36 B per node per sweep (b and u read,
+    b written, FP32); a separate IB launch adds 24 B per wall-shell node (it
+    reads and writes the shell).  Fields larger than L2 make it an HBM
+    roofline; the resident kernel's working set stays in L2 and shared memory,
+    so its figure is an effective bandwidth."""
+    n = solver.n
+    n_mag = solver.units["n_mag"]
+    _, name, per_launch = sweep_kernel_info(solver, p)
+    k = solver.units["sweep_kernel"]
+    n_shell = int(solver.units["shell_nodes"])
+    per_sweep = 36 * n + (24 * n_shell if k == "split" else 0)
+    alg_bytes = per_sweep * per_launch
+    launch_ms = sweep_ms * per_launch
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    fields_bytes = 2 * 3 * 4 * n + 3 * 4 * n  # b (two buffers) and u
+    import torch
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    bound = "hbm" if (k != "resident" and fields_bytes > l2) else "l2_resident"
+    return {"bound": "hbm" if bound == "hbm" else "l2", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(workload), "kernel": name,
+            "workload": workload, "bytes_per_launch": alg_bytes, "ms_per_launch": launch_ms,
+            "sweeps_per_launch": per_launch, "us_per_sweep": sweep_ms * 1e3,
+            "peak_kind": f"{peak_kind} (hbm_gbs)",
+            "note": ("fields exceed L2: every sweep streams b and u from HBM" if bound == "hbm" else
+                     "working set is L2-resident within a step: achieved counts algorithmic bytes "
+                     "(effective bandwidth), not DRAM traffic")}
+
+
+def run_hbm_workload(stream, flush, peak, peak_kind, steps: int = 10, warmup: int = 3):
+    """The 96x96x512 ramped pipe (fields above L2): MLUPS over `steps` flow
+    steps and the roofline of its sweep kernel, CUDA events on `stream`."""
+    import torch
+
+    from paper_2211_09370_gb300 import _lib
+
+    name, make = WORKLOADS["ramp96"]
+    p = make(0)
+    s = _lib.Solver(p, stream=stream.cuda_stream)
+    n_mag = s.units["n_mag"]
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    step_ms = sum(a.elapsed_time(b) for a, b in ms) / steps
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.mag_sweeps(n_mag)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / n_mag
+    roof = roofline_block(s, p, "ramp96", sweep_ms, peak, peak_kind)
+    out = {"workload": name, "nodes": s.n, "n_mag": n_mag, "sweep_kernel": s.units["sweep_kernel"],
+           "MLUPS": s.n / step_ms / 1e3, "ms_per_step": step_ms, "steps": steps, "us_per_sweep": sweep_ms * 1e3,
+           "roofline": roof}
+    s.close()
+    return out
 
 
 def run_reference(args):
@@ -428,53 +513,38 @@ def main():
     obs_bytes = C.sizeof(_lib.qslbm_obs)
 
     peak, peak_kind = peaks()
-    if solver.units["sweep_kernel"] == "resident":
-        kernel_name = "k_sweeps_resident<float,3> (all sweeps + IB on b, planes held in shared memory)"
-        launches_per_step = 2 + 1
-        per_launch_units = n_mag  # one launch runs every sweep of the step
-    elif solver.units["sweep_kernel"] == "split" and p["nx"] % 2 == 0:
-        kernel_name = ("k_sweep_march_pair<float> + k_ib_staged<float> (one sweep: z-marching stencil on node "
-                       "pairs, then the IB corrector on b, one CTA per plane)")
-        launches_per_step = 2 * n_mag + 2
-        per_launch_units = 1
-    elif solver.units["sweep_kernel"] == "split":
-        kernel_name = ("k_sweep_march<float> + k_ib_staged<float> (one sweep: z-marching stencil, then the IB "
-                       "corrector on b, one CTA per plane)")
-        launches_per_step = 2 * n_mag + 2
-        per_launch_units = 1
-    else:
-        kernel_name = "k_sweep_ib<float,3> (one sweep + IB on b, one z plane per CTA)"
-        launches_per_step = n_mag + 2
-        per_launch_units = 1
-    n_shell = int(solver.units["shell_nodes"])
-    alg_bytes = (36 * n + 24 * n_shell) * per_launch_units
-    launch_ms = sweep_ms * n_mag / (n_mag // per_launch_units)
-    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    launches_per_step, _, _ = sweep_kernel_info(solver, p)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name, "nodes": n, "n_mag": n_mag, "precision": "fp32",
+                   "sweep_kernel": solver.units["sweep_kernel"],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                    "l2": "flushed before every timed step (256 MB write)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-                     "kernel": kernel_name,
-                     "bytes_per_launch": alg_bytes, "ms_per_launch": launch_ms,
-                     "sweeps_per_launch": per_launch_units, "us_per_sweep": sweep_ms * 1e3,
-                     "peak_kind": f"{peak_kind} (hbm_gbs)",
-                     "note": "working set is L2-resident within a step; achieved counts algorithmic bytes"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + obs_bytes, "steps": e2e_steps},
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
     }
+    headline_roof = roofline_block(solver, p, args.workload, sweep_ms, peak, peak_kind)
+    solver.close()
+    if headline_roof["bound"] == "hbm":
+        result["roofline"] = headline_roof
+    else:
+        # the headline's working set stays in L2 and shared memory: its kernel
+        # is reported by effective bandwidth, and the HBM roofline is taken on
+        # the pipe whose fields exceed L2 (the workload the HBM target is set on)
+        result["roofline_l2_resident"] = headline_roof
+        if rank == 0:
+            hbm = run_hbm_workload(stream, flush, peak, peak_kind)
+            result["roofline"] = hbm.pop("roofline")
+            result["hbm_workload"] = hbm
     if rank == 0 and not args.no_extras:
         result["batched"] = run_batched()
         result["serving"] = run_serving()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample()
-    solver.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if ws > 1:

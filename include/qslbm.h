@@ -70,7 +70,14 @@ extern "C" {
  * keeps every plane in shared memory (needs nz co-resident CTAs and a plane of
  * at most 8192 nodes; create fails with QSLBM_EINVAL if the domain does not
  * fit).  SPLIT: per sweep a node-parallel sweep launch and a per-plane IB
- * launch.  AUTO picks RESIDENT when it fits, otherwise SPLIT. */
+ * launch.  FUSED: per sweep one launch in which each CTA sweeps a band of
+ * rows of a z chunk, plane by plane, and applies the IB on b to it in shared
+ * memory (the band's rows are staged by the tensor memory accelerator with
+ * three halo rows on each side); FP32, 3-D, nx a multiple of 4 up to 256, the
+ * same wall ring on every plane; create fails with QSLBM_EINVAL otherwise.
+ * AUTO picks RESIDENT when it fits; else, when FUSED applies, it times one
+ * sweep of FUSED and one of SPLIT on the handle's fields at creation and keeps
+ * the faster (the two give bitwise equal results); else SPLIT. */
 /* Initial velocity: rest (plus the seeded noise), or the Ha = 0 profile
  * U0 (1 - r^2/R^2) along the axis inside the wall (plus the noise). */
 #define QSLBM_INIT_REST 0
@@ -80,6 +87,7 @@ extern "C" {
 #define QSLBM_SWEEP_PLANES 1
 #define QSLBM_SWEEP_RESIDENT 2
 #define QSLBM_SWEEP_SPLIT 3
+#define QSLBM_SWEEP_FUSED 4
 
 /* Flow schemes.  SINGLE_STEP: the single-step update (Sec. III.E, V.A), tau < 1.
  * MACROSCOPIC: the tau = 1 scheme at particle speed c = 6 nu for tau >= 1
@@ -124,7 +132,7 @@ typedef struct qslbm_params {
     uint64_t seed;          /* initial perturbation seed                           */
     double perturb;         /* initial |u| noise, fraction of U0, inside the wall  */
     int32_t init_kind;      /* QSLBM_INIT_REST (default) | QSLBM_INIT_POISEUILLE   */
-    int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT | _SPLIT */
+    int32_t sweep_kernel;   /* QSLBM_SWEEP_AUTO (default) | _PLANES | _RESIDENT | _SPLIT | _FUSED */
     double alpha;           /* accelerated sweep (Sec. V.H, Eq. "magnetic field
                                quasi-static acelerated"): b <- b + (sweep(b) - b)/alpha;
                                1 (default; 0 also means 1) is the plain sweep; stable
@@ -155,6 +163,14 @@ typedef struct qslbm_units {
     int32_t flow_q;       /* velocities of the flow lattice: 9, 19 or 27        */
     double gamma;         /* time-step rescaling in use (6 nu on the macroscopic
                              scheme)                                            */
+    int32_t fused_rows;   /* QSLBM_SWEEP_FUSED: rows per band, 0 otherwise      */
+    int32_t fused_bands;  /* bands per plane                                    */
+    int32_t fused_chunk;  /* z planes each CTA marches per sweep                */
+    int32_t fused_ctas;   /* CTAs per sweep launch                              */
+    double sweep_us_fused; /* AUTO on a domain both FP32 sweep paths take: one   */
+    double sweep_us_split; /* sweep of each timed at creation (microseconds); the
+                              faster is kept (their results are bitwise equal);
+                              0 when not timed                                   */
 } qslbm_units;
 
 /* Diagnostics (Sec. IV Eq. "Energy balance equations", Sec. V.H Eq. "Error l2

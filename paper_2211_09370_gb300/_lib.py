@@ -19,8 +19,9 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUDGET, ENOTFOUND, EARCH = 0, -
 CHANNEL, PIPE, PERIODIC = 0, 1, 2
 B0_UNIFORM, B0_TANH, B0_FIELD = 0, 1, 2
 FP32, FP64 = 0, 1
-SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT, SWEEP_SPLIT = 0, 1, 2, 3
-SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT, "split": SWEEP_SPLIT}
+SWEEP_AUTO, SWEEP_PLANES, SWEEP_RESIDENT, SWEEP_SPLIT, SWEEP_FUSED = 0, 1, 2, 3, 4
+SWEEP_KERNEL = {"auto": SWEEP_AUTO, "planes": SWEEP_PLANES, "resident": SWEEP_RESIDENT, "split": SWEEP_SPLIT,
+                "fused": SWEEP_FUSED}
 GEOMETRY = {"channel": CHANNEL, "pipe": PIPE, "none": PERIODIC, "periodic": PERIODIC}
 B0_KIND = {"uniform": B0_UNIFORM, "tanh": B0_TANH, "field": B0_FIELD}
 PRECISION = {"fp32": FP32, "fp64": FP64}
@@ -46,7 +47,9 @@ class qslbm_units(C.Structure):
                 ("R", "U0", "nu", "tau", "eta", "B0", "F0", "c_mag", "lambda_", "lambda_m", "cs2", "cm2")]
     _fields_ += [("n_mag", C.c_int32), ("n_markers", C.c_int32), ("nodes", C.c_int64), ("device_bytes", C.c_int64),
                 ("shell_nodes", C.c_int64), ("sweep_kernel", C.c_int32), ("tau_m", C.c_double),
-                ("flow_q", C.c_int32), ("gamma", C.c_double)]
+                ("flow_q", C.c_int32), ("gamma", C.c_double), ("fused_rows", C.c_int32),
+                ("fused_bands", C.c_int32), ("fused_chunk", C.c_int32), ("fused_ctas", C.c_int32),
+                ("sweep_us_fused", C.c_double), ("sweep_us_split", C.c_double)]
 
 
 class qslbm_obs(C.Structure):
@@ -247,7 +250,7 @@ class Solver:
         self.units = {k: getattr(u, k) for k, _ in qslbm_units._fields_}
         self.units["lambda"] = self.units.pop("lambda_")
         self.units["sweep_kernel"] = {SWEEP_PLANES: "planes", SWEEP_RESIDENT: "resident",
-                                      SWEEP_SPLIT: "split"}.get(u.sweep_kernel)
+                                      SWEEP_SPLIT: "split", SWEEP_FUSED: "fused"}.get(u.sweep_kernel)
         self.n = int(u.nodes)
         self.shape = (self._q.nz, self._q.ny, self._q.nx)
 

@@ -1,5 +1,7 @@
 // qslbm C ABI: parameter mapping, wall markers and IB weights, device memory,
 // CUDA-graph stepping, diagnostics and state transfer.  See include/qslbm.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,10 +12,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qslbm.h"
 #include "qslbm_internal.h"
 
 using qslbm::State;
+
+// NVTX range over a host-side phase (shown by profilers that record NVTX; a
+// no-op otherwise): "qslbm step", "magnetic sweeps + IB on b", "force + flow +
+// IB on u", "diagnostics", "state transfer".
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct qslbm_handle {
     State s;
@@ -132,7 +146,7 @@ int validate(const qslbm_params& p) {
     if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
     if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
     if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
-    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_SPLIT) return QSLBM_EINVAL;
+    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_FUSED) return QSLBM_EINVAL;
     if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
     if (p.dim == 3 && p.flow_q != 0 && p.flow_q != 19 && p.flow_q != 27) return QSLBM_EINVAL;
     if (p.dim == 2 && p.flow_q != 0 && p.flow_q != 9) return QSLBM_EINVAL;
@@ -427,6 +441,172 @@ int upload_ib(State& s) {
     return QSLBM_OK;
 }
 
+// The fused sweep + IB kernel (FP32): rows per band TY, the per-band IB
+// tables (plane 0's ring: every plane carries it) and the tensor maps of b
+// and u.  Leaves s.fused false when the kernel does not apply: other
+// precision or dimension, nx not a multiple of 4 or above 256, planes with
+// different rings, no band height that fits shared memory and keeps every
+// 3-row box off the periodic boundary.
+int plan_fused(State& s) {
+    s.fused = false;
+    if (s.p.precision != QSLBM_FP32 || s.dim != 3) return QSLBM_OK;
+    if (s.nx % 4 != 0 || s.nx > 256 || s.ny < 8 || s.nz < 3) return QSLBM_OK;
+    if (s.ib.nm > 0 && !s.ib.zinv) return QSLBM_OK;
+    if (3LL * s.n >= (1LL << 31)) return QSLBM_OK;
+    int dev = 0, optin = 0;
+    QCHK(cudaGetDevice(&dev));
+    QCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const qslbm::HostIB& h = s.hib;
+    const int R0 = h.ring_off.size() > 1 ? h.ring_off[1] - h.ring_off[0] : 0;
+    const int S0 = h.shell_off.size() > 1 ? h.shell_off[1] - h.shell_off[0] : 0;
+    const int ny = s.ny, nx = s.nx;
+    // tallest band whose swept rows give at most one node pair per thread
+    int TY = std::min(ny - 6, qslbm::kFusedMaxThreads * 2 / nx - 4);
+    for (; TY >= 3; --TY) {
+        const int bands = (ny + TY - 1) / TY;
+        if (bands < 2) continue;
+        // every 3-row box lies on one side of the periodic boundary
+        bool ok = true;
+        for (int b = 0; b < bands && ok; ++b) {
+            const int y0 = std::min(b * TY, ny - TY);
+            if (y0 > 0 && y0 < 3) ok = false;
+            if (y0 + TY != ny && y0 + TY + 3 > ny) ok = false;
+        }
+        if (!ok) continue;
+        // local row of y in band b's swept rows (y0 - 2 .. y0 + TY + 1), or -1
+        auto local = [&](int y0, int y) {
+            const int r = ((y - (y0 - 2)) % ny + ny) % ny;
+            return r < TY + 4 ? r : -1;
+        };
+        // markers of each band: support centred on rows y0 - 1 .. y0 + TY
+        std::vector<std::vector<int>> mk(bands), sh(bands);
+        for (int b = 0; b < bands; ++b) {
+            const int y0 = std::min(b * TY, ny - TY);
+            for (int j = 0; j < R0; ++j) {
+                const int r = local(y0, h.iy[3 * j + 1]);
+                if (r >= 1 && r <= TY + 2) mk[b].push_back(j);
+            }
+            for (int i = 0; i < S0; ++i) {
+                const int y = h.shell_xy[i] / nx;
+                if (y >= y0 && y < y0 + TY) sh[b].push_back(i);
+            }
+        }
+        int Mmax = 1, Smax = 1, K = 4;
+        for (int b = 0; b < bands; ++b) {
+            Mmax = std::max(Mmax, (int)mk[b].size());
+            Smax = std::max(Smax, (int)sh[b].size());
+        }
+        Mmax = (Mmax + 3) / 4 * 4;  // 16-byte alignment of the tables in shared memory
+        Smax = (Smax + 3) / 4 * 4;
+        for (int i = 0; i < S0; ++i) K = std::max(K, (h.csr_off[i + 1] - h.csr_off[i] + 3) / 4 * 4);
+        int slots = 5;
+        size_t smem = qslbm::fused_smem_bytes(nx, TY, Mmax, Smax, K, slots);
+        if (smem + 1024 > (size_t)optin) smem = qslbm::fused_smem_bytes(nx, TY, Mmax, Smax, K, slots = 4);
+        if (smem + 1024 > (size_t)optin) continue;
+        std::vector<int> mk_cnt(bands), mk_off((size_t)bands * Mmax * 9, 0), sh_cnt(bands),
+            sh_off((size_t)bands * Smax, 0), sh_m((size_t)bands * Smax * K, 0), sh_ce((size_t)bands * Smax, 0);
+        std::vector<double> mk_w((size_t)bands * Mmax * 9, 0.0), mk_s((size_t)bands * Mmax, 0.0),
+            sh_w((size_t)bands * Smax * K, 0.0);
+        for (int b = 0; b < bands; ++b) {
+            const int y0 = std::min(b * TY, ny - TY);
+            std::vector<int> pos(R0, -1);  // marker -> index in the band's list
+            mk_cnt[b] = (int)mk[b].size();
+            for (int m = 0; m < mk_cnt[b]; ++m) {
+                const int j = mk[b][m];
+                pos[j] = m;
+                const size_t e = ((size_t)b * Mmax + m) * 9;
+                for (int bb = 0; bb < 3; ++bb)
+                    for (int a = 0; a < 3; ++a) {
+                        const int r = local(y0, h.iy[3 * j + bb]);
+                        if (r < 0) return QSLBM_EINVAL;  // not reachable: the support is within one row
+                        mk_off[e + 3 * bb + a] = r * nx + h.ix[3 * j + a];
+                        mk_w[e + 3 * bb + a] = h.wx[3 * j + a] * h.wy[3 * j + bb];
+                    }
+                mk_s[(size_t)b * Mmax + m] = h.sm[j];
+            }
+            sh_cnt[b] = (int)sh[b].size();
+            for (int k = 0; k < sh_cnt[b]; ++k) {
+                const int i = sh[b][k];
+                const int y = h.shell_xy[i] / nx, x = h.shell_xy[i] - y * nx;
+                sh_off[(size_t)b * Smax + k] = (y - y0 + 2) * nx + x;
+                sh_ce[(size_t)b * Smax + k] = h.csr_off[i + 1] - h.csr_off[i];
+                for (int e = h.csr_off[i]; e < h.csr_off[i + 1]; ++e) {
+                    const int m = pos[h.csr_m[e]];
+                    if (m < 0) return QSLBM_EINVAL;  // not reachable: its markers are the band's
+                    const size_t q = ((size_t)b * Smax + k) * K + (e - h.csr_off[i]);
+                    sh_m[q] = m;
+                    sh_w[q] = h.csr_w[e];
+                }
+            }
+        }
+        int rc;
+        if ((rc = upload(s, (void**)&s.fu_mk_cnt, mk_cnt))) return rc;
+        if ((rc = upload(s, (void**)&s.fu_mk_off, mk_off))) return rc;
+        if ((rc = upload_real(s, (void**)&s.fu_mk_w, mk_w))) return rc;
+        if ((rc = upload_real(s, (void**)&s.fu_mk_s, mk_s))) return rc;
+        if ((rc = upload(s, (void**)&s.fu_sh_cnt, sh_cnt))) return rc;
+        if ((rc = upload(s, (void**)&s.fu_sh_off, sh_off))) return rc;
+        if ((rc = upload(s, (void**)&s.fu_sh_m, sh_m))) return rc;
+        if ((rc = upload_real(s, (void**)&s.fu_sh_w, sh_w))) return rc;
+        if ((rc = upload(s, (void**)&s.fu_sh_ce, sh_ce))) return rc;
+        if ((rc = dev_alloc(s, (void**)&s.fu_err, sizeof(int)))) return rc;
+        QCHK(cudaMemsetAsync(s.fu_err, 0, sizeof(int), s.stream));
+        // tensor maps: b[i] and u[i] as 4-D (x, y, z, component) FP32 tensors,
+        // boxes of 3 rows and of TY rows of one component
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        QCHK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) {
+            g_last_error = "cuTensorMapEncodeTiled is not available";
+            return QSLBM_ECUDA;
+        }
+        auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)s.nz, 3};
+        const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)s.n * 4};
+        const cuuint32_t box3[4] = {(cuuint32_t)nx, 3, 1, 1};
+        const cuuint32_t boxt[4] = {(cuuint32_t)nx, (cuuint32_t)TY, 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        for (int i = 0; i < 2; ++i) {
+            CUtensorMap* maps[4] = {&s.fu_map_b3[i], &s.fu_map_bt[i], &s.fu_map_u3[i], &s.fu_map_ut[i]};
+            void* ptrs[4] = {s.b[i], s.b[i], s.u[i], s.u[i]};
+            for (int f = 0; f < 4; ++f) {
+                CUresult r = encode(maps[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ptrs[f], dims, strides,
+                                    f % 2 ? boxt : box3, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    g_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+                    return QSLBM_ECUDA;
+                }
+            }
+        }
+        s.fu_TY = TY;
+        s.fu_bands = bands;
+        s.fu_Mmax = Mmax;
+        s.fu_Smax = Smax;
+        s.fu_K = K;
+        s.fu_smem = smem;
+        s.fu_slots = slots;
+        s.fused = true;
+        QCHK(ops(s).plan_fused(s));
+        return QSLBM_OK;
+    }
+    return QSLBM_OK;
+}
+
+// A fused sweep whose copy wait timed out leaves 1 in fu_err; report it once.
+int check_fused(State& s) {
+    if (!s.fu_err) return QSLBM_OK;
+    int err = 0;
+    QCHK(cudaMemcpyAsync(&err, s.fu_err, sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    if (!err) return QSLBM_OK;
+    QCHK(cudaMemsetAsync(s.fu_err, 0, sizeof(int), s.stream));
+    QCHK(cudaStreamSynchronize(s.stream));
+    g_last_error = "fused sweep kernel: a plane copy did not complete in time";
+    return QSLBM_ETIMEOUT;
+}
+
 double body_force(const State& s, long long t) {
     double f = s.units.F0;
     if (s.p.force_amp != 0.0) f *= 1.0 + s.p.force_amp * std::sin(s.omega * (double)t);
@@ -465,6 +645,7 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
     qslbm_handle* h = new (std::nothrow) qslbm_handle();
     if (!h) return QSLBM_ENOMEM;
     State& s = h->s;
+    bool tune_sweep = false;  // AUTO on a domain both FP32 sweep paths take: time them
     s.p = *pin;
     s.dim = s.p.dim;
     s.nx = s.p.nx;
@@ -561,6 +742,16 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
             goto fail;
         }
     }
+    tune_sweep = !s.resident && s.p.sweep_kernel == QSLBM_SWEEP_AUTO;
+    if (!s.resident && (s.p.sweep_kernel == QSLBM_SWEEP_AUTO || s.p.sweep_kernel == QSLBM_SWEEP_FUSED)) {
+        if ((rc = plan_fused(s))) goto fail;
+        if (!s.fused && s.p.sweep_kernel == QSLBM_SWEEP_FUSED) {
+            g_last_error = "the fused sweep kernel does not apply to this domain";
+            rc = QSLBM_EINVAL;
+            goto fail;
+        }
+        if (s.fused) s.p.sweep_kernel = QSLBM_SWEEP_FUSED;
+    }
     if (!s.resident && s.p.sweep_kernel == QSLBM_SWEEP_AUTO) s.p.sweep_kernel = QSLBM_SWEEP_SPLIT;
     {
         cudaError_t e = ops(s).plan_march(s);
@@ -569,7 +760,6 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
             goto fail;
         }
     }
-    s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : s.p.sweep_kernel;
     {
         long long zero = 0;
         cudaError_t e = cudaMemcpyAsync(s.tdev, &zero, sizeof(zero), cudaMemcpyHostToDevice, s.stream);
@@ -587,6 +777,21 @@ int create_impl(const qslbm_params* pin, qslbm_handle** out) {
         }
         // initial mass: rho = 1 everywhere
         s.mass0 = (double)s.n;
+    }
+    if (tune_sweep && s.fused) {
+        // both FP32 sweep paths apply: keep the faster on this domain
+        cudaError_t e = ops(s).tune_fused(s, &s.units.sweep_us_fused, &s.units.sweep_us_split);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "tune_fused");
+            goto fail;
+        }
+    }
+    s.units.sweep_kernel = s.resident ? QSLBM_SWEEP_RESIDENT : s.p.sweep_kernel;
+    if (s.fused) {
+        s.units.fused_rows = s.fu_TY;
+        s.units.fused_bands = s.fu_bands;
+        s.units.fused_chunk = s.fu_chunk;
+        s.units.fused_ctas = s.fu_bands * s.fu_chunks;
     }
     s.units.device_bytes = s.device_bytes;
     *out = h;
@@ -607,7 +812,11 @@ int capture_chunk(State& s, int bc, int fc, cudaGraphExec_t* exec) {
     cudaGraph_t g = nullptr;
     QCHK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphSteps; ++i) {
-        ops(s).sweeps(s, s.units.n_mag, s.stream);
+        {
+            NvtxRange r("magnetic sweeps + IB on b");
+            ops(s).sweeps(s, s.units.n_mag, s.stream);
+        }
+        NvtxRange r("force + flow + IB on u");
         ops(s).force_flow(s, s.stream);
     }
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
@@ -624,6 +833,7 @@ int capture_chunk(State& s, int bc, int fc, cudaGraphExec_t* exec) {
 
 int step_impl(State& s, long long nsteps) {
     if (nsteps < 0) return QSLBM_EINVAL;
+    NvtxRange range("qslbm step");
     const qslbm::Ops& o = ops(s);
     long long done = 0;
     while (nsteps - done >= kGraphSteps) {
@@ -639,13 +849,17 @@ int step_impl(State& s, long long nsteps) {
         done += kGraphSteps;
     }
     for (; done < nsteps; ++done) {
-        o.sweeps(s, s.units.n_mag, s.stream);
+        {
+            NvtxRange r("magnetic sweeps + IB on b");
+            o.sweeps(s, s.units.n_mag, s.stream);
+        }
+        NvtxRange r("force + flow + IB on u");
         o.force_flow(s, s.stream);
     }
     QCHK(cudaGetLastError());
     if (s.launch_error) {
         s.launch_error = false;
-        g_last_error = "cudaLaunchKernelEx failed for the resident sweep kernel";
+        g_last_error = "a launch of the resident or fused sweep kernel failed";
         return QSLBM_ECUDA;
     }
     s.t += nsteps;
@@ -673,6 +887,7 @@ int ensure_staging(State& s) {
 }
 
 int observe_impl(State& s, qslbm_obs* out) {
+    NvtxRange range("diagnostics");
     double r[qslbm::kObs];
     ops(s).observe(s, body_force(s, s.t), s.stream);
     QCHK(cudaGetLastError());
@@ -680,6 +895,7 @@ int observe_impl(State& s, qslbm_obs* out) {
     QCHK(cudaMemcpyAsync(s.usnap, s.u[s.fcur], 3 * (size_t)s.n * s.esz, cudaMemcpyDeviceToDevice, s.stream));
     QCHK(cudaStreamSynchronize(s.stream));
     if (int rc = check_resident(s)) return rc;
+    if (int rc = check_fused(s)) return rc;
     const long long dt = s.t - s.tsnap;
     s.tsnap = s.t;
     if (out) {
@@ -702,6 +918,7 @@ int observe_impl(State& s, qslbm_obs* out) {
 
 int get_fields(State& s, double* rho, double* u, double* b) {
     if (!rho && !u && !b) return QSLBM_OK;
+    NvtxRange range("state transfer");
     int rc = ensure_staging(s);
     if (rc) return rc;
     ops(s).to_f64(s, s.stream);
@@ -715,6 +932,7 @@ int get_fields(State& s, double* rho, double* u, double* b) {
 }
 
 int set_fields(State& s, const double* rho, const double* u, const double* b, long long t) {
+    NvtxRange range("state transfer");
     int rc = ensure_staging(s);
     if (rc) return rc;
     const size_t n = (size_t)s.n;
@@ -789,11 +1007,12 @@ int qslbm_step(qslbm_handle* h, int64_t nsteps) {
 
 int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps) {
     if (!h || nsweeps < 0) return QSLBM_EINVAL;
+    NvtxRange range("magnetic sweeps + IB on b");
     ops(h->s).sweeps(h->s, nsweeps, h->s.stream);
     QCHK(cudaGetLastError());
     if (h->s.launch_error) {
         h->s.launch_error = false;
-        g_last_error = "cudaLaunchKernelEx failed for the resident sweep kernel";
+        g_last_error = "a launch of the resident or fused sweep kernel failed";
         return QSLBM_ECUDA;
     }
     return QSLBM_OK;

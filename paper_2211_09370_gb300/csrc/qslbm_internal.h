@@ -1,6 +1,7 @@
 // Internal host-side structures of the qslbm library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -29,6 +30,25 @@ struct DeviceIB {
     void* pad_w = nullptr;   // [nsp pad_k] and their weights
     int pad_k = 0;           // list length, a multiple of 4 (0: none)
 };
+
+// The fused sweep + IB kernel (FP32): a plane slot holds, per field and
+// component, the 3 rows above a band, its TY rows and the 3 rows below, each
+// block padded to 128 bytes.
+constexpr int kFusedMaxThreads = 768;  // threads of a CTA of the fused kernel, at most
+__host__ __device__ inline int fused_pad32(int v) { return (v + 31) / 32 * 32; }
+inline size_t fused_slot_floats(int nx, int TY) {
+    return (size_t)6 * (2 * fused_pad32(3 * nx) + fused_pad32(TY * nx));
+}
+// Shared memory (bytes): `slots` plane slots, two buffers of b* of TY + 4
+// rows (three components), two buffers of deltas and the tables of up to
+// Mmax markers and
+// Smax shell nodes with K list entries (Mmax, Smax multiples of 4), one
+// mbarrier per slot, and 128 bytes of room to align the region's start.
+inline size_t fused_smem_bytes(int nx, int TY, int Mmax, int Smax, int K, int slots) {
+    const size_t f = (size_t)slots * fused_slot_floats(nx, TY) + (size_t)6 * (TY + 4) * nx + (size_t)25 * Mmax +
+                     (size_t)Smax * (2 + 2 * K) + 1;
+    return f * sizeof(float) + (size_t)slots * sizeof(unsigned long long) + 128;
+}
 
 // Longest padded marker list of a shell node (longer lists: the staged IB
 // corrector is not used).
@@ -87,6 +107,18 @@ struct State {
     void* xbuf = nullptr;   // [2][nz][3][P] plane exchange
     void* rsync = nullptr;  // ResidentSync + flags[nz]
     int graph_steps = 0;
+    // fused sweep + IB (FP32 planes beyond the resident kernel): bands of
+    // fu_TY rows, fu_chunk z planes per CTA, per-band IB tables
+    bool fused = false;
+    int fu_TY = 0, fu_bands = 0, fu_chunk = 0, fu_chunks = 0, fu_threads = 0, fu_slots = 4;
+    size_t fu_smem = 0;
+    int fu_Mmax = 0, fu_Smax = 0, fu_K = 0;
+    int *fu_mk_cnt = nullptr, *fu_mk_off = nullptr, *fu_sh_cnt = nullptr, *fu_sh_off = nullptr, *fu_sh_m = nullptr,
+        *fu_sh_ce = nullptr;
+    float *fu_mk_w = nullptr, *fu_mk_s = nullptr, *fu_sh_w = nullptr;
+    int* fu_err = nullptr;  // 1: a copy wait timed out
+    // b[i], u[i] as (x, y, z, component) tensors: boxes of 3 rows and of TY rows of one component
+    CUtensorMap fu_map_b3[2], fu_map_bt[2], fu_map_u3[2], fu_map_ut[2];
     std::vector<void*> allocations;
     long long device_bytes = 0;
 };
@@ -128,6 +160,13 @@ struct Ops {
     // s.resident, s.resident_uhalo, s.resident_smem (no allocation)
     cudaError_t (*plan_resident)(State&);
     cudaError_t (*plan_march)(State&);  // sets s.march_chunk and s.ib_staged_smem
+    // launch shape of the fused sweep for the tables already in s (fu_TY,
+    // fu_bands, fu_smem): sets fu_threads, fu_chunk, fu_chunks, or clears
+    // s.fused when it cannot run here
+    cudaError_t (*plan_fused)(State&);
+    // one sweep of each of the fused kernel and the split path timed on the
+    // handle's fields; keeps the faster (s.fused, s.p.sweep_kernel)
+    cudaError_t (*tune_fused)(State&, double* us_fused, double* us_split);
 };
 
 const Ops& ops_f32();

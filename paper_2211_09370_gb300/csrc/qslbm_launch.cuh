@@ -4,6 +4,7 @@
 
 #include <algorithm>
 
+#include "qslbm_fused.cuh"
 #include "qslbm_internal.h"
 #include "qslbm_kernels.cuh"
 #include "qslbm_resident.cuh"
@@ -69,6 +70,13 @@ struct Launch {
         if (s.resident && nsweeps > 0) {
             launch_resident(s, nsweeps, c, v, st);
             s.bcur ^= 1;
+            return;
+        }
+        if (s.fused) {
+            for (int i = 0; i < nsweeps; ++i) {
+                launch_fused(s, c, st);
+                s.bcur ^= 1;
+            }
             return;
         }
         if (s.p.sweep_kernel == QSLBM_SWEEP_SPLIT) {
@@ -155,6 +163,119 @@ struct Launch {
                                    s.ib.max_nnz);
         // a failed launch is recorded for the caller
         if (e != cudaSuccess) s.launch_error = true;
+    }
+
+    static FusedIB fused_ib(const State& s) {
+        FusedIB t;
+        t.mk_cnt = s.fu_mk_cnt;
+        t.mk_off = s.fu_mk_off;
+        t.mk_w = s.fu_mk_w;
+        t.mk_s = s.fu_mk_s;
+        t.sh_cnt = s.fu_sh_cnt;
+        t.sh_off = s.fu_sh_off;
+        t.sh_m = s.fu_sh_m;
+        t.sh_w = s.fu_sh_w;
+        t.sh_cnt_e = s.fu_sh_ce;
+        t.Mmax = s.fu_Mmax;
+        t.Smax = s.fu_Smax;
+        t.K = s.fu_K;
+        return t;
+    }
+
+    // the instantiation for this handle's shape: compile-time (nx, rows per
+    // band, slots) for common plane widths, the general one otherwise
+    static decltype(&k_sweep_fused<false>) fused_kernel(const State& s) {
+        if (s.bext_xy) return k_sweep_fused<true>;
+        if (s.nx == 96 && s.fu_TY == 12 && s.fu_slots == 4) return k_sweep_fused<false, 96, 12, 4>;
+        if (s.nx == 64 && s.fu_TY == 20 && s.fu_slots == 4) return k_sweep_fused<false, 64, 20, 4>;
+        if (s.nx == 128 && s.fu_TY == 8 && s.fu_slots == 4) return k_sweep_fused<false, 128, 8, 4>;
+        return k_sweep_fused<false>;
+    }
+
+    // one sweep + IB on b, bin = b[bcur] -> b[1 - bcur], u = u[fcur]
+    static void launch_fused(State& s, const SweepCoef<T>& c, cudaStream_t st) {
+        if constexpr (sizeof(T) == 4) {
+            const dim3 grid((unsigned)s.fu_bands, (unsigned)s.fu_chunks);
+            const FusedGeo g{s.nx, s.ny, s.nz, s.fu_TY, s.fu_chunk, (int)s.n, s.fu_slots};
+            const int bc = s.bcur, fc = s.fcur;
+            fused_kernel(s)<<<grid, s.fu_threads, s.fu_smem, st>>>(s.fu_map_b3[bc], s.fu_map_bt[bc], s.fu_map_u3[fc],
+                                                                    s.fu_map_ut[fc], (float*)s.b[1 - bc], c,
+                                                                    fused_ib(s), g, s.fu_err);
+        } else {
+            s.launch_error = true;  // never planned: the fused sweep is the FP32 path
+        }
+    }
+
+    // threads, and z planes per CTA so that the grid is one CTA per SM
+    static cudaError_t plan_fused(State& s) {
+        if constexpr (sizeof(T) != 4) {
+            s.fused = false;
+            return cudaSuccess;
+        } else {
+            // one node pair per thread and pass over the band's swept rows
+            const int pairs = (s.fu_TY + 4) * s.nx / 2;
+            s.fu_threads = std::min(kFusedMaxThreads, (pairs + 31) / 32 * 32);
+            auto kern = fused_kernel(s);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.fu_smem);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s.fused = false;
+                return cudaSuccess;
+            }
+            int dev = 0, sms = 0, per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.fu_threads, s.fu_smem)) !=
+                cudaSuccess)
+                return e;
+            if (per_sm < 1) {
+                s.fused = false;
+                return cudaSuccess;
+            }
+            const int slots_total = per_sm * sms;
+            const int chunks = std::max(1, slots_total / s.fu_bands);
+            s.fu_chunk = (s.nz + chunks - 1) / chunks;
+            s.fu_chunks = (s.nz + s.fu_chunk - 1) / s.fu_chunk;
+            return cudaSuccess;
+        }
+    }
+
+    // Times one sweep of the fused kernel and one of the split path (each
+    // reads b[bcur] and writes b[1 - bcur], which holds no state) on this
+    // handle's own fields: two sweeps to warm up, then four, CUDA events on
+    // the handle's stream.  Leaves the fused kernel in use when it is the
+    // faster one.
+    static cudaError_t tune_fused(State& s, double* us_fused, double* us_split) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        double us[2] = {0.0, 0.0};
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            s.fused = k == 0;
+            s.p.sweep_kernel = k == 0 ? QSLBM_SWEEP_FUSED : QSLBM_SWEEP_SPLIT;
+            for (int r = 0; r < 2; ++r) {
+                sweeps(s, 1, s.stream);
+                s.bcur ^= 1;
+            }
+            e = cudaEventRecord(e0, s.stream);
+            for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+                sweeps(s, 1, s.stream);
+                s.bcur ^= 1;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            us[k] = 1e3 * ms / 4;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        *us_fused = us[0];
+        *us_split = us[1];
+        s.fused = e == cudaSuccess && us[0] <= us[1];
+        s.p.sweep_kernel = s.fused ? QSLBM_SWEEP_FUSED : QSLBM_SWEEP_SPLIT;
+        return e;
     }
 
     static bool small_plane(const State& s) { return (long long)s.nx * s.ny <= (long long)kResidentSmallPlane; }
@@ -384,8 +505,9 @@ struct Launch {
     }
 
     static const Ops& table() {
-        static const Ops o = {&init,   &sweeps,   &force_flow,    &observe,   &observe_fields,
-                              &to_f64, &from_f64, &plan_resident, &plan_march};
+        static const Ops o = {&init,     &sweeps,        &force_flow, &observe,     &observe_fields,
+                              &to_f64,   &from_f64,      &plan_resident, &plan_march, &plan_fused,
+                              &tune_fused};
         return o;
     }
 };

@@ -14,6 +14,10 @@ Fixtures
                   pulsating body force, Rm = 1e-2 (N_mag = 270), 1 % noise
                   (seed 7), clock started at t = 500: 4096 sampled nodes after
                   1 step.
+  ramp_96x96x512_rm<Rm>
+                  the same pipe at the other magnetic Reynolds numbers of the
+                  workload's sweep, Rm = 1e-4, 1e-3, 1e-1 (N_mag = 270, 270,
+                  176: 1 step) and Rm = 1 (N_mag = 18: 3 steps).
 """
 from __future__ import annotations
 
@@ -84,7 +88,17 @@ def ramp_96x96x512():
                        seed=2)
 
 
+# the workload's magnetic Reynolds number sweep (1e-2 is ramp_96x96x512 itself)
+RAMP_RM_STEPS = {"1e-4": 1, "1e-3": 1, "1e-1": 1, "1": 3}
+
+
+def ramp_96x96x512_rm(rm: str):
+    return lambda: run_sampled(W.pipe_ramp_96x96x512(Rm=float(rm), precision="fp64", perturb=0.01, seed=7),
+                               steps=RAMP_RM_STEPS[rm], t0=500, seed=2)
+
+
 FIXTURES = {"hartmann_2000": hartmann_2000, "pipe_64x64x128": pipe_64x64x128, "ramp_96x96x512": ramp_96x96x512}
+FIXTURES.update({f"ramp_96x96x512_rm{rm}": ramp_96x96x512_rm(rm) for rm in RAMP_RM_STEPS})
 
 
 def load(name: str) -> dict:

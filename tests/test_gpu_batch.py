@@ -92,3 +92,24 @@ def test_batch_steps_in_chunks_equal_one_call():
         for i in range(len(ps)):
             for a, b in zip(A.member(i).state(), B.member(i).state()):
                 np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_workload_member_matches_oracle(precision):
+    # a real member of the 64-pipe batched workload (seed 4): its smallest
+    # pipe (D = 27, 35 x 35 x 126, tanh-ramped field, N_mag = 270) stepped in
+    # a batch with the next smallest, against the oracle on every node
+    ps = W.batched_pipes(precision=precision)
+    order = sorted(range(len(ps)), key=lambda k: W.nodes(ps[k]))
+    a, b = ps[order[0]], ps[order[1]]
+    steps = 2
+    with Batch([b, a]) as B:
+        B.step(steps)
+        rho, u, bb = B.member(1).state()
+    o = oracle.Oracle(dict(a, precision="fp64"))
+    o.step(steps)
+    orho, ou, ob = o.state()
+    tol = 1e-12 if precision == "fp64" else 1e-4
+    assert rel(u, ou) <= tol and rel(bb, ob) <= tol, (rel(u, ou), rel(bb, ob))
+    if precision == "fp64":
+        assert np.abs(rho - orho).max() <= 1e-12

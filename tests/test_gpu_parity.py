@@ -105,12 +105,15 @@ def test_mag_sweeps_with_frozen_velocity_fp64(kernel):
     np.testing.assert_array_equal(gu, u)
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("kernel", KERNELS + ["fused"])
 @pytest.mark.parametrize("shape", [(22, 22, 6), (36, 21, 7), (64, 40, 9)])
 def test_mag_sweeps_with_frozen_velocity_fp32(kernel, shape):
     # FP32 sweeps (the flux-component form and, for even nx, the node-pair
-    # kernel): tiles with ghost columns and rows, ramped field
+    # kernel; the fused kernel for nx a multiple of 4): tiles with ghost
+    # columns and rows, ramped field
     nx, ny, nz = shape
+    if kernel == "fused" and nx % 4:
+        pytest.skip("the fused kernel takes nx a multiple of 4")
     p = W.small_pipe(nx=nx, ny=ny, nz=nz, diameter=min(nx, ny) - 6.0, precision="fp32", sweep_kernel=kernel,
                      b0_kind="tanh", ramp_center=nz / 2, ramp_width=2.0, Ha=30.0, Rm=0.05)
     z, y, x = np.meshgrid(np.arange(float(nz)), np.arange(float(ny)), np.arange(float(nx)), indexing="ij")
@@ -332,6 +335,107 @@ def test_ramp_96x96x512_full_size_sampled(precision):
     _sampled(W.pipe_ramp_96x96x512(Rm=1e-2, precision=precision, perturb=0.01, seed=7), g, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("rm", ["1e-4", "1e-3", "1e-1", "1"])
+def test_ramp_96x96x512_rm_sweep_sampled(rm, precision):
+    # the other four magnetic Reynolds numbers of the ramped pipe's sweep
+    # (N_mag = 270, 270, 176, 18), each against its oracle fixture
+    g = golden.load(f"ramp_96x96x512_rm{rm}")
+    _sampled(W.pipe_ramp_96x96x512(Rm=float(rm), precision=precision, perturb=0.01, seed=7), g, precision)
+
+
+@pytest.mark.parametrize("shape", [(72, 72), (71, 72)], ids=["pairs", "odd_nx"])
+def test_resident_large_plane_form_fp32(shape):
+    # planes of 4097 to 8192 nodes take the resident kernel's large-plane shape
+    # (512 threads x 16 nodes in FP32); even nx moves node pairs, odd nx single
+    # nodes
+    nx, ny = shape
+    p = W.small_pipe(nx=nx, ny=ny, nz=10, diameter=64.0, perturb=0.0, n_mag=60, precision="fp32",
+                     sweep_kernel="resident")
+    assert 4096 < nx * ny <= 8192
+    with Solver(p) as s:
+        assert s.units["sweep_kernel"] == "resident"
+    got, want, _ = run_both(p, 8)
+    check_fields(got, want, "fp32", f"resident {nx}x{ny}")
+
+
+def test_resident_large_plane_form_fp64():
+    # in FP64 a plane above 4096 nodes fits the resident kernel's shared memory
+    # only without wall tables: a periodic box of 65 x 64 planes
+    p = W.small_pipe(nx=65, ny=64, nz=6, diameter=40.0, geometry="none", perturb=0.02, seed=5, n_mag=40,
+                     precision="fp64", sweep_kernel="resident")
+    with Solver(p) as s:
+        assert s.units["sweep_kernel"] == "resident"
+    got, want, _ = run_both(p, 3)
+    check_fields(got, want, "fp64", "resident 65x64 periodic")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["small_pipe", "smooth_pipe_long"])
+def test_viscosity_scaled_ib_parity(name, precision, kernel):
+    # Sec. V.E with a reference viscosity below nu: lambda = nu / nu_ref = 2, so
+    # the wall correction on u carries s_j = lambda / (d (1 + d (lambda - 1)))
+    # instead of 1/d; two of the parity cases above with nu_ref = nu / 2
+    p, steps, t0 = FP64_CASES[name]
+    nu = oracle.derive(dict(p, precision="fp64"))["nu"]
+    p = dict(p, nu_ref=nu / 2.0, precision=precision, sweep_kernel=kernel)
+    assert oracle.derive(dict(p, precision="fp64"))["lambda"] == pytest.approx(2.0, rel=1e-14)
+    with Solver(p) as s:
+        assert s.units["lambda"] == pytest.approx(2.0, rel=1e-14)
+    got, want, _ = run_both(p, steps, t0=t0)
+    check_fields(got, want, precision, name + " lambda 2")
+
+
+# ------------------------------------------------ the fused sweep + IB kernel
+
+# (nx, ny, nz, diameter): two bands sharing rows, four bands with the last one
+# shifted, eight equal bands; chunks of one plane up to several planes; the
+# widths 64, 96 and 128 take the kernel's compile-time instantiations
+FUSED_SHAPES = [(24, 22, 10, 16.0), (28, 27, 11, 19.0), (64, 64, 12, 56.0), (96, 96, 8, 88.0), (40, 36, 64, 28.0),
+                (128, 40, 12, 32.0), (96, 96, 512, 88.0)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES, ids=lambda s: "x".join(map(str, s[:3])))
+def test_fused_kernel_equals_split_path_bitwise(shape):
+    # the same EMF-form sweep and the same IB sums in the same order as the
+    # marching sweep + staged IB, so every field is bitwise the split path's
+    nx, ny, nz, D = shape
+    p = W.small_pipe(nx=nx, ny=ny, nz=nz, diameter=D, Re=300.0, Ha=40.0, Rm=1e-2, b0_kind="tanh",
+                     ramp_center=nz / 2, ramp_width=2.0, force_amp=0.2, force_period=9.0, perturb=0.01, seed=13,
+                     n_mag=25, precision="fp32")
+    outs = []
+    for k in ("fused", "split"):
+        with Solver(dict(p, sweep_kernel=k)) as s:
+            assert s.units["sweep_kernel"] == k
+            s.step(3)
+            s.mag_sweeps(7)
+            outs.append(s.state())
+            s.observables()  # reports a timed-out copy wait as an error
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["ramp_pulsating", "shared_rows"])
+def test_fused_kernel_parity_fp32(name):
+    if name == "ramp_pulsating":
+        p, steps, t0 = FP64_CASES[name]
+    else:
+        p, steps, t0 = W.small_pipe(nx=28, ny=27, nz=11, diameter=19.0, perturb=0.0, n_mag=60), 20, 0
+    got, want, _ = run_both(dict(p, precision="fp32", sweep_kernel="fused"), steps, t0=t0)
+    check_fields(got, want, "fp32", name + " fused")
+
+
+def test_fused_kernel_six_magnet_field_fp32():
+    # the in-plane applied field variant of the kernel (Sec. VI)
+    nx, ny, D = 28, 24, 18.0
+    p = W.small_pipe(nx=nx, ny=ny, nz=8, diameter=D, U0=0.05, Re=60.0, Ha=15.0, Rm=5e-3, perturb=0.0, n_mag=40,
+                     b0_kind="field", b0_field=W.six_magnet_field(nx, ny, D), precision="fp32",
+                     sweep_kernel="fused")
+    got, want, _ = run_both(p, 30)
+    check_fields(got, want, "fp32", "six magnets fused")
+
+
 # ------------------------------------------------------------- API behaviour
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -401,11 +505,20 @@ def test_kernel_selection_reported():
         assert s.units["sweep_kernel"] == "resident"
     with Solver(W.pipe_64x64x128(nz=16, sweep_kernel="planes")) as s:
         assert s.units["sweep_kernel"] == "planes"
-    # 96 x 96 planes exceed the resident kernel's 8192-node plane limit
+    # 96 x 96 planes exceed the resident kernel's 8192-node plane limit: in
+    # FP32 AUTO times the fused kernel and the split path and keeps the faster,
+    # in FP64 it takes the split path
     with Solver(W.pipe_ramp_96x96x512(nz=8)) as s:
-        assert s.units["sweep_kernel"] == "split"
+        u = s.units
+        assert u["sweep_us_fused"] > 0 and u["sweep_us_split"] > 0
+        assert u["sweep_kernel"] == ("fused" if u["sweep_us_fused"] <= u["sweep_us_split"] else "split")
+    with Solver(W.pipe_ramp_96x96x512(nz=8, precision="fp64")) as s:
+        assert s.units["sweep_kernel"] == "split" and s.units["sweep_us_fused"] == 0
     with pytest.raises(QSLBMError):
         Solver(W.pipe_ramp_96x96x512(nz=8, sweep_kernel="resident"))
+    for bad in (dict(precision="fp64"), dict(nx=95)):  # the fused kernel: FP32, nx a multiple of 4
+        with pytest.raises(QSLBMError):
+            Solver(W.pipe_ramp_96x96x512(nz=8, sweep_kernel="fused", **bad))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -50,3 +50,12 @@ def test_degenerate_horizon_is_well_conditioned(case):
     p, steps = degenerate(case)
     su, sb = _sensitivity(dict(p, precision="fp64"), steps, 0)
     assert su < 1e-13 and sb < 1e-13, (su, sb)
+
+
+@pytest.mark.parametrize("name", ["small_pipe", "smooth_pipe_long"])
+def test_viscosity_scaled_ib_horizon_is_well_conditioned(name):
+    # the same cases with lambda = nu / nu_ref = 2 (Sec. V.E)
+    p, steps, t0 = FP64_CASES[name]
+    nu = oracle.derive(dict(p, precision="fp64"))["nu"]
+    su, sb = _sensitivity(dict(p, precision="fp64", nu_ref=nu / 2.0), steps, t0)
+    assert su < 1e-13 and sb < 1e-13, (su, sb)
