@@ -296,12 +296,24 @@ int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_
 
 /* ------------------------------------------------------------------ batches
  * Many independent instances (3-D, one precision) advanced together: every
- * phase of a flow step is one fused launch over all instances' work (the
- * magnetic sweep s only over instances with N_mag > s), the step is replayed
- * from a CUDA graph, and the node-parallel sweep's block size and persistent
- * grid are chosen by timing candidates on the batch at creation.  Each
- * instance follows the same arithmetic as a handle created alone with
- * QSLBM_SWEEP_SPLIT. */
+ * phase of a flow step is one fused launch over all instances' work, and the
+ * steps are replayed from CUDA graphs (one of many steps, one of a single
+ * step for the remainder).  The magnetic sub-iteration (Sec. V.G, with the IB
+ * on b after each sweep, Sec. V.D) takes one of two routes per instance:
+ *  - resident groups (FP32): an instance with a straight wall (the same ring
+ *    on every plane) and planes of at most 8192 nodes runs all its N_mag
+ *    sweeps in one cooperative launch shared by every such instance; each CTA
+ *    holds a group of whole planes in shared memory, and the groups of an
+ *    instance exchange their end planes through global memory with bounded
+ *    waits (a wait that times out is reported as QSLBM_ETIMEOUT by
+ *    qslbm_batch_handle and the server).  Instances are admitted smallest
+ *    first while their groups fit co-resident on the device;
+ *  - marching: every other instance (and any created with sweep_kernel =
+ *    QSLBM_SWEEP_SPLIT) takes one persistent z-marching launch per sweep over
+ *    the instances with N_mag > s, then one IB launch; the sweep's persistent
+ *    grid is chosen by timing candidates on the batch at creation.
+ * Each instance follows the same arithmetic as a handle created alone with
+ * QSLBM_SWEEP_SPLIT (the same expressions in the same order). */
 typedef struct qslbm_batch qslbm_batch;
 
 typedef struct qslbm_batch_info_t {
@@ -310,6 +322,10 @@ typedef struct qslbm_batch_info_t {
     int32_t launches_per_step;
     int64_t nodes, node_sweeps_per_step, device_bytes, steps;
     double tune_us[8];                  /* microseconds per sweep of each candidate tried  */
+    int32_t resident_instances;         /* members whose sweeps run in the resident group kernel */
+    int32_t resident_groups;            /* its CTAs (groups of whole planes)               */
+    int32_t graph_steps;                /* flow steps per captured graph chunk             */
+    int32_t march_chunk;                /* z planes per work item of the marching sweep    */
 } qslbm_batch_info_t;
 
 /* Create count instances from params[0..count-1] (their stream fields are

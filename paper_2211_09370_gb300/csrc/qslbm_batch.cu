@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "qslbm.h"
+#include "qslbm_groups.cuh"
 #include "qslbm_internal.h"
 #include "qslbm_kernels.cuh"
 
@@ -194,7 +195,7 @@ __global__ void k_batch_advance(InstDesc<T>* d, int k) {
 using qslbm::State;
 
 struct qslbm_batch {
-    std::vector<qslbm_handle*> members;  // in N_mag-descending order
+    std::vector<qslbm_handle*> members;  // marching members by N_mag (descending), then the resident groups' members
     std::vector<int> order;              // order[k] = caller's index of member k
     std::vector<int> rank;               // rank[caller index] = k
     cudaStream_t stream = nullptr;
@@ -219,10 +220,27 @@ struct qslbm_batch {
     int sms = 1;                // SMs of the device
     bool has_field = false;     // some member has an in-plane applied field
     int threads = 256, grid = 0;         // autotuned sweep launch
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;        // one flow step
+    cudaGraphExec_t graph_chunk = nullptr;  // chunk_steps flow steps
+    int chunk_steps = 1;
+    int chunk_target = 1000;                // steps a chunk graph should hold
     long long steps = 0;
     long long device_bytes = 0;
     std::vector<double> tune_us;         // timing of each candidate
+    // resident groups (FP32): members [kmarch, K) run all their sweeps in one
+    // cooperative launch of k_batch_resident, a group of whole planes per CTA
+    int kmarch = 0;
+    std::vector<int> gplanes;            // per member: planes per group (0: marching)
+    int ngroups = 0;
+    size_t group_smem = 0;
+    std::vector<qslbm::GroupDesc> h_groups;
+    qslbm::GroupDesc* groups = nullptr;
+    int groups_cap = 0;
+    float* xbuf = nullptr;               // exchange planes of every group
+    long long xbuf_cap = 0;              // floats
+    unsigned* gflags = nullptr;          // [groups_cap] sweep counters
+    int* gerr = nullptr;                 // 1: a neighbour wait timed out
+    cudaError_t launch_err = cudaSuccess;  // a launch of the group kernel that failed
 };
 
 namespace {
@@ -330,14 +348,124 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     }
 }
 
+// Every sweep of the resident groups' members: one cooperative launch (its
+// CTAs wait on one another, so all must be co-resident).
+template <typename T>
+void launch_groups(qslbm_batch& B, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (B.ngroups == 0) return;
+        const auto* d = (const qslbm::InstDesc<float>*)B.desc;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(B.ngroups);
+        cfg.blockDim = dim3(qslbm::kGroupThreads);
+        cfg.dynamicSmemBytes = B.group_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e;
+        if (B.has_field)
+            e = cudaLaunchKernelEx(&cfg, qslbm::k_batch_resident<qslbm::InstDesc<float>, true>, d,
+                                   (const qslbm::GroupDesc*)B.groups, B.xbuf, B.gflags, B.gerr);
+        else
+            e = cudaLaunchKernelEx(&cfg, qslbm::k_batch_resident<qslbm::InstDesc<float>, false>, d,
+                                   (const qslbm::GroupDesc*)B.groups, B.xbuf, B.gflags, B.gerr);
+        if (e != cudaSuccess) B.launch_err = e;
+    }
+}
+
 template <typename T>
 void launch_step(qslbm_batch& B, cudaStream_t st) {
+    launch_groups<T>(B, st);
     for (int s = 0; s < B.max_nmag; ++s) launch_sweep<T>(B, s, B.threads, B.grid, st);
     const int K = (int)B.members.size();
     auto* d = (qslbm::InstDesc<T>*)B.desc;
     qslbm::k_batch_force<T><<<B.h_pfirst[K], qslbm::kNodeThreads, 0, st>>>(d, B.pfirst, K);
     qslbm::k_batch_flow<T><<<B.h_pfirst[K], qslbm::kPlaneThreads, B.ib_smem, st>>>(d, B.pfirst, K);
     qslbm::k_batch_advance<T><<<(K + 127) / 128, 128, 0, st>>>(d, K);
+}
+
+// Planes per group for a member that the resident group kernel can hold (0:
+// it cannot): FP32, a wall ring with the same tables on every plane, planes of
+// at most kGroupMaxNodes nodes, and a group's b, e and IB tables within the
+// opt-in shared memory.  The planes are split into the fewest groups, of
+// nearly equal size.
+int group_planes(const State& s, int optin) {
+    if (s.esz != 4 || s.dim != 3 || s.ib.nm == 0 || !s.ib.zinv || s.units.n_mag < 1) return 0;
+    const int P = s.nx * s.ny;
+    if (P > qslbm::kGroupMaxNodes) return 0;
+    int G = std::min(s.nz, qslbm::kGroupMaxNodes / P);
+    while (G > 0 && qslbm::group_smem_bytes(G * P, s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G) > (size_t)optin)
+        --G;
+    if (G == 0) return 0;
+    const int ng = (s.nz + G - 1) / G;
+    return (s.nz + ng - 1) / ng;  // the largest group of the balanced split
+}
+
+int group_count(const State& s, int G) { return G > 0 ? (s.nz + G - 1) / G : 0; }
+
+// Device tables of the resident groups (members kmarch .. K-1): the groups of
+// each member (balanced split of its planes), their neighbours, exchange
+// areas; the counters and the error flag start at zero.
+int build_groups(qslbm_batch& B) {
+    const int K = (int)B.members.size();
+    B.h_groups.clear();
+    long long xoff = 0;
+    size_t smem = 0;
+    for (int k = B.kmarch; k < K; ++k) {
+        const State& s = qslbm::handle_state_mut(B.members[k]);
+        const int P = s.nx * s.ny;
+        const int ng = group_count(s, B.gplanes[k]);
+        const int first = (int)B.h_groups.size();
+        int z0 = 0;
+        for (int j = 0; j < ng; ++j) {
+            const int G = s.nz / ng + (j < s.nz % ng ? 1 : 0);
+            qslbm::GroupDesc g;
+            g.inst = k;
+            g.z0 = z0;
+            g.G = G;
+            g.prev = first + (j == 0 ? ng - 1 : j - 1);
+            g.next = first + (j == ng - 1 ? 0 : j + 1);
+            g.xoff = xoff;
+            xoff += 12LL * P;
+            z0 += G;
+            B.h_groups.push_back(g);
+            smem = std::max(smem, qslbm::group_smem_bytes(G * P, s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G));
+        }
+    }
+    B.ngroups = (int)B.h_groups.size();
+    B.group_smem = smem;
+    if (B.ngroups == 0) return QSLBM_OK;
+    if (B.ngroups > B.groups_cap) {
+        if (B.groups) cudaFree(B.groups);
+        if (B.gflags) cudaFree(B.gflags);
+        B.groups = nullptr;
+        B.gflags = nullptr;
+        const int cap = std::max(B.ngroups, 2 * B.groups_cap);
+        BCHK(cudaMalloc((void**)&B.groups, sizeof(qslbm::GroupDesc) * cap));
+        BCHK(cudaMalloc((void**)&B.gflags, sizeof(unsigned) * cap));
+        B.groups_cap = cap;
+    }
+    if (xoff > B.xbuf_cap) {
+        if (B.xbuf) cudaFree(B.xbuf);
+        B.xbuf = nullptr;
+        const long long cap = std::max(xoff, 2 * B.xbuf_cap);
+        BCHK(cudaMalloc((void**)&B.xbuf, sizeof(float) * cap));
+        B.xbuf_cap = cap;
+    }
+    if (!B.gerr) BCHK(cudaMalloc((void**)&B.gerr, sizeof(int)));
+    BCHK(cudaMemcpyAsync(B.groups, B.h_groups.data(), sizeof(qslbm::GroupDesc) * B.ngroups, cudaMemcpyHostToDevice,
+                         B.stream));
+    BCHK(cudaMemsetAsync(B.gflags, 0, sizeof(unsigned) * B.ngroups, B.stream));
+    BCHK(cudaMemsetAsync(B.gerr, 0, sizeof(int), B.stream));
+    for (bool xy : {false, true}) {
+        const void* fn = xy ? (const void*)qslbm::k_batch_resident<qslbm::InstDesc<float>, true>
+                            : (const void*)qslbm::k_batch_resident<qslbm::InstDesc<float>, false>;
+        BCHK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    return QSLBM_OK;
 }
 
 // The node-block layout depends on the sweep block size (nodes per block).
@@ -360,7 +488,7 @@ int build_tables(qslbm_batch& B, int threads) {
         BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         auto items = [&](int chunk) {
             long long w = 0;
-            for (int k = 0; k < K; ++k) {
+            for (int k = 0; k < B.kmarch; ++k) {
                 const State& s = qslbm::handle_state_mut(B.members[k]);
                 w += (long long)((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
                      ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) * ((s.nz + chunk - 1) / chunk);
@@ -432,6 +560,10 @@ int build_tables(qslbm_batch& B, int threads) {
     BCHK(cudaMemcpyAsync(B.pfirst, B.h_pfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.mfirst, B.h_mfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
     BCHK(cudaMemcpyAsync(B.sfirst, B.h_sfirst.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, B.stream));
+    if (sizeof(T) == 4) {
+        const int rc = build_groups(B);
+        if (rc) return rc;
+    }
     BCHK(cudaStreamSynchronize(B.stream));
     return QSLBM_OK;
 }
@@ -479,21 +611,69 @@ int autotune(qslbm_batch& B) {
     return build_tables<T>(B, B.threads);
 }
 
+// Capture `steps` flow steps into one graph (the parities live in device
+// memory, so a graph replays any steps).
 template <typename T>
-int capture(qslbm_batch& B) {
-    if (B.graph) {
-        cudaGraphExecDestroy(B.graph);
-        B.graph = nullptr;
+int capture_steps(qslbm_batch& B, int steps, cudaGraphExec_t* out) {
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
     }
     cudaGraph_t g = nullptr;
+    B.launch_err = cudaSuccess;
     BCHK(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
-    launch_step<T>(B, B.stream);
+    for (int i = 0; i < steps; ++i) launch_step<T>(B, B.stream);
     cudaError_t e = cudaStreamEndCapture(B.stream, &g);
+    if (e == cudaSuccess && B.launch_err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(B.launch_err, "cudaLaunchKernelEx (k_batch_resident)");
+    }
     if (e != cudaSuccess) return fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&B.graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
     return QSLBM_OK;
+}
+
+// Launches of one flow step: the group kernel, each marching sweep with its
+// IB pass (or two), force, flow, parity advance.
+int step_launches(const qslbm_batch& B) {
+    int n = 3 + (B.ngroups > 0 ? 1 : 0);
+    for (int s = 0; s < B.max_nmag; ++s)
+        if (B.active[s] > 0) n += 1 + (B.h_mfirst[B.active[s]] > 0 ? (B.ib_staged_smem ? 1 : 2) : 0);
+    return n;
+}
+
+// The one-step graph and a graph of many steps (chunk_target, or as many as
+// keep it near kChunkLaunches launches), which qslbm_batch_step replays.
+constexpr int kChunkLaunches = 4096;
+
+template <typename T>
+int capture(qslbm_batch& B) {
+    int rc = capture_steps<T>(B, 1, &B.graph);
+    if (rc) return rc;
+    B.chunk_steps = std::max(1, std::min(B.chunk_target, kChunkLaunches / step_launches(B)));
+    if (B.chunk_steps == 1) {
+        if (B.graph_chunk) cudaGraphExecDestroy(B.graph_chunk);
+        B.graph_chunk = nullptr;
+        return QSLBM_OK;
+    }
+    return capture_steps<T>(B, B.chunk_steps, &B.graph_chunk);
+}
+
+// A timed-out neighbour wait of the group kernel, seen after the stream's
+// work: restart the counters and report it.
+int check_groups(qslbm_batch& B) {
+    if (B.ngroups == 0 || !B.gerr) return QSLBM_OK;
+    int bad = 0;
+    BCHK(cudaMemcpyAsync(&bad, B.gerr, sizeof(int), cudaMemcpyDeviceToHost, B.stream));
+    BCHK(cudaStreamSynchronize(B.stream));
+    if (!bad) return QSLBM_OK;
+    BCHK(cudaMemsetAsync(B.gflags, 0, sizeof(unsigned) * B.ngroups, B.stream));
+    BCHK(cudaMemsetAsync(B.gerr, 0, sizeof(int), B.stream));
+    BCHK(cudaStreamSynchronize(B.stream));
+    qslbm::set_last_error("batched resident sweep: a neighbour wait timed out");
+    return QSLBM_ETIMEOUT;
 }
 
 // Mirror the device-side parity updates on the members' host state.
@@ -511,7 +691,12 @@ void destroy_batch(qslbm_batch* B) {
     if (!B) return;
     if (B->stream) cudaStreamSynchronize(B->stream);
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->graph_chunk) cudaGraphExecDestroy(B->graph_chunk);
     if (B->desc) cudaFree(B->desc);
+    if (B->groups) cudaFree(B->groups);
+    if (B->gflags) cudaFree(B->gflags);
+    if (B->gerr) cudaFree(B->gerr);
+    if (B->xbuf) cudaFree(B->xbuf);
     if (B->first) cudaFree(B->first);
     if (B->pfirst) cudaFree(B->pfirst);
     if (B->mfirst) cudaFree(B->mfirst);
@@ -522,38 +707,114 @@ void destroy_batch(qslbm_batch* B) {
     delete B;
 }
 
-// (Re)build the batch over the given handles: order by N_mag, device tables,
-// autotune (first time only) and the per-step graph.  The handles' host parity
-// must match their device buffers (true for handles created by this library).
-int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs) {
+// (Re)build the batch over the given handles: choose the members the
+// resident group kernel holds (allowed ones that fit, smallest first, while
+// their groups fit co-resident on the device), order the marching members by
+// N_mag, device tables, autotune (first time only) and the per-step graph.
+// The handles' host parity must match their device buffers (true for handles
+// created by this library).  allow[i] (empty: all) lets handle i run in the
+// group kernel.
+int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs, const std::vector<char>& allow) {
     const int count = (int)hs.size();
     B->members.clear();
     B->order.assign(count, 0);
     B->rank.assign(count, 0);
+    B->gplanes.clear();
+    B->kmarch = 0;
+    B->ngroups = 0;
     if (count == 0) {
         if (B->graph) {
             cudaGraphExecDestroy(B->graph);
             B->graph = nullptr;
         }
+        if (B->graph_chunk) {
+            cudaGraphExecDestroy(B->graph_chunk);
+            B->graph_chunk = nullptr;
+        }
         B->max_nmag = 0;
         B->active.clear();
         return QSLBM_OK;
     }
+    // planes per group of each handle, and the members the launch can hold
+    std::vector<int> gp(count, 0);
+    if (B->precision == QSLBM_FP32) {
+        int dev = 0, sms = 0, optin = 0, occ = 0;
+        BCHK(cudaGetDevice(&dev));
+        BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        // dynamic shared memory a CTA may take: the opt-in limit less the
+        // kernel's static shared memory
+        const void* fn = (const void*)qslbm::k_batch_resident<qslbm::InstDesc<float>, true>;
+        cudaFuncAttributes fa;
+        BCHK(cudaFuncGetAttributes(&fa, fn));
+        optin -= (int)fa.sharedSizeBytes;
+        BCHK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        BCHK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, qslbm::kGroupThreads, optin));
+        const int cap = occ * sms;
+        std::vector<int> cand;
+        for (int i = 0; i < count; ++i) {
+            if (!allow.empty() && !allow[i]) continue;
+            gp[i] = group_planes(qslbm::handle_state_mut(hs[i]), optin);
+            if (gp[i] > 0) cand.push_back(i);
+        }
+        std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+            return qslbm::handle_state_mut(hs[a]).n < qslbm::handle_state_mut(hs[b]).n;
+        });
+        int used = 0;
+        std::vector<int> adm;
+        for (int i : cand) {
+            const int ng = group_count(qslbm::handle_state_mut(hs[i]), gp[i]);
+            if (used + ng <= cap) {
+                used += ng;
+                adm.push_back(i);
+            } else {
+                gp[i] = 0;
+            }
+        }
+        // spread the admitted members over every co-resident CTA: the
+        // smallest group size (nodes) at which their groups still fit
+        auto planes_at = [&](int i, int T) {
+            const State& s = qslbm::handle_state_mut(hs[i]);
+            const int G = std::max(1, std::min(gp[i], T / (s.nx * s.ny)));
+            return (s.nz + group_count(s, G) - 1) / group_count(s, G);
+        };
+        auto groups_at = [&](int T) {
+            int tot = 0;
+            for (int i : adm) tot += group_count(qslbm::handle_state_mut(hs[i]), planes_at(i, T));
+            return tot;
+        };
+        int lo = 1, hi = qslbm::kGroupMaxNodes;  // groups_at(hi) <= cap
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (groups_at(mid) <= cap)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        std::vector<int> spread(count, 0);
+        for (int i : adm) spread[i] = planes_at(i, lo);
+        for (int i : adm) gp[i] = spread[i];
+    }
     std::vector<int> idx(count);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        if ((gp[a] > 0) != (gp[b] > 0)) return gp[b] > 0;  // marching members first
         return qslbm::handle_state_mut(hs[a]).units.n_mag > qslbm::handle_state_mut(hs[b]).units.n_mag;
     });
     B->order = idx;
     for (int k = 0; k < count; ++k) {
         B->members.push_back(hs[idx[k]]);
         B->rank[idx[k]] = k;
+        B->gplanes.push_back(gp[idx[k]]);
+        if (gp[idx[k]] == 0) B->kmarch = k + 1;
     }
-    B->max_nmag = qslbm::handle_state_mut(B->members[0]).units.n_mag;
+    B->max_nmag = 0;
+    for (qslbm_handle* h : B->members) B->max_nmag = std::max(B->max_nmag, qslbm::handle_state_mut(h).units.n_mag);
+    // active[s]: marching members with N_mag > s (a prefix)
     B->active.assign(B->max_nmag, 0);
     for (int s = 0; s < B->max_nmag; ++s) {
         int a = 0;
-        while (a < count && qslbm::handle_state_mut(B->members[a]).units.n_mag > s) ++a;
+        while (a < B->kmarch && qslbm::handle_state_mut(B->members[a]).units.n_mag > s) ++a;
         B->active[s] = a;
     }
     int rc;
@@ -600,7 +861,11 @@ int create_batch(const qslbm_params* params, int32_t count, void* stream, qslbm_
             return rc;
         }
     }
-    int rc = set_members(B, hs);
+    // QSLBM_SWEEP_SPLIT keeps a member on the marching sweep; any other choice
+    // lets it run in the resident group kernel when it fits
+    std::vector<char> allow(count);
+    for (int i = 0; i < count; ++i) allow[i] = params[i].sweep_kernel != QSLBM_SWEEP_SPLIT;
+    int rc = set_members(B, hs, allow);
     if (rc) {
         destroy_batch(B);
         return rc;
@@ -624,7 +889,10 @@ int qslbm_batch_create(const qslbm_params* params, int32_t count, void* stream, 
 int qslbm_batch_step(qslbm_batch* B, int64_t nsteps) {
     if (!B || nsteps < 0) return QSLBM_EINVAL;
     if (B->members.empty()) return QSLBM_OK;
-    for (long long i = 0; i < nsteps; ++i) BCHK(cudaGraphLaunch(B->graph, B->stream));
+    long long i = 0;
+    if (B->graph_chunk)
+        for (; i + B->chunk_steps <= nsteps; i += B->chunk_steps) BCHK(cudaGraphLaunch(B->graph_chunk, B->stream));
+    for (; i < nsteps; ++i) BCHK(cudaGraphLaunch(B->graph, B->stream));
     advance_host(*B, nsteps);
     return QSLBM_OK;
 }
@@ -632,6 +900,8 @@ int qslbm_batch_step(qslbm_batch* B, int64_t nsteps) {
 int qslbm_batch_handle(qslbm_batch* B, int32_t i, qslbm_handle** out) {
     if (!B || !out || i < 0 || i >= (int)B->members.size()) return QSLBM_EINVAL;
     BCHK(cudaStreamSynchronize(B->stream));
+    const int rc = check_groups(*B);
+    if (rc) return rc;
     *out = B->members[B->rank[i]];
     return QSLBM_OK;
 }
@@ -643,7 +913,9 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
     info->max_n_mag = B->max_nmag;
     info->sweep_threads = B->threads;
     info->sweep_grid = B->grid;
-    long long nodes = 0, bytes = B->device_bytes, sweeps = 0;
+    long long nodes = 0, sweeps = 0;
+    long long bytes = B->device_bytes + (long long)B->groups_cap * (sizeof(qslbm::GroupDesc) + sizeof(unsigned)) +
+                      B->xbuf_cap * (long long)sizeof(float) + (B->gerr ? (long long)sizeof(int) : 0);
     for (qslbm_handle* h : B->members) {
         const State& s = qslbm::handle_state_mut(h);
         nodes += s.n;
@@ -653,7 +925,11 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
     info->nodes = nodes;
     info->node_sweeps_per_step = sweeps;
     info->device_bytes = bytes;
-    info->launches_per_step = (B->ib_staged_smem ? 2 : 3) * B->max_nmag + 3;  // sweep + IB per sweep; force, flow, advance
+    info->launches_per_step = B->members.empty() ? 0 : step_launches(*B);
+    info->resident_instances = (int32_t)B->members.size() - B->kmarch;
+    info->resident_groups = B->ngroups;
+    info->graph_steps = B->chunk_steps;
+    info->march_chunk = B->chunk;
     info->steps = B->steps;
     for (size_t c = 0; c < B->tune_us.size() && c < 8; ++c) info->tune_us[c] = B->tune_us[c];
     return QSLBM_OK;
@@ -802,13 +1078,18 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
     }
     if (changed) {
         std::vector<qslbm_handle*> hs;
-        for (const Running& r : S.running) hs.push_back(r.h);
-        int rc = set_members(S.batch, hs);
+        std::vector<char> allow;
+        for (const Running& r : S.running) {
+            hs.push_back(r.h);
+            allow.push_back(r.r.p.sweep_kernel != QSLBM_SWEEP_SPLIT);
+        }
+        int rc = set_members(S.batch, hs, allow);
         if (rc) return rc;
         ++S.rebuilds;
     }
     if (!S.running.empty()) {
         int rc = qslbm_batch_step(S.batch, S.cfg.chunk_steps);
+        if (!rc) rc = check_groups(*S.batch);
         if (rc) return rc;
         ++S.chunks;
         S.steps += S.cfg.chunk_steps;
@@ -838,8 +1119,12 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
                 if (r.h) keep.push_back(r);
             S.running.swap(keep);
             std::vector<qslbm_handle*> hs;
-            for (const Running& r : S.running) hs.push_back(r.h);
-            rc = set_members(S.batch, hs);
+            std::vector<char> allow;
+            for (const Running& r : S.running) {
+                hs.push_back(r.h);
+                allow.push_back(r.r.p.sweep_kernel != QSLBM_SWEEP_SPLIT);
+            }
+            rc = set_members(S.batch, hs, allow);
             if (rc) return rc;
             ++S.rebuilds;
         }
@@ -871,6 +1156,7 @@ int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out) {
     }
     B->owns_members = false;
     B->precision = cfg->precision;
+    B->chunk_target = (int)std::min<int64_t>(cfg->chunk_steps, 1000);
     if (cfg->stream) {
         B->stream = (cudaStream_t)cfg->stream;
     } else {

@@ -113,3 +113,76 @@ def test_batched_workload_member_matches_oracle(precision):
     assert rel(u, ou) <= tol and rel(bb, ob) <= tol, (rel(u, ou), rel(bb, ob))
     if precision == "fp64":
         assert np.abs(rho - orho).max() <= 1e-12
+
+
+def grouped(precision="fp32"):
+    # more planes than the device has CTA slots (217 against 152 SMs), so that
+    # the group kernel splits them: 2-plane groups of the two 24 x 24 x 96
+    # pipes, 1-plane groups of the 40 x 40 x 20 pipe, two unequal groups (2 and
+    # 1 planes, each the other's both neighbours) of a 3-plane pipe, and one
+    # group of every plane (2 planes)
+    return [
+        W.small_pipe(nx=24, ny=24, nz=96, diameter=16.0, Re=200.0, Ha=30.0, Rm=1e-3, precision=precision, seed=11),
+        W.small_pipe(nx=24, ny=24, nz=96, diameter=18.0, Re=60.0, Ha=10.0, Rm=2e-3, b0_kind="tanh",
+                     ramp_center=48.0, ramp_width=8.0, precision=precision, seed=16),
+        W.small_pipe(nx=40, ny=40, nz=20, diameter=32.0, Re=80.0, Ha=50.0, Rm=5e-3, b0_kind="tanh",
+                     ramp_center=10.0, ramp_width=4.0, precision=precision, seed=12),
+        W.small_pipe(nx=24, ny=24, nz=3, diameter=18.0, Re=40.0, Ha=10.0, Rm=2e-2, n_mag=60, precision=precision,
+                     seed=13),
+        W.small_pipe(nx=20, ny=20, nz=2, diameter=14.0, n_mag=33, precision=precision, seed=14),
+    ]
+
+
+def test_resident_groups_match_single_instances():
+    import torch
+
+    ps = grouped()
+    steps = 5
+    with Batch(ps) as B:
+        info = B.info()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert info["resident_instances"] == len(ps)
+        assert len(ps) < info["resident_groups"] <= sms
+        assert info["launches_per_step"] == 4  # groups, force, flow, parity advance
+        assert info["graph_steps"] > 1
+        B.step(steps)
+        got = [B.member(i).state() for i in range(len(ps))]
+    for i, p in enumerate(ps):
+        with Solver(dict(p, sweep_kernel="split")) as s:
+            s.step(steps)
+            want = s.state()
+        for a, b in zip(got[i], want):
+            assert rel(a, b) <= 1e-6, i
+
+
+def test_resident_groups_and_marching_in_one_batch():
+    # the same instances, half of them kept on the marching sweep, and one too
+    # large for a group (a 96 x 96 plane): every member as when the batch holds
+    # only its own kind
+    ps = grouped()
+    ps = [dict(p, sweep_kernel="split") if k % 2 else p for k, p in enumerate(ps)]
+    big = W.small_pipe(nx=96, ny=96, nz=4, diameter=88.0, Re=500.0, Ha=50.0, Rm=1e-2, n_mag=40, seed=15)
+    steps = 4
+    with Batch(ps + [big]) as B:
+        info = B.info()
+        assert info["resident_instances"] == 3
+        B.step(steps)
+        mixed = [B.member(i).state() for i in range(len(ps) + 1)]
+    for i, p in enumerate(ps + [big]):
+        with Batch([p]) as A:
+            A.step(steps)
+            alone = A.member(0).state()
+        for a, b in zip(mixed[i], alone):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_resident_groups_chunked_steps_equal_single_steps():
+    ps = grouped()[:2]
+    with Batch(ps) as A, Batch(ps) as B:
+        n = A.info()["graph_steps"] + 3  # one chunk graph and three single steps
+        A.step(n)
+        for _ in range(n):
+            B.step(1)
+        for i in range(len(ps)):
+            for a, b in zip(A.member(i).state(), B.member(i).state()):
+                np.testing.assert_array_equal(a, b)
