@@ -397,8 +397,7 @@ int group_planes(const State& s, int optin) {
     const int P = s.nx * s.ny;
     if (P > qslbm::kGroupMaxNodes) return 0;
     int G = std::min(s.nz, qslbm::kGroupMaxNodes / P);
-    while (G > 0 && qslbm::group_smem_bytes(G * P, s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G) > (size_t)optin)
-        --G;
+    while (G > 0 && qslbm::group_smem_bytes(s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G) > (size_t)optin) --G;
     if (G == 0) return 0;
     const int ng = (s.nz + G - 1) / G;
     return (s.nz + ng - 1) / ng;  // the largest group of the balanced split
@@ -432,7 +431,7 @@ int build_groups(qslbm_batch& B) {
             xoff += 12LL * P;
             z0 += G;
             B.h_groups.push_back(g);
-            smem = std::max(smem, qslbm::group_smem_bytes(G * P, s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G));
+            smem = std::max(smem, qslbm::group_smem_bytes(s.ib.max_ring, s.ib.max_shell, s.ib.max_nnz, G));
         }
     }
     B.ngroups = (int)B.h_groups.size();

@@ -26,8 +26,12 @@
 namespace qslbm {
 
 constexpr int kGroupThreads = 1024;
-constexpr int kGroupNpt = 6;                                  // nodes per thread, at most
+constexpr int kGroupNpt = 5;                                  // nodes per thread, at most
 constexpr int kGroupMaxNodes = kGroupThreads * kGroupNpt;     // nodes a CTA holds, at most
+// Shared-memory stride of one field component (nodes): a compile-time
+// constant, so that the components of a node are one base address apart by
+// immediate offsets.
+constexpr int kGS = kGroupMaxNodes;
 
 // One CTA's group: planes z0 .. z0 + G - 1 of instance inst; prev / next: the
 // groups holding planes z0 - 1 and z0 + G (periodic; possibly itself); xoff:
@@ -37,12 +41,12 @@ struct GroupDesc {
     long long xoff;
 };
 
-// Shared memory of one group (bytes): two buffers of b and one of e for its
-// GN nodes, B^ext of its G planes and their two neighbours, the IB tables of
-// one ring (R markers, S shell nodes, E list entries) and the deltas of its G
-// rings.  A launch gives every CTA the largest group's size.
-inline size_t group_smem_bytes(int GN, int R, int S, int E, int G) {
-    const size_t f = (size_t)9 * GN + (size_t)3 * (G + 2) + (size_t)10 * R + E + (size_t)3 * G * R;
+// Shared memory of one group (bytes): two buffers of b and one of e (kGS
+// nodes each), B^ext of its G planes and their two neighbours, the IB tables
+// of one ring (R markers, S shell nodes, E list entries) and the deltas of
+// its G rings.  A launch gives every CTA the largest group's size.
+inline size_t group_smem_bytes(int R, int S, int E, int G) {
+    const size_t f = (size_t)9 * kGS + (size_t)3 * (G + 2) + (size_t)10 * R + E + (size_t)3 * G * R;
     const size_t i = (size_t)9 * R + S + (S + 1) + E;
     return f * sizeof(float) + i * sizeof(int) + 16;
 }
@@ -80,11 +84,11 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
     const int E = S > 0 ? D.ibm.csr_off[s0 + S] - e0 : 0;
     const int zm = z0 == 0 ? nz - 1 : z0 - 1;  // plane below the group
     const int zp = z0 + G == nz ? 0 : z0 + G;  // plane above it
-    // shared memory: b [2][3][GN] (sweep s reads b[s % 2], writes b[(s + 1) % 2]),
-    // e [3][GN], B^ext [G + 2][3], tables, deltas
+    // shared memory: b [2][3][kGS] (sweep s reads b[s % 2], writes b[(s + 1) % 2]),
+    // e [3][kGS], B^ext [G + 2][3], tables, deltas
     float* sb0 = reinterpret_cast<float*>(smem_raw);
-    float* se = sb0 + 6 * GN;
-    float* sbz = se + 3 * GN;           // B^ext of planes zm, z0 .. z0 + G - 1, zp
+    float* se = sb0 + 6 * kGS;
+    float* sbz = se + 3 * kGS;           // B^ext of planes zm, z0 .. z0 + G - 1, zp
     float* tw = sbz + 3 * (G + 2);      // [9 R] weights D(x_k - X_j)
     float* tsc = tw + 9 * R;            // [R]   s^m_j
     float* tcw = tsc + R;               // [E]   list weights
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
         const float* __restrict__ bin = D.b[D.bpar];
         for (int i = tid; i < GN; i += kGroupThreads)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) sb0[a * GN + i] = bin[a * n + z0 * P + i];
+            for (int a = 0; a < 3; ++a) sb0[a * kGS + i] = bin[a * n + z0 * P + i];
     }
     __syncthreads();
     const unsigned int base = s_base;
@@ -140,8 +144,8 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
     int s = 0;  // sweeps done
     for (; s < nmag; ++s) {
         const float* __restrict__ u = D.u[D.fpar];
-        const float* sb = sb0 + (s & 1) * 3 * GN;       // b after sweep s - 1
-        float* sn = sb0 + ((s + 1) & 1) * 3 * GN;       // b after sweep s
+        const float* sb = sb0 + (s & 1) * 3 * kGS;      // b after sweep s - 1
+        float* sn = sb0 + ((s + 1) & 1) * 3 * kGS;      // b after sweep s
         // (a) every node's e from its b (shared memory) and u (L2); the loads
         // of u are issued kGroupNpt / 2 nodes at a time before their first use
 #pragma unroll 1
@@ -166,11 +170,11 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
                     const int g = group_div(i, P, mP);
                     float be[3] = {sbz[3 * g + 3], sbz[3 * g + 4], sbz[3 * g + 5]};
                     if constexpr (XY) bext_add_xy(bxy, P, i - g * P, be);
-                    float r[6] = {sb[i], sb[GN + i], sb[2 * GN + i], ur[k][0], ur[k][1], ur[k][2]};
+                    float r[6] = {sb[i], sb[kGS + i], sb[2 * kGS + i], ur[k][0], ur[k][1], ur[k][2]};
                     node_emf(r, be, sq);
                     se[i] = r[3];
-                    se[GN + i] = r[4];
-                    se[2 * GN + i] = r[5];
+                    se[kGS + i] = r[4];
+                    se[2 * kGS + i] = r[5];
                 }
             }
         }
@@ -201,49 +205,63 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
                 r[5] = __ldg(u + 2 * n + zz * P + p);
                 node_emf(r, be, s_w[3]);
             };
+            const float* E1 = se;
+            const float* E2 = se + kGS;
+            const float* E3 = se + 2 * kGS;
+            // each thread walks whole z columns of the group: the column's
+            // (b, e) at planes g - 1, g, g + 1 stay in registers
 #pragma unroll 1
-            for (int i = tid; i < GN; i += kGroupThreads) {
-                {
-                    const int g = group_div(i, P, mP), p = i - g * P;
-                    const int y = group_div(p, nx, mX), x = p - y * nx;
-                    const int il = x == 0 ? i + nx - 1 : i - 1, ir = x == nx - 1 ? i - nx + 1 : i + 1;
-                    const int iu = y == 0 ? i + P - nx : i - nx, id = y == ny - 1 ? i - P + nx : i + nx;
-                    float zl[6], zh[6];  // (b, e) of the z neighbours below and above
-                    if (g > 0 || whole) {
-                        const int j = g > 0 ? i - P : i + (G - 1) * P;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            zl[a] = sb[a * GN + j];
-                            zl[3 + a] = se[a * GN + j];
-                        }
-                    } else {
-                        halo(s == 0 ? bin + zm * P : xp, s == 0 ? n : P, zm, 0, p, zl);
-                    }
-                    if (g < G - 1 || whole) {
-                        const int j = g < G - 1 ? i + P : i - (G - 1) * P;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            zh[a] = sb[a * GN + j];
-                            zh[3 + a] = se[a * GN + j];
-                        }
-                    } else {
-                        halo(s == 0 ? bin + zp * P : xq, s == 0 ? n : P, zp, G + 1, p, zh);
-                    }
-                    const float* E1 = se;
-                    const float* E2 = se + GN;
-                    const float* E3 = se + 2 * GN;
+            for (int p = tid; p < P; p += kGroupThreads) {
+                const int y = group_div(p, nx, mX), x = p - y * nx;
+                const int dl = x == 0 ? nx - 1 : -1, dr = x == nx - 1 ? 1 - nx : 1;
+                const int du = y == 0 ? P - nx : -nx, dd = y == ny - 1 ? nx - P : nx;
+                float prv[6], cur[6], nxt[6];
+                if (whole) {
+                    const int j = (G - 1) * P + p;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        const float* Ba = sb + a * GN;
-                        const float sa = (Ba[il] + Ba[ir]) + (Ba[iu] + Ba[id]) + (zl[a] + zh[a]);
+                        prv[a] = sb[a * kGS + j];
+                        prv[3 + a] = se[a * kGS + j];
+                    }
+                } else {
+                    halo(s == 0 ? bin + zm * P : xp, s == 0 ? n : P, zm, 0, p, prv);
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cur[a] = sb[a * kGS + p];
+                    cur[3 + a] = se[a * kGS + p];
+                }
+#pragma unroll 1
+                for (int g = 0; g < G; ++g) {
+                    const int i = g * P + p;
+                    if (g < G - 1 || whole) {
+                        const int j = g < G - 1 ? i + P : p;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            nxt[a] = sb[a * kGS + j];
+                            nxt[3 + a] = se[a * kGS + j];
+                        }
+                    } else {
+                        halo(s == 0 ? bin + zp * P : xq, s == 0 ? n : P, zp, G + 1, p, nxt);
+                    }
+                    const int il = i + dl, ir = i + dr, iu = i + du, id = i + dd;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float* Ba = sb + a * kGS;
+                        const float sa = (Ba[il] + Ba[ir]) + (Ba[iu] + Ba[id]) + (prv[a] + nxt[a]);
                         float da;
                         if (a == 0)
-                            da = (E1[id] - E1[iu]) + (zh[4] - zl[4]);
+                            da = (E1[id] - E1[iu]) + (nxt[4] - prv[4]);
                         else if (a == 1)
-                            da = (E1[il] - E1[ir]) + (zh[5] - zl[5]);
+                            da = (E1[il] - E1[ir]) + (nxt[5] - prv[5]);
                         else
                             da = (E2[il] - E2[ir]) + (E3[iu] - E3[id]);
-                        sn[a * GN + i] = emf_update(w0, w1, w1k, Ba[i], sa, da);
+                        sn[a * kGS + i] = emf_update(w0, w1, w1k, cur[a], sa, da);
+                    }
+#pragma unroll
+                    for (int v = 0; v < 6; ++v) {
+                        prv[v] = cur[v];
+                        cur[v] = nxt[v];
                     }
                 }
             }
@@ -263,8 +281,8 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
                     const float w = tw[9 * m + j];
                     const int q = tq[9 * m + j];
                     a0 += w * f[q];
-                    a1 += w * f[GN + q];
-                    a2 += w * f[2 * GN + q];
+                    a1 += w * f[kGS + q];
+                    a2 += w * f[2 * kGS + q];
                 }
                 const float sm = tsc[m];
                 sdelta[3 * t + 0] = -sm * a0;
@@ -286,8 +304,8 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
                 }
                 const int q = g * P + tshell[k];
                 sn[q] += c0;
-                sn[GN + q] += c1;
-                sn[2 * GN + q] += c2;
+                sn[kGS + q] += c1;
+                sn[2 * kGS + q] += c2;
             }
             __syncthreads();
         }
@@ -299,7 +317,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
                     const int h = t >= P, p = t - h * P;
                     const int i = h ? (G - 1) * P + p : p;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) __stcg(xo + h * 3 * P + a * P + p, sn[a * GN + i]);
+                    for (int a = 0; a < 3; ++a) __stcg(xo + h * 3 * P + a * P + p, sn[a * kGS + i]);
                 }
                 __syncthreads();
             }
@@ -310,11 +328,11 @@ __global__ void __launch_bounds__(kGroupThreads, 1)
         }
     }
     // the b of the last sweep done (all of them unless a wait gave up)
-    const float* sb = sb0 + (s & 1) * 3 * GN;
+    const float* sb = sb0 + (s & 1) * 3 * kGS;
     float* __restrict__ bfin = D.b[(D.bpar + nmag) & 1];
     for (int i = tid; i < GN; i += kGroupThreads)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) bfin[a * n + z0 * P + i] = sb[a * GN + i];
+        for (int a = 0; a < 3; ++a) bfin[a * n + z0 * P + i] = sb[a * kGS + i];
 }
 
 }  // namespace qslbm
