@@ -326,32 +326,41 @@ def run_batched(steps: int = 3, count: int = 64):
             "MLUPS": info["nodes"] / ms / 1e3, "sweep_GLUPS": info["node_sweeps_per_step"] / ms / 1e6,
             "tuned_sweep": {"threads": info["sweep_threads"], "grid": info["sweep_grid"],
                             "candidates_us": [round(x, 1) for x in info["tune_us"]]},
-            "launches_per_step": info["launches_per_step"], "build_s": build_s, "steps": steps}
+            "launches_per_step": info["launches_per_step"], "graph_steps": info["graph_steps"],
+            "resident_instances": info["resident_instances"], "resident_groups": info["resident_groups"],
+            "build_s": build_s, "steps": steps}
 
 
-def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_steps: int = 20000, chunk: int = 100,
-                diameters=(16, 24), time_cap_s: float = 150.0, baseline: int = 4):
-    """Serving: Poisson arrivals of steady-state pipe solves (seed 5; diameters
-    restricted so that the run stays bounded), admitted under a device-memory
-    budget and advanced by continuous batching in FP32.  Reports solves/s and
-    p50/p99 latency (submit to result) of the converged requests, and solves/s
-    of the first `baseline` requests solved one at a time in FP64 with the same
-    stop rule, with the largest rel-L2 between the two answers."""
+def run_serving(window_s: float = 30.0, time_cap_s: float = 120.0, rate: float = 20.0, tol: float = 1e-6,
+                max_steps: int = 20000, chunk: int = 200, max_running: int = 16, budget: int = 64 << 20,
+                fp64_cap_s: float = 150.0):
+    """Serving at the stated request mix: Poisson arrivals (mean `rate` per
+    second, seed 5) during the first `window_s` seconds of steady-state pipe
+    solves with D in {16, 32, 48, 64, 96, 128}, box (D + 8)^2 x 6D, starting
+    from the Poiseuille profile, stop at FP64 steady residual `tol` or
+    `max_steps`; FP32 fields, admitted smallest first under an HBM budget and
+    at most `max_running` at a time, advanced by continuous batching until
+    `time_cap_s`.  The stated arrivals bring about 10^3 times more work than
+    one GPU can finish (a D = 128 solve alone needs ~10^6 steps of 14 M
+    nodes), so the budget (64 MB) admits the pipes that can reach the residual
+    within minutes (D <= 32) and answers larger ones at once with
+    QSLBM_EBUDGET.  Reports solves/s and p50/p99 time-to-steady (submit to
+    result) of the converged requests, and every request's outcome by
+    diameter.  The FP64 arm solves the first converged request alone in FP64
+    (a single-instance handle, same stop rule) to convergence and reports its
+    wall time and the rel-L2 between the two steady answers."""
     import threading as th
 
     import numpy as np
 
     from paper_2211_09370_gb300 import _lib
 
-    reqs = []
-    for r in W.serving_requests(n=8 * count, seed=5, rate=rate):
-        D = int(r["params"]["diameter"])
-        if D in diameters:
-            reqs.append((r["arrival_s"], dict(r["params"], init_kind="poiseuille", nz=6 * D)))
-        if len(reqs) == count:
-            break
+    reqs = [(r["arrival_s"], dict(r["params"], init_kind="poiseuille"))
+            for r in W.serving_requests(n=int(rate * window_s * 2) + 10, seed=5, rate=rate)
+            if r["arrival_s"] < window_s]
     t_first = reqs[0][0]
-    S = _lib.Server(hbm_budget_bytes=8 << 30, chunk_steps=chunk, precision="fp32")
+    S = _lib.Server(hbm_budget_bytes=budget, chunk_steps=chunk, max_running=max_running, precision="fp32",
+                    admit="smallest")
     ids = [None] * len(reqs)
     t0 = time.perf_counter()
 
@@ -360,61 +369,70 @@ def run_serving(count: int = 12, rate: float = 20.0, tol: float = 1e-6, max_step
             delay = (ta - t_first) - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            ids[k] = S.submit(p, tol=tol, max_steps=max_steps)
+            ids[k] = S.submit(p, tol=tol, max_steps=max_steps, keep_fields=int(p["diameter"]) == 16)
 
     feed = th.Thread(target=feeder, daemon=True)
     feed.start()
-    results = {}
+    results, kept = {}, None
     while (len(results) < len(reqs) or feed.is_alive()) and time.perf_counter() - t0 < time_cap_s:
         nr, npd = S.run()
         for r in S.poll():
             results[r["id"]] = r
+            if int(S.params[r["id"]]["diameter"]) == 16 and r["status"] in (0, _lib.ETIMEOUT, _lib.EUNSTABLE):
+                if kept is None and r["status"] == 0:
+                    kept = r["id"]
+                else:
+                    S.release(r["id"])
         if nr == 0 and npd == 0 and feed.is_alive():
             time.sleep(0.002)
     elapsed = time.perf_counter() - t0
     feed.join(timeout=1)
+    stats = S.stats()
     ok = [r for r in results.values() if r["status"] == 0]
     lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
-    stats = S.stats()
-    by_k = {k: results.get(ids[k]) for k in range(len(reqs))}
+    by_d = {}
+    for k, (_, p) in enumerate(reqs):
+        d = by_d.setdefault(int(p["diameter"]), {"submitted": 0, "converged": 0, "step_cap": 0, "over_budget": 0,
+                                                 "other": 0, "unfinished": 0})
+        d["submitted"] += 1
+        r = results.get(ids[k]) if ids[k] is not None else None
+        if r is None:
+            d["unfinished"] += 1
+        else:
+            key = {0: "converged", _lib.ETIMEOUT: "step_cap", _lib.EBUDGET: "over_budget"}.get(r["status"], "other")
+            d[key] += 1
+    served_fields = S.fields(kept) if kept is not None else None
+    kept_req = S.params[kept] if kept is not None else None
+    kept_res = results.get(kept)
     S.close()
-    # The same first requests one at a time in FP64 (single-instance handles).
-    # A full FP64 solve of a request that needs ~10^4 steps takes minutes, so
-    # the FP64 step time is measured over `fp64_probe` steps and multiplied by
-    # the steps the served solve needed; accuracy is compared at equal steps.
-    fp64_probe = 200
-    t64_total, worst, solve_s = 0.0, 0.0, []
-    for k in range(min(baseline, len(reqs))):
-        r = by_k.get(k)
-        if not r or r["status"] != 0:
-            continue
-        with _lib.Solver(dict(reqs[k][1], precision="fp64")) as s64, \
-                _lib.Solver(dict(reqs[k][1], precision="fp32", sweep_kernel="split")) as s32:
-            s64.step(2)
-            s64.sync()
+    fp64 = {"requests": 0}
+    if kept_req is not None:
+        with _lib.Solver(dict(kept_req, precision="fp64")) as s64:
             t1 = time.perf_counter()
-            s64.step(fp64_probe)
-            s64.sync()
+            steps, res = 0, float("inf")
+            while steps < max_steps and time.perf_counter() - t1 < fp64_cap_s:
+                s64.step(chunk)
+                steps += chunk
+                res = s64.observables()["steady_residual"]
+                if res < tol:
+                    break
             dt = time.perf_counter() - t1
-            t64_total += dt
-            solve_s.append(dt / fp64_probe * r["steps"])
-            s32.step(fp64_probe + 2)
-            a = s32.state()
-            b = s64.state()
-            for x, y in zip(a[1:], b[1:]):
-                worst = max(worst, float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)))
+            f64 = s64.state()
+        worst = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                    for a, b in zip(served_fields[1:], f64[1:]))
+        fp64 = {"requests": 1, "diameter": int(kept_req["diameter"]), "converged": bool(res < tol),
+                "steps": steps, "residual": res, "seconds_per_solve": dt, "solves_per_s": 1.0 / dt,
+                "served_steps": kept_res["steps"], "method": "solved alone to the same stop rule, FP64 handle",
+                "fp32_served_vs_fp64_rel_l2": worst}
     pct = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None  # noqa: E731
-    return {"requests": len(reqs), "completed": len(results), "converged": len(ok),
+    return {"mix": "D in {16,32,48,64,96,128}, box (D+8)^2 x 6D, Poisson arrivals, seed 5",
+            "arrival_rate_per_s": rate, "window_s": window_s, "time_cap_s": time_cap_s, "tol": tol,
+            "max_steps": max_steps, "chunk_steps": chunk, "max_running": max_running, "admit": "smallest first",
+            "hbm_budget_bytes": budget, "requests": len(reqs), "converged": len(ok),
             "solves_per_s": len(ok) / elapsed, "p50_s": pct(0.5), "p99_s": pct(0.99), "elapsed_s": elapsed,
-            "arrival_rate_per_s": rate, "tol": tol, "chunk_steps": chunk, "max_steps": max_steps,
-            "diameters": list(diameters),
             "mean_steps_converged": float(np.mean([r["steps"] for r in ok])) if ok else None,
-            "statuses": sorted({r["status"] for r in results.values()}), "rebuilds": stats["rebuilds"],
-            "fp64_one_at_a_time": {"requests": len(solve_s),
-                                   "seconds_per_solve": float(np.mean(solve_s)) if solve_s else None,
-                                   "solves_per_s": len(solve_s) / float(np.sum(solve_s)) if solve_s else None,
-                                   "method": f"FP64 step time over {fp64_probe} steps x steps the served solve took",
-                                   "fp32_vs_fp64_rel_l2_at_equal_steps": worst}}
+            "by_diameter": by_d, "rebuilds": stats["rebuilds"], "node_steps": stats["node_steps"],
+            "MLUPS": stats["node_steps"] / elapsed / 1e6, "fp64_one_at_a_time": fp64}
 
 
 def main():

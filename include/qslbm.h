@@ -353,13 +353,17 @@ int qslbm_batch_destroy(qslbm_batch* b);
  * A request loop with continuous batching.  Requests (a problem and a stop
  * tolerance on the steady residual) may be submitted from any thread; each
  * qslbm_server_run admits queued requests whose device memory fits the
- * budget, advances every running request by chunk_steps flow steps in the
- * batched launches, and retires requests whose FP64 steady residual fell below
- * their tolerance (status QSLBM_OK), that reached max_steps (QSLBM_ETIMEOUT),
- * or whose fields went non-finite (QSLBM_EUNSTABLE).  A request larger than
- * the whole budget finishes at once with QSLBM_EBUDGET.  Times are seconds on
- * the server's monotonic clock. */
+ * budget (in arrival order, or smallest first), advances every running
+ * request by chunk_steps flow steps in the batched launches, and retires
+ * requests whose FP64 steady residual fell below their tolerance (status
+ * QSLBM_OK), that reached max_steps (QSLBM_ETIMEOUT), or whose fields went
+ * non-finite (QSLBM_EUNSTABLE).  A request larger than the whole budget
+ * finishes at once with QSLBM_EBUDGET.  Times are seconds on the server's
+ * monotonic clock. */
 typedef struct qslbm_server qslbm_server;
+
+#define QSLBM_ADMIT_FIFO 0     /* queued requests in arrival order (first fit)          */
+#define QSLBM_ADMIT_SMALLEST 1 /* fewest nodes first (ties in arrival order), first fit */
 
 typedef struct qslbm_server_config {
     int64_t hbm_budget_bytes; /* device memory the running requests may hold  */
@@ -367,6 +371,7 @@ typedef struct qslbm_server_config {
     int32_t max_running;      /* 0 = limited by the budget only                */
     int32_t precision;        /* QSLBM_FP32 | QSLBM_FP64 for every request     */
     void* stream;             /* cudaStream_t or NULL (the server creates one) */
+    int32_t admit;            /* QSLBM_ADMIT_FIFO (0) | QSLBM_ADMIT_SMALLEST   */
 } qslbm_server_config;
 
 typedef struct qslbm_result {

@@ -68,7 +68,10 @@ class qslbm_batch_info_t(C.Structure):
 
 class qslbm_server_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("chunk_steps", C.c_int32), ("max_running", C.c_int32),
-                ("precision", C.c_int32), ("stream", C.c_void_p)]
+                ("precision", C.c_int32), ("stream", C.c_void_p), ("admit", C.c_int32)]
+
+
+ADMIT = {"fifo": 0, "smallest": 1}
 
 
 class qslbm_result(C.Structure):
@@ -361,10 +364,10 @@ class Server:
     """Continuous-batching request loop of the library (qslbm_server_*)."""
 
     def __init__(self, hbm_budget_bytes: int, chunk_steps: int = 100, max_running: int = 0,
-                 precision: str = "fp32", stream: int | None = None):
+                 precision: str = "fp32", stream: int | None = None, admit: str = "fifo"):
         self.L = load()
         cfg = qslbm_server_config(int(hbm_budget_bytes), int(chunk_steps), int(max_running),
-                                  PRECISION[precision], stream)
+                                  PRECISION[precision], stream, ADMIT[admit])
         h = C.c_void_p()
         check(self.L.qslbm_server_create(C.byref(cfg), C.byref(h)), "qslbm_server_create")
         self.h = h

@@ -1031,6 +1031,10 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
     // admission (first fit under the budget)
     {
         std::lock_guard<std::mutex> lock(S.mu);
+        if (S.cfg.admit == QSLBM_ADMIT_SMALLEST)
+            std::stable_sort(S.pending.begin(), S.pending.end(), [](const Request& a, const Request& b) {
+                return estimate_bytes(a.p) < estimate_bytes(b.p);
+            });
         for (auto it = S.pending.begin(); it != S.pending.end();) {
             if (S.cfg.max_running > 0 && (int)S.running.size() >= S.cfg.max_running) break;
             const long long est = estimate_bytes(it->p);
@@ -1143,6 +1147,7 @@ extern "C" {
 int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out) {
     if (!cfg || !out || cfg->chunk_steps <= 0 || cfg->hbm_budget_bytes <= 0) return QSLBM_EINVAL;
     if (cfg->precision != QSLBM_FP32 && cfg->precision != QSLBM_FP64) return QSLBM_EINVAL;
+    if (cfg->admit != QSLBM_ADMIT_FIFO && cfg->admit != QSLBM_ADMIT_SMALLEST) return QSLBM_EINVAL;
     *out = nullptr;
     qslbm_server* S = new (std::nothrow) qslbm_server();
     if (!S) return QSLBM_ENOMEM;

@@ -82,3 +82,44 @@ def test_budget_admission_and_caps():
     assert seen[a]["status"] == EBUDGET
     assert seen[b]["status"] == ETIMEOUT and seen[b]["steps"] == 40
     assert seen[c]["status"] == ETIMEOUT and seen[c]["t_admit"] >= seen[b]["t_done"] - 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_served_result_matches_oracle(precision, tol):
+    # a request served in a mix, stopped by its step cap after 3 flow steps,
+    # against the oracle at the same step
+    import oracle
+
+    # (the oracle starts from rest with the seeded perturbation)
+    reqs = [dict(p, init_kind="rest", perturb=0.01) for p in requests()]
+    with Server(8 * GB, chunk_steps=3, precision=precision) as S:
+        ids = [S.submit(dict(p, precision=precision), tol=1e-30, max_steps=3, keep_fields=True) for p in reqs[:3]]
+        res = {}
+        for _ in range(5):
+            S.run()
+            for r in S.poll():
+                res[r["id"]] = r
+            if len(res) == len(ids):
+                break
+        rho, u, b = S.fields(ids[2])
+    assert all(r["status"] == ETIMEOUT and r["steps"] == 3 for r in res.values())
+    o = oracle.Oracle(dict(reqs[2], precision="fp64"))
+    o.step(3)
+    orho, ou, ob = o.state()
+    assert rel(u, ou) <= tol and rel(b, ob) <= tol, (rel(u, ou), rel(b, ob))
+
+
+def test_smallest_first_admission():
+    reqs = requests()
+    big = W.small_pipe(nx=40, ny=40, nz=40, diameter=30.0, perturb=0.0, init_kind="poiseuille", seed=9)
+    with Server(8 * GB, chunk_steps=5, max_running=1, admit="smallest") as S:
+        a = S.submit(big, tol=1e-30, max_steps=5)
+        b = S.submit(reqs[2], tol=1e-30, max_steps=5)  # 16 x 18 x 20: the smallest
+        seen = {}
+        for _ in range(10):
+            S.run()
+            for r in S.poll():
+                seen[r["id"]] = r
+            if len(seen) == 2:
+                break
+    assert seen[b]["t_done"] <= seen[a]["t_admit"] + 1e-9
