@@ -153,13 +153,14 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the roofline kernel from the committed ncu
-    summary (profiles/traffic.json), or None when the kernel sources changed
-    since that capture."""
+def profiled_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of the roofline kernel (`kernel`: the handle's
+    sweep route) from the committed ncu summary (profiles/traffic.json), or
+    None when there is none for that route or the kernel sources changed since
+    that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            d = json.load(f)[workload]
+            d = json.load(f)[f"{workload}:{kernel}"]
         if d.get("kernel_source_sha") != kernel_source_sha():
             return None
         return float(d["dram_bytes_per_launch"])
@@ -204,7 +205,7 @@ def roofline_block(solver, p, workload, sweep_ms, peak, peak_kind):
     l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
     bound = "hbm" if (k != "resident" and fields_bytes > l2) else "l2_resident"
     return {"bound": "hbm" if bound == "hbm" else "l2", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(workload), "kernel": name,
+            "frac": achieved / peak, "traffic": profiled_traffic(workload, k), "kernel": name,
             "workload": workload, "bytes_per_launch": alg_bytes, "ms_per_launch": launch_ms,
             "sweeps_per_launch": per_launch, "us_per_sweep": sweep_ms * 1e3,
             "peak_kind": f"{peak_kind} (hbm_gbs)",
@@ -213,7 +214,7 @@ def roofline_block(solver, p, workload, sweep_ms, peak, peak_kind):
                      "(effective bandwidth), not DRAM traffic")}
 
 
-def run_hbm_workload(stream, flush, peak, peak_kind, steps: int = 10, warmup: int = 3):
+def run_hbm_workload(stream, flush, peak, peak_kind, steps: int = 10, warmup: int = 3, sweep_kernel: str = "auto"):
     """The 96x96x512 ramped pipe (fields above L2): MLUPS over `steps` flow
     steps and the roofline of its sweep kernel, CUDA events on `stream`."""
     import torch
@@ -222,6 +223,8 @@ def run_hbm_workload(stream, flush, peak, peak_kind, steps: int = 10, warmup: in
 
     name, make = WORKLOADS["ramp96"]
     p = make(0)
+    if sweep_kernel != "auto":
+        p = dict(p, sweep_kernel=sweep_kernel)
     s = _lib.Solver(p, stream=stream.cuda_stream)
     n_mag = s.units["n_mag"]
     for _ in range(warmup):
@@ -444,6 +447,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--workload", default="pipe64", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "resident", "split", "fused", "planes"],
+                    help="magnetic sweep route (auto: the library's choice; profiles pin the route it took)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -466,6 +471,8 @@ def main():
     torch.cuda.set_stream(stream)
     workload_name, make = WORKLOADS[args.workload]
     p = make(rank)
+    if args.sweep_kernel != "auto":
+        p = dict(p, sweep_kernel=args.sweep_kernel)
     solver = _lib.Solver(p, stream=stream.cuda_stream)
     n = solver.n
     n_mag = solver.units["n_mag"]
@@ -555,7 +562,8 @@ def main():
         # the pipe whose fields exceed L2 (the workload the HBM target is set on)
         result["roofline_l2_resident"] = headline_roof
         if rank == 0:
-            hbm = run_hbm_workload(stream, flush, peak, peak_kind)
+            hbm = run_hbm_workload(stream, flush, peak, peak_kind,
+                                   sweep_kernel=args.sweep_kernel if args.sweep_kernel != "resident" else "auto")
             result["roofline"] = hbm.pop("roofline")
             result["hbm_workload"] = hbm
     if rank == 0 and not args.no_extras:
