@@ -506,12 +506,12 @@ def test_kernel_selection_reported():
     with Solver(W.pipe_64x64x128(nz=16, sweep_kernel="planes")) as s:
         assert s.units["sweep_kernel"] == "planes"
     # 96 x 96 planes exceed the resident kernel's 8192-node plane limit: in
-    # FP32 AUTO times the fused kernel and the split path and keeps the faster,
-    # in FP64 it takes the split path
+    # FP32 AUTO times the fused kernel and the split path and keeps the fused
+    # kernel only when it is at least 2 % faster; in FP64 it takes the split path
     with Solver(W.pipe_ramp_96x96x512(nz=8)) as s:
         u = s.units
         assert u["sweep_us_fused"] > 0 and u["sweep_us_split"] > 0
-        assert u["sweep_kernel"] == ("fused" if u["sweep_us_fused"] <= u["sweep_us_split"] else "split")
+        assert u["sweep_kernel"] == ("fused" if u["sweep_us_fused"] < 0.98 * u["sweep_us_split"] else "split")
     with Solver(W.pipe_ramp_96x96x512(nz=8, precision="fp64")) as s:
         assert s.units["sweep_kernel"] == "split" and s.units["sweep_us_fused"] == 0
     with pytest.raises(QSLBMError):
