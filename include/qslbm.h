@@ -75,9 +75,10 @@ extern "C" {
  * memory (the band's rows are staged by the tensor memory accelerator with
  * three halo rows on each side); FP32, 3-D, nx a multiple of 4 up to 256, the
  * same wall ring on every plane; create fails with QSLBM_EINVAL otherwise.
- * AUTO picks RESIDENT when it fits; else, when FUSED applies, it times one
- * sweep of FUSED and one of SPLIT on the handle's fields at creation and keeps
- * the faster (the two give bitwise equal results); else SPLIT. */
+ * AUTO picks RESIDENT when it fits; else, when FUSED applies, it times FUSED
+ * and SPLIT on the handle's fields at creation (without changing them) and
+ * keeps FUSED only when it is at least 2 % faster (the two give bitwise equal
+ * results); else SPLIT. */
 /* Initial velocity: rest (plus the seeded noise), or the Ha = 0 profile
  * U0 (1 - r^2/R^2) along the axis inside the wall (plus the noise). */
 #define QSLBM_INIT_REST 0
@@ -310,18 +311,22 @@ int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_
  *    first while their groups fit co-resident on the device;
  *  - marching: every other instance (and any created with sweep_kernel =
  *    QSLBM_SWEEP_SPLIT) takes one persistent z-marching launch per sweep over
- *    the instances with N_mag > s, then one IB launch; the sweep's persistent
- *    grid is chosen by timing candidates on the batch at creation.
+ *    the instances with N_mag > s, then one IB launch; the sweep's tile shape
+ *    and persistent grid are chosen by timing candidates on the batch when it
+ *    is first built with such a member.
  * Each instance follows the same arithmetic as a handle created alone with
  * QSLBM_SWEEP_SPLIT (the same expressions in the same order). */
 typedef struct qslbm_batch qslbm_batch;
 
 typedef struct qslbm_batch_info_t {
     int32_t count, max_n_mag;
-    int32_t sweep_threads, sweep_grid;  /* tuned launch; grid 0 = one block per work item */
+    int32_t sweep_threads, sweep_grid;  /* tuned marching launch: threads = 32 x the tile's rows
+                                           (4, 8 or 16); grid 0 = one block per work item  */
     int32_t launches_per_step;
     int64_t nodes, node_sweeps_per_step, device_bytes, steps;
-    double tune_us[8];                  /* microseconds per sweep of each candidate tried  */
+    double tune_us[16];                 /* microseconds per sweep of each candidate tried, in
+                                           the order rows 4, 8, 16 x grid 1, 2, 4, 8 CTAs
+                                           per SM, one per item (0 when not timed)          */
     int32_t resident_instances;         /* members whose sweeps run in the resident group kernel */
     int32_t resident_groups;            /* its CTAs (groups of whole planes)               */
     int32_t graph_steps;                /* flow steps per captured graph chunk             */

@@ -64,24 +64,25 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ first, int k, i
 // Persistent z-marching sweep over every active instance's tiles: work item w
 // is (instance, tile x, tile y, z chunk of `chunk` planes) in the prefix table
 // `first`.
-// XY: some instance has an in-plane applied field (QSLBM_B0_FIELD)
-template <typename T, bool XY>
-__global__ void __launch_bounds__(kMarchTX* kMarchTY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
-                                                                    const int* __restrict__ first, int kact, int s,
-                                                                    int chunk) {
-    __shared__ MarchTile<T> tile;
+// XY: some instance has an in-plane applied field (QSLBM_B0_FIELD); TY: rows
+// of the tile (the autotuner's choice; results do not depend on it).
+template <typename T, bool XY, int TY>
+__global__ void __launch_bounds__(kMarchTX* TY) k_batch_sweep(const InstDesc<T>* __restrict__ d,
+                                                              const int* __restrict__ first, int kact, int s,
+                                                              int chunk) {
+    __shared__ MarchTile<T, TY> tile;
     const int total = first[kact];
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int i = find_inst(first, kact, w);
         const InstDesc<T>& D = d[i];
         const int local = w - first[i];
         const int tiles_x = (D.g.nx + kMarchTX - 1) / kMarchTX;
-        const int tiles_y = (D.g.ny + kMarchTY - 1) / kMarchTY;
+        const int tiles_y = (D.g.ny + TY - 1) / TY;
         const int bz = local / (tiles_x * tiles_y);
         const int r = local - bz * tiles_x * tiles_y;
         const int by = r / tiles_x, bx = r - by * tiles_x;
         const int par = (D.bpar + s) & 1;
-        march_tile<T, XY>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, chunk, tile);
+        march_tile<T, XY, TY>(D.g, D.b[par], D.b[par ^ 1], D.u[D.fpar], D.sc, bx, by, bz, chunk, tile);
         __syncthreads();
     }
 }
@@ -326,11 +327,17 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int total = B.h_first[kact];
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
-    (void)threads;
-    if (B.has_field)
-        qslbm::k_batch_sweep<T, true><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
-    else
-        qslbm::k_batch_sweep<T, false><<<g, qslbm::kMarchTX * qslbm::kMarchTY, 0, st>>>(d, B.first, kact, s, B.chunk);
+    // threads = kMarchTX x the tile's rows (4, 8 or 16)
+    auto run = [&](auto kernel) { kernel<<<g, threads, 0, st>>>(d, B.first, kact, s, B.chunk); };
+    if (B.has_field) {
+        if (threads == qslbm::kMarchTX * 4) run(qslbm::k_batch_sweep<T, true, 4>);
+        else if (threads == qslbm::kMarchTX * 16) run(qslbm::k_batch_sweep<T, true, 16>);
+        else run(qslbm::k_batch_sweep<T, true, 8>);
+    } else {
+        if (threads == qslbm::kMarchTX * 4) run(qslbm::k_batch_sweep<T, false, 4>);
+        else if (threads == qslbm::kMarchTX * 16) run(qslbm::k_batch_sweep<T, false, 16>);
+        else run(qslbm::k_batch_sweep<T, false, 8>);
+    }
     const int nm = B.h_mfirst[kact], ns = B.h_sfirst[kact];
     if (nm > 0 && B.ib_staged_smem > 0) {
         const int np = B.h_pfirst[kact], R = B.max_ring, S = B.max_shell;
@@ -467,9 +474,11 @@ int build_groups(qslbm_batch& B) {
     return QSLBM_OK;
 }
 
-// The node-block layout depends on the sweep block size (nodes per block).
+// The work list depends on the sweep's tile: kMarchTX x (threads / kMarchTX)
+// columns per item.
 template <typename T>
 int build_tables(qslbm_batch& B, int threads) {
+    const int TY = threads / qslbm::kMarchTX;
     const int K = (int)B.members.size();
     std::vector<qslbm::InstDesc<T>> h(K);
     B.h_first.assign(K + 1, 0);
@@ -489,8 +498,8 @@ int build_tables(qslbm_batch& B, int threads) {
             long long w = 0;
             for (int k = 0; k < B.kmarch; ++k) {
                 const State& s = qslbm::handle_state_mut(B.members[k]);
-                w += (long long)((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
-                     ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) * ((s.nz + chunk - 1) / chunk);
+                w += (long long)((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) * ((s.ny + TY - 1) / TY) *
+                     ((s.nz + chunk - 1) / chunk);
             }
             return w;
         };
@@ -503,8 +512,7 @@ int build_tables(qslbm_batch& B, int threads) {
         const State& s = qslbm::handle_state_mut(B.members[k]);
         h[k] = make_desc<T>(s);
         if (s.bext_xy) B.has_field = true;
-        const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) *
-                          ((s.ny + qslbm::kMarchTY - 1) / qslbm::kMarchTY) *
+        const int tiles = ((s.nx + qslbm::kMarchTX - 1) / qslbm::kMarchTX) * ((s.ny + TY - 1) / TY) *
                           ((s.nz + B.chunk - 1) / B.chunk);
         h[k].bpp = tiles;
         B.h_first[k + 1] = B.h_first[k] + tiles;
@@ -568,9 +576,10 @@ int build_tables(qslbm_batch& B, int threads) {
 }
 
 // Autotuner: time the first sweep of the batch for each (block size, grid)
-// candidate on the real instances and keep the fastest.  The sweeps run on a
-// copy of the state that is restored afterwards, so tuning does not advance
-// the solution.
+// candidate on the real instances and keep the fastest: the marching tile's
+// rows (4, 8 or 16, i.e. 128, 256 or 512 threads) and the persistent grid (1,
+// 2, 4 or 8 CTAs per SM, or one CTA per work item).  The sweeps do not advance
+// the solution (below).
 template <typename T>
 int autotune(qslbm_batch& B) {
     int dev = 0, sms = 0;
@@ -580,7 +589,8 @@ int autotune(qslbm_batch& B) {
         int threads, grid;
     };
     std::vector<Cand> cands;
-    for (int per_sm : {1, 2, 4, 8, 0}) cands.push_back({qslbm::kMarchTX * qslbm::kMarchTY, per_sm ? per_sm * sms : 0});
+    for (int ty : {4, 8, 16})
+        for (int per_sm : {1, 2, 4, 8, 0}) cands.push_back({qslbm::kMarchTX * ty, per_sm ? per_sm * sms : 0});
     // the tuning sweeps write b[other parity]; they read b[current] and u only,
     // so the state the batch starts from is untouched
     cudaEvent_t e0, e1;
@@ -817,7 +827,7 @@ int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs, const std:
         B->active[s] = a;
     }
     int rc;
-    if (!B->tuned) {
+    if (!B->tuned && B->kmarch > 0) {  // (no marching member: nothing to time yet)
         rc = B->precision == QSLBM_FP64 ? autotune<double>(*B) : autotune<float>(*B);
         B->tuned = true;
     } else {
@@ -930,7 +940,7 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
     info->graph_steps = B->chunk_steps;
     info->march_chunk = B->chunk;
     info->steps = B->steps;
-    for (size_t c = 0; c < B->tune_us.size() && c < 8; ++c) info->tune_us[c] = B->tune_us[c];
+    for (size_t c = 0; c < B->tune_us.size() && c < 16; ++c) info->tune_us[c] = B->tune_us[c];
     return QSLBM_OK;
 }
 

@@ -293,11 +293,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_sweep_nodes(Geo g, const T* __
 // from the tile of plane z staged in shared memory.
 constexpr int kMarchTX = 32, kMarchTY = 8, kMarchChunk = 16;
 
-// Halo cell of a march tile handled by thread hid: the ring of
-// (kMarchTX + 2) x (kMarchTY + 2) tile cells around the interior.  hp is the
+// Halo cell of a march tile of TY rows handled by thread hid: the ring of
+// (kMarchTX + 2) x (TY + 2) tile cells around the interior.  hp is the
 // in-plane index of the node it stages (periodic image), -1 for no cell.
+template <int TY = kMarchTY>
 __device__ __forceinline__ void march_halo(int hid, int x0, int y0, int nx, int ny, int& hx, int& hy, int& hp) {
-    constexpr int W = kMarchTX + 2, H = kMarchTY + 2, NH = 2 * W + 2 * kMarchTY;
+    constexpr int W = kMarchTX + 2, H = TY + 2, NH = 2 * W + 2 * TY;
     hx = 0;
     hy = 0;
     hp = -1;
@@ -343,10 +344,10 @@ __device__ __forceinline__ float emf_update(float w0, float w1, float w1k, float
     return __fmaf_rn(w0, b, __fmaf_rn(w1k, d, __fmul_rn(w1, s)));
 }
 
-// Shared tile of one march plane: six fields of (kMarchTY + 2) x (kMarchTX + 2)
+// Shared tile of one march plane: six fields of (TY + 2) x (kMarchTX + 2)
 // cells, the tile and its one-cell halo.
-template <typename T>
-using MarchTile = T[6][kMarchTY + 2][kMarchTX + 2];
+template <typename T, int TY = kMarchTY>
+using MarchTile = T[6][TY + 2][kMarchTX + 2];
 
 // The sweep over one tile and z chunk, one node per thread.  FP32 (EMF form):
 // each node's (e1, e2, e3) is formed once, where its (b, u) is loaded, and the
@@ -356,15 +357,18 @@ using MarchTile = T[6][kMarchTY + 2][kMarchTX + 2];
 // every neighbour's flux is formed as in sweep_node, with the same
 // expressions and neighbour order, so that it rounds like the other FP64 sweep
 // kernels.  The column's plane z + 2 is loaded one plane ahead of its use.
-template <typename T, bool XY = true>
+// TY: rows of the tile (the CTA has kMarchTX * TY threads); the results do not
+// depend on it.
+template <typename T, bool XY = true, int TY = kMarchTY>
 __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ bin, T* __restrict__ bout,
                                            const T* __restrict__ u, const SweepCoef<T>& c, int bx, int by, int bz,
-                                           int chunk, MarchTile<T>& tile) {
+                                           int chunk, MarchTile<T, TY>& tile) {
+    static_assert(kMarchTX * TY >= 2 * (kMarchTX + 2) + 2 * TY, "every halo cell needs a thread");
     constexpr bool EMF = sizeof(T) == 4;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int n = (int)g.n, P = nx * ny;
     const int tx = threadIdx.x % kMarchTX, ty = threadIdx.x / kMarchTX;
-    const int x0 = bx * kMarchTX, y0 = by * kMarchTY;
+    const int x0 = bx * kMarchTX, y0 = by * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
     // columns past the domain edge stage the periodic images their neighbours need
@@ -374,7 +378,7 @@ __device__ __forceinline__ void march_tile(const Geo& g, const T* __restrict__ b
     const int z1 = min(z0 + chunk, nz);
     const T* src[6] = {bin, bin + n, bin + 2 * n, u, u + n, u + 2 * n};
     int hx, hy, hp;
-    march_halo(threadIdx.x, x0, y0, nx, ny, hx, hy, hp);
+    march_halo<TY>(threadIdx.x, x0, y0, nx, ny, hx, hy, hp);
     // prv / cur / nxt: the column at z - 1, z, z + 1 ((b, e) or (b, u)); ahd:
     // raw (b, u) of plane z + 2
     T prv[6], cur[6], nxt[6], ahd[6];

@@ -45,7 +45,7 @@ def test_batch_members_match_single_instances(precision):
     with Batch(ps) as B:
         info = B.info()
         assert info["count"] == len(ps) and info["max_n_mag"] == 270
-        assert info["sweep_threads"] == 256
+        assert info["sweep_threads"] in (128, 256, 512)
         B.step(steps)
         got = [B.member(i).state() for i in range(len(ps))]
     for i, p in enumerate(ps):
