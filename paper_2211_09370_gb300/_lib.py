@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes as C
 import math
 import os
+import threading
 
 import numpy as np
 
@@ -372,13 +373,18 @@ class Server:
         check(self.L.qslbm_server_create(C.byref(cfg), C.byref(h)), "qslbm_server_create")
         self.h = h
         self.params = {}
+        # a result can be ready as soon as its request is queued (a request
+        # above the budget is answered at once): submit records the request's
+        # parameters before poll may return its result
+        self._lock = threading.Lock()
 
     def submit(self, params: dict, tol: float = 1e-6, max_steps: int = 100000, keep_fields: bool = False) -> int:
         q = make_params(params)
         rid = C.c_int64()
-        check(self.L.qslbm_server_submit(self.h, C.byref(q), float(tol), int(max_steps), int(keep_fields),
-                                         C.byref(rid)), "qslbm_server_submit")
-        self.params[rid.value] = dict(params)
+        with self._lock:
+            check(self.L.qslbm_server_submit(self.h, C.byref(q), float(tol), int(max_steps), int(keep_fields),
+                                             C.byref(rid)), "qslbm_server_submit")
+            self.params[rid.value] = dict(params)
         return rid.value
 
     def run(self):
@@ -389,7 +395,8 @@ class Server:
     def poll(self, max_results: int = 1024):
         arr = (qslbm_result * max_results)()
         n = C.c_int32()
-        check(self.L.qslbm_server_poll(self.h, arr, int(max_results), C.byref(n)), "qslbm_server_poll")
+        with self._lock:
+            check(self.L.qslbm_server_poll(self.h, arr, int(max_results), C.byref(n)), "qslbm_server_poll")
         out = []
         for r in arr[: n.value]:
             d = {k: getattr(r, k) for k in ("id", "status", "steps", "nodes", "residual", "t_submit", "t_admit",
