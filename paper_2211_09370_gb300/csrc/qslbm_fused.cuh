@@ -221,16 +221,10 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    // planes z0 - 1 .. z1 are needed (relative index j: plane z0 - 1 + j, in
-    // slot j % NS, completing phase (j / NS) & 1 of that slot's mbarrier)
-    // the warp that issues the copies: one in the middle, away from the
-    // interpolation (first threads) and the spread (last threads)
-    const int warp = tid >> 5, lane = tid & 31, copy_warp = (nthr >> 5) / 2;
-    if (warp == copy_warp)
-        for (int j = 0; j < NS && j <= L + 1; ++j)
-            fused_load_plane(&tm_b3, &tm_bt, &tm_u3, &tm_ut, slot_of(j), lay, zwrap(z0 - 1 + j), yA, y0, yB,
-                             &bars[j % NS], lane);
+    // the next sweep may be scheduled as these CTAs exit; the band's IB
+    // tables (constant) are read while the previous sweep finishes, b only
+    // after it has
+    pdl_trigger();
     // the band's IB tables, once
     const int Mr = ib.mk_cnt[band], Sr = ib.sh_cnt[band];
     for (int e = tid; e < 9 * Mr; e += nthr) {
@@ -246,6 +240,17 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         t_sm[e] = ib.sh_m[(size_t)band * Sm * K + e];
         t_sw[e] = ib.sh_w[(size_t)band * Sm * K + e];
     }
+    pdl_wait();
+    __syncthreads();
+    // planes z0 - 1 .. z1 are needed (relative index j: plane z0 - 1 + j, in
+    // slot j % NS, completing phase (j / NS) & 1 of that slot's mbarrier)
+    // the warp that issues the copies: one in the middle, away from the
+    // interpolation (first threads) and the spread (last threads)
+    const int warp = tid >> 5, lane = tid & 31, copy_warp = (nthr >> 5) / 2;
+    if (warp == copy_warp)
+        for (int j = 0; j < NS && j <= L + 1; ++j)
+            fused_load_plane(&tm_b3, &tm_bt, &tm_u3, &tm_ut, slot_of(j), lay, zwrap(z0 - 1 + j), yA, y0, yB,
+                             &bars[j % NS], lane);
 
     // this thread's pair: swept row r (staged row r + 1), columns x, x + 1
     const int r = owner ? tid / half : 0;

@@ -32,6 +32,17 @@ namespace qslbm {
 
 constexpr int kPlaneThreads = 512;
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may start while the previous kernel in
+// its stream is still running, once every CTA of that kernel has called
+// pdl_trigger (or exited); pdl_wait then blocks until the previous kernel has
+// completed and its memory is visible.  Every read of data another kernel
+// writes, and every global write, comes after pdl_wait; only reads of
+// constant tables may come before it.  Both are no-ops in a kernel launched
+// without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 struct Geo {
     int nx, ny, nz;
     long long n;  // nx * ny * nz
@@ -612,6 +623,10 @@ __global__ void __launch_bounds__(kPairThreads) k_sweep_march_pair(Geo g, const 
         }
     };
     float2 prv[6], cur[6], nxt[6], ahd[6], hcur[6], hnxt[6];
+    // the IB pass after this sweep may be scheduled as this grid's CTAs exit;
+    // b comes from the kernel before this one
+    pdl_trigger();
+    pdl_wait();
     {
         const int zm = wrap_dec(z0, nz), zn = wrap_inc(z0, nz);
 #pragma unroll
@@ -817,7 +832,14 @@ __device__ __forceinline__ void ib_staged_plane(const IBView<T>& ib, T* f, int n
     T* f1 = f0 + n;
     T* f2 = f1 + n;
     const int tid = threadIdx.x;
-    // (A) shell values (in-plane index, then the value) and marker tables
+    // (A) the markers' tables (constant: read before the wait for the
+    // sweep that wrote f), then the shell values (in-plane index, then value)
+    for (int e = tid; e < 9 * R; e += THREADS) {
+        tw[e] = __ldg(ib.mk_w + 9 * m0 + e);
+        tslot[e] = __ldg(ib.mk_slot + 9 * m0 + e);
+    }
+    for (int m = tid; m < R; m += THREADS) tsc[m] = __ldg(ib.mk_s + m0 + m);
+    pdl_wait();
     for (int i0 = 0; i0 < S; i0 += U * THREADS) {
         int q[U];
 #pragma unroll
@@ -844,11 +866,6 @@ __device__ __forceinline__ void ib_staged_plane(const IBView<T>& ib, T* f, int n
             }
         }
     }
-    for (int e = tid; e < 9 * R; e += THREADS) {
-        tw[e] = __ldg(ib.mk_w + 9 * m0 + e);
-        tslot[e] = __ldg(ib.mk_slot + 9 * m0 + e);
-    }
-    for (int m = tid; m < R; m += THREADS) tsc[m] = __ldg(ib.mk_s + m0 + m);
     __syncthreads();
     // (B) delta_j = -s_j D f* at every marker
     for (int m = tid; m < R; m += THREADS) {
@@ -918,6 +935,7 @@ __global__ void __launch_bounds__(kNodeThreads, (kIbStagedMinBlocks<T, U>))
     k_ib_staged(Geo g, T* f, IBView<T> ib, int max_ring, int max_shell) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z = blockIdx.x;
+    pdl_trigger();  // the next sweep may be scheduled as these CTAs exit
     ib_staged_plane<T, kNodeThreads, U>(ib, f, (int)g.n, z * g.nx * g.ny, ib.zinv ? 0 : z, max_ring, max_shell,
                                      smem_raw);
 }

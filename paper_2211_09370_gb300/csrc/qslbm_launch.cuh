@@ -40,6 +40,25 @@ struct Launch {
         return v;
     }
 
+    // A launch that may begin while the previous kernel in the stream finishes
+    // (programmatic dependent launch; the kernel calls pdl_wait before it
+    // touches that kernel's results).
+    template <typename... KArgs, typename... Args>
+    static void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args... args) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, kernel, args...);  // errors surface at the next synchronising call
+    }
+
     static size_t ib_smem(const State& s) { return (size_t)3 * (s.ib.max_ring > 0 ? s.ib.max_ring : 1) * sizeof(T); }
 
     static int grid_for(long long n, int threads) {
@@ -93,11 +112,11 @@ struct Launch {
                     const dim3 pgrid((unsigned)((s.nx + 2 * kPairTXP - 1) / (2 * kPairTXP)),
                                      (unsigned)((s.ny + kPairTY - 1) / kPairTY), (unsigned)((s.nz + chunk - 1) / chunk));
                     if (s.bext_xy)
-                        k_sweep_march_pair<float, true><<<pgrid, kPairThreads, 0, st>>>(
-                            geo(s), (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
+                        launch_pdl(k_sweep_march_pair<float, true>, pgrid, dim3(kPairThreads), 0, st, geo(s),
+                                   (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
                     else
-                        k_sweep_march_pair<float, false><<<pgrid, kPairThreads, 0, st>>>(
-                            geo(s), (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
+                        launch_pdl(k_sweep_march_pair<float, false>, pgrid, dim3(kPairThreads), 0, st, geo(s),
+                                   (const float*)bin, (float*)bout, (const float*)u, fcoef(c), chunk);
                 } else if (s.dim == 3)
                 {
                     if (s.bext_xy)
@@ -110,10 +129,11 @@ struct Launch {
                 if (s.ib.nm > 0 && s.ib_staged_smem > 0) {
                     const int R = s.ib.max_ring, S = s.ib.max_shell;
                     const size_t sm = s.ib_staged_smem;
+                    const dim3 ig((unsigned)s.nz), ib(kNodeThreads);
                     switch (s.ib_staged_u) {
-                        case 1: k_ib_staged<T, 1><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
-                        case 2: k_ib_staged<T, 2><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
-                        default: k_ib_staged<T, 5><<<s.nz, kNodeThreads, sm, st>>>(geo(s), bout, v, R, S); break;
+                        case 1: launch_pdl(k_ib_staged<T, 1>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
+                        case 2: launch_pdl(k_ib_staged<T, 2>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
+                        default: launch_pdl(k_ib_staged<T, 5>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
                     }
                 } else if (s.ib.nm > 0) {
                     k_ib_markers<T><<<(s.ib.nm + kNodeThreads - 1) / kNodeThreads, kNodeThreads, 0, st>>>(geo(s), bout, v);
@@ -198,9 +218,8 @@ struct Launch {
             const dim3 grid((unsigned)s.fu_bands, (unsigned)s.fu_chunks);
             const FusedGeo g{s.nx, s.ny, s.nz, s.fu_TY, s.fu_chunk, (int)s.n, s.fu_slots};
             const int bc = s.bcur, fc = s.fcur;
-            fused_kernel(s)<<<grid, s.fu_threads, s.fu_smem, st>>>(s.fu_map_b3[bc], s.fu_map_bt[bc], s.fu_map_u3[fc],
-                                                                    s.fu_map_ut[fc], (float*)s.b[1 - bc], c,
-                                                                    fused_ib(s), g, s.fu_err);
+            launch_pdl(fused_kernel(s), grid, dim3(s.fu_threads), s.fu_smem, st, s.fu_map_b3[bc], s.fu_map_bt[bc],
+                       s.fu_map_u3[fc], s.fu_map_ut[fc], (float*)s.b[1 - bc], c, fused_ib(s), g, s.fu_err);
         } else {
             s.launch_error = true;  // never planned: the fused sweep is the FP32 path
         }
