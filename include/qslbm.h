@@ -324,13 +324,16 @@ typedef struct qslbm_batch_info_t {
                                            (4, 8 or 16); grid 0 = one block per work item  */
     int32_t launches_per_step;
     int64_t nodes, node_sweeps_per_step, device_bytes, steps;
-    double tune_us[16];                 /* microseconds per sweep of each candidate tried, in
-                                           the order rows 4, 8, 16 x grid 1, 2, 4, 8 CTAs
-                                           per SM, one per item (0 when not timed)          */
+    double tune_us[32];                 /* microseconds per sweep of each candidate tried, in
+                                           the order ordinary / programmatic launches x rows
+                                           4, 8, 16 x grid 1, 2, 4, 8 CTAs per SM, one per
+                                           item (0 when not timed)                          */
     int32_t resident_instances;         /* members whose sweeps run in the resident group kernel */
     int32_t resident_groups;            /* its CTAs (groups of whole planes)               */
     int32_t graph_steps;                /* flow steps per captured graph chunk             */
     int32_t march_chunk;                /* z planes per work item of the marching sweep    */
+    int32_t sweep_pdl;                  /* 1: the marching sweep and its IB pass are launched
+                                           with programmatic stream serialization           */
 } qslbm_batch_info_t;
 
 /* Create count instances from params[0..count-1] (their stream fields are

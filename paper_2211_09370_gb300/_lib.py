@@ -63,8 +63,8 @@ class qslbm_batch_info_t(C.Structure):
     _fields_ = [("count", C.c_int32), ("max_n_mag", C.c_int32), ("sweep_threads", C.c_int32),
                 ("sweep_grid", C.c_int32), ("launches_per_step", C.c_int32), ("nodes", C.c_int64),
                 ("node_sweeps_per_step", C.c_int64), ("device_bytes", C.c_int64), ("steps", C.c_int64),
-                ("tune_us", C.c_double * 16), ("resident_instances", C.c_int32), ("resident_groups", C.c_int32),
-                ("graph_steps", C.c_int32), ("march_chunk", C.c_int32)]
+                ("tune_us", C.c_double * 32), ("resident_instances", C.c_int32), ("resident_groups", C.c_int32),
+                ("graph_steps", C.c_int32), ("march_chunk", C.c_int32), ("sweep_pdl", C.c_int32)]
 
 
 class qslbm_server_config(C.Structure):

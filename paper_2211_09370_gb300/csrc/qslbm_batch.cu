@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(kMarchTX* TY) k_batch_sweep(const InstDesc<T>*
                                                               const int* __restrict__ first, int kact, int s,
                                                               int chunk) {
     __shared__ MarchTile<T, TY> tile;
+    pdl_trigger();  // the IB pass may be scheduled as these CTAs exit
+    pdl_wait();     // b comes from the kernel before this one
     const int total = first[kact];
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int i = find_inst(first, kact, w);
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kNodeThreads, (kIbStagedMinBlocks<T, U>)) k_ba
                                                                   const int* __restrict__ pfirst, int kact, int s,
                                                                   int max_ring, int max_shell) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();  // the next sweep may be scheduled as these CTAs exit
     const int i = find_inst(pfirst, kact, blockIdx.x);
     const InstDesc<T>& D = d[i];
     const int z = blockIdx.x - pfirst[i];
@@ -221,6 +224,7 @@ struct qslbm_batch {
     int sms = 1;                // SMs of the device
     bool has_field = false;     // some member has an in-plane applied field
     int threads = 256, grid = 0;         // autotuned sweep launch
+    bool pdl = false;                    // autotuned: programmatic dependent launches of the marching route
     cudaGraphExec_t graph = nullptr;        // one flow step
     cudaGraphExec_t graph_chunk = nullptr;  // chunk_steps flow steps
     int chunk_steps = 1;
@@ -320,6 +324,24 @@ qslbm::InstDesc<T> make_desc(const State& s) {
     return D;
 }
 
+// A launch that may begin while the previous kernel in the stream finishes
+// (programmatic dependent launch; the kernel waits for that kernel's results).
+template <typename... KArgs, typename... Args>
+void launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);  // errors end the graph capture
+}
+
 template <typename T>
 void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st) {
     const int kact = B.active[s];
@@ -328,7 +350,9 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     const int g = grid > 0 ? std::min(grid, total) : total;
     const auto* d = (const qslbm::InstDesc<T>*)B.desc;
     // threads = kMarchTX x the tile's rows (4, 8 or 16)
-    auto run = [&](auto kernel) { kernel<<<g, threads, 0, st>>>(d, B.first, kact, s, B.chunk); };
+    auto run = [&](auto kernel) {
+        launch_pdl(B.pdl, kernel, dim3(g), dim3(threads), 0, st, d, (const int*)B.first, kact, s, B.chunk);
+    };
     if (B.has_field) {
         if (threads == qslbm::kMarchTX * 4) run(qslbm::k_batch_sweep<T, true, 4>);
         else if (threads == qslbm::kMarchTX * 16) run(qslbm::k_batch_sweep<T, true, 16>);
@@ -342,10 +366,12 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
     if (nm > 0 && B.ib_staged_smem > 0) {
         const int np = B.h_pfirst[kact], R = B.max_ring, S = B.max_shell;
         const size_t sm = B.ib_staged_smem;
+        const dim3 ig((unsigned)np), ib(qslbm::kNodeThreads);
+        const int* pf = B.pfirst;
         switch (qslbm::ib_staged_unroll(S, np, B.sms)) {
-            case 1: qslbm::k_batch_ib_staged<T, 1><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
-            case 2: qslbm::k_batch_ib_staged<T, 2><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
-            default: qslbm::k_batch_ib_staged<T, 5><<<np, qslbm::kNodeThreads, sm, st>>>(d, B.pfirst, kact, s, R, S); break;
+            case 1: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 1>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
+            case 2: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 2>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
+            default: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 5>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
         }
     } else if (nm > 0) {
         qslbm::k_batch_ib_markers<T><<<(nm + qslbm::kNodeThreads - 1) / qslbm::kNodeThreads, qslbm::kNodeThreads, 0,
@@ -587,10 +613,13 @@ int autotune(qslbm_batch& B) {
     BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     struct Cand {
         int threads, grid;
+        bool pdl;
     };
     std::vector<Cand> cands;
-    for (int ty : {4, 8, 16})
-        for (int per_sm : {1, 2, 4, 8, 0}) cands.push_back({qslbm::kMarchTX * ty, per_sm ? per_sm * sms : 0});
+    for (int pdl : {0, 1})
+        for (int ty : {4, 8, 16})
+            for (int per_sm : {1, 2, 4, 8, 0})
+                cands.push_back({qslbm::kMarchTX * ty, per_sm ? per_sm * sms : 0, pdl != 0});
     // the tuning sweeps write b[other parity]; they read b[current] and u only,
     // so the state the batch starts from is untouched
     cudaEvent_t e0, e1;
@@ -598,9 +627,11 @@ int autotune(qslbm_batch& B) {
     BCHK(cudaEventCreate(&e1));
     float best = 1e30f;
     B.tune_us.clear();
+    bool best_pdl = false;
     for (const Cand& c : cands) {
         int rc = build_tables<T>(B, c.threads);
         if (rc) return rc;
+        B.pdl = c.pdl;
         launch_sweep<T>(B, 0, c.threads, c.grid, B.stream);  // warm-up
         BCHK(cudaEventRecord(e0, B.stream));
         for (int r = 0; r < 3; ++r) launch_sweep<T>(B, 0, c.threads, c.grid, B.stream);
@@ -613,10 +644,12 @@ int autotune(qslbm_batch& B) {
             best = ms;
             B.threads = c.threads;
             B.grid = c.grid;
+            best_pdl = c.pdl;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    B.pdl = best_pdl;
     return build_tables<T>(B, B.threads);
 }
 
@@ -940,7 +973,8 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
     info->graph_steps = B->chunk_steps;
     info->march_chunk = B->chunk;
     info->steps = B->steps;
-    for (size_t c = 0; c < B->tune_us.size() && c < 16; ++c) info->tune_us[c] = B->tune_us[c];
+    for (size_t c = 0; c < B->tune_us.size() && c < 32; ++c) info->tune_us[c] = B->tune_us[c];
+    info->sweep_pdl = B->pdl ? 1 : 0;
     return QSLBM_OK;
 }
 
