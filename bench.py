@@ -335,14 +335,15 @@ def run_batched(steps: int = 3, count: int = 64):
 
 
 def run_serving(window_s: float = 30.0, time_cap_s: float = 120.0, rate: float = 20.0, tol: float = 1e-6,
-                max_steps: int = 20000, chunk: int = 200, max_running: int = 16, budget: int = 64 << 20,
+                max_steps: int = 20000, chunk: int = 200, max_running: int = 0, budget: int = 64 << 20,
                 fp64_cap_s: float = 150.0):
     """Serving at the stated request mix: Poisson arrivals (mean `rate` per
     second, seed 5) during the first `window_s` seconds of steady-state pipe
     solves with D in {16, 32, 48, 64, 96, 128}, box (D + 8)^2 x 6D, starting
     from the Poiseuille profile, stop at FP64 steady residual `tol` or
-    `max_steps`; FP32 fields, admitted smallest first under an HBM budget and
-    at most `max_running` at a time, advanced by continuous batching until
+    `max_steps`; FP32 fields, admitted smallest first under an HBM budget
+    (and `max_running`, 0 = no limit) while the running requests fit the
+    batch's resident group kernel, advanced by continuous batching until
     `time_cap_s`.  The stated arrivals bring about 10^3 times more work than
     one GPU can finish (a D = 128 solve alone needs ~10^6 steps of 14 M
     nodes), so the budget (64 MB) admits the pipes that can reach the residual

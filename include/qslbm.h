@@ -371,7 +371,11 @@ int qslbm_batch_destroy(qslbm_batch* b);
 typedef struct qslbm_server qslbm_server;
 
 #define QSLBM_ADMIT_FIFO 0     /* queued requests in arrival order (first fit)          */
-#define QSLBM_ADMIT_SMALLEST 1 /* fewest nodes first (ties in arrival order), first fit */
+#define QSLBM_ADMIT_SMALLEST 1 /* fewest nodes first (ties in arrival order), first fit;
+                                  in FP32, while any request runs, admission stops at the
+                                  first request that would not fit beside the running
+                                  ones in the batch's resident group kernel (so that the
+                                  running requests keep its one launch per step)       */
 
 typedef struct qslbm_server_config {
     int64_t hbm_budget_bytes; /* device memory the running requests may hold  */

@@ -245,6 +245,7 @@ struct qslbm_batch {
     long long xbuf_cap = 0;              // floats
     unsigned* gflags = nullptr;          // [groups_cap] sweep counters
     int* gerr = nullptr;                 // 1: a neighbour wait timed out
+    int gcap = -1, goptin = 0;           // co-resident CTAs of the group kernel and its shared memory (bytes)
     cudaError_t launch_err = cudaSuccess;  // a launch of the group kernel that failed
 };
 
@@ -749,6 +750,26 @@ void destroy_batch(qslbm_batch* B) {
     delete B;
 }
 
+// CTAs of the group kernel the device holds at once (one per SM) and the
+// dynamic shared memory one may take (the opt-in limit less the kernel's
+// static shared memory), computed once per batch.
+int group_capacity(qslbm_batch& B) {
+    if (B.gcap >= 0) return QSLBM_OK;
+    int dev = 0, sms = 0, optin = 0, occ = 0;
+    BCHK(cudaGetDevice(&dev));
+    BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const void* fn = (const void*)qslbm::k_batch_resident<qslbm::InstDesc<float>, true>;
+    cudaFuncAttributes fa;
+    BCHK(cudaFuncGetAttributes(&fa, fn));
+    optin -= (int)fa.sharedSizeBytes;
+    BCHK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    BCHK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, qslbm::kGroupThreads, optin));
+    B.gcap = occ * sms;
+    B.goptin = optin;
+    return QSLBM_OK;
+}
+
 // (Re)build the batch over the given handles: choose the members the
 // resident group kernel holds (allowed ones that fit, smallest first, while
 // their groups fit co-resident on the device), order the marching members by
@@ -780,19 +801,9 @@ int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs, const std:
     // planes per group of each handle, and the members the launch can hold
     std::vector<int> gp(count, 0);
     if (B->precision == QSLBM_FP32) {
-        int dev = 0, sms = 0, optin = 0, occ = 0;
-        BCHK(cudaGetDevice(&dev));
-        BCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        BCHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        // dynamic shared memory a CTA may take: the opt-in limit less the
-        // kernel's static shared memory
-        const void* fn = (const void*)qslbm::k_batch_resident<qslbm::InstDesc<float>, true>;
-        cudaFuncAttributes fa;
-        BCHK(cudaFuncGetAttributes(&fa, fn));
-        optin -= (int)fa.sharedSizeBytes;
-        BCHK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-        BCHK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, qslbm::kGroupThreads, optin));
-        const int cap = occ * sms;
+        int rc0 = group_capacity(*B);
+        if (rc0) return rc0;
+        const int cap = B->gcap, optin = B->goptin;
         std::vector<int> cand;
         for (int i = 0; i < count; ++i) {
             if (!allow.empty() && !allow[i]) continue;
@@ -1041,6 +1052,17 @@ double now_s(const qslbm_server& S) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
 }
 
+// Groups of the resident group kernel a request would take at the largest
+// group size (-1: the kernel does not hold it: 2-D, no wall, planes above
+// kGroupMaxNodes nodes).
+int groups_needed(const qslbm_params& p) {
+    if (p.dim != 3 || p.geometry == QSLBM_PERIODIC) return -1;
+    const long long P = (long long)p.nx * p.ny;
+    if (P > qslbm::kGroupMaxNodes || p.nz < 1) return -1;
+    const int G = std::max(1, std::min(p.nz, (int)(qslbm::kGroupMaxNodes / P)));
+    return (p.nz + G - 1) / G;
+}
+
 // Device bytes a request will hold (fields, double buffers, scratch, tables).
 long long estimate_bytes(const qslbm_params& p) {
     const long long n = (long long)p.nx * p.ny * (p.dim == 2 ? 1 : p.nz);
@@ -1075,13 +1097,27 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
     // admission (first fit under the budget)
     {
         std::lock_guard<std::mutex> lock(S.mu);
-        if (S.cfg.admit == QSLBM_ADMIT_SMALLEST)
+        // smallest first in FP32: keep the running requests within the group
+        // kernel's capacity (a request beyond it would put the whole batch on
+        // the marching route's launches every step)
+        const bool hold = S.cfg.admit == QSLBM_ADMIT_SMALLEST && S.cfg.precision == QSLBM_FP32;
+        int used_groups = 0;
+        if (hold) {
             std::stable_sort(S.pending.begin(), S.pending.end(), [](const Request& a, const Request& b) {
                 return estimate_bytes(a.p) < estimate_bytes(b.p);
             });
+            int rc0 = group_capacity(*S.batch);
+            if (rc0) return rc0;
+            for (const Running& r : S.running) used_groups += std::max(0, groups_needed(r.r.p));
+        }
         for (auto it = S.pending.begin(); it != S.pending.end();) {
             if (S.cfg.max_running > 0 && (int)S.running.size() >= S.cfg.max_running) break;
             const long long est = estimate_bytes(it->p);
+            if (hold && est <= S.cfg.hbm_budget_bytes) {
+                const int ng = groups_needed(it->p);
+                if (!S.running.empty() && (ng < 0 || used_groups + ng > S.batch->gcap)) break;
+                if (S.used + est <= S.cfg.hbm_budget_bytes) used_groups += std::max(0, ng);
+            }
             if (est > S.cfg.hbm_budget_bytes) {
                 qslbm_result res;
                 std::memset(&res, 0, sizeof(res));

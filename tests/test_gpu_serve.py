@@ -123,3 +123,26 @@ def test_smallest_first_admission():
             if len(seen) == 2:
                 break
     assert seen[b]["t_done"] <= seen[a]["t_admit"] + 1e-9
+
+
+def test_smallest_first_keeps_the_running_set_in_the_group_kernel():
+    # 24 x 24 x 96 pipes take 12 groups each at the largest group size, so at
+    # most floor(SMs / 12) of them run at once; the rest wait their turn
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p = W.small_pipe(nx=24, ny=24, nz=96, diameter=16.0, Re=50.0, Ha=10.0, Rm=1e-3, perturb=0.0,
+                     init_kind="poiseuille", seed=21)
+    n = sms // 12 + 3
+    with Server(8 * GB, chunk_steps=10, admit="smallest") as S:
+        ids = [S.submit(dict(p, seed=21 + k), tol=1e-30, max_steps=20) for k in range(n)]
+        most, seen = 0, {}
+        for _ in range(20):
+            nr, _ = S.run()
+            most = max(most, nr)
+            for r in S.poll():
+                seen[r["id"]] = r
+            if len(seen) == n:
+                break
+    assert most == sms // 12
+    assert all(seen[i]["status"] == ETIMEOUT and seen[i]["steps"] == 20 for i in ids)
