@@ -1102,6 +1102,21 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
         // the marching route's launches every step)
         const bool hold = S.cfg.admit == QSLBM_ADMIT_SMALLEST && S.cfg.precision == QSLBM_FP32;
         int used_groups = 0;
+        // a request larger than the whole budget is answered at once
+        for (auto it = S.pending.begin(); it != S.pending.end();) {
+            if (estimate_bytes(it->p) > S.cfg.hbm_budget_bytes) {
+                qslbm_result res;
+                std::memset(&res, 0, sizeof(res));
+                res.id = it->id;
+                res.status = QSLBM_EBUDGET;
+                res.t_submit = it->t_submit;
+                res.t_admit = res.t_done = now_s(S);
+                S.done.push_back(res);
+                it = S.pending.erase(it);
+            } else {
+                ++it;
+            }
+        }
         if (hold) {
             std::stable_sort(S.pending.begin(), S.pending.end(), [](const Request& a, const Request& b) {
                 return estimate_bytes(a.p) < estimate_bytes(b.p);
@@ -1113,21 +1128,10 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
         for (auto it = S.pending.begin(); it != S.pending.end();) {
             if (S.cfg.max_running > 0 && (int)S.running.size() >= S.cfg.max_running) break;
             const long long est = estimate_bytes(it->p);
-            if (hold && est <= S.cfg.hbm_budget_bytes) {
+            if (hold) {
                 const int ng = groups_needed(it->p);
                 if (!S.running.empty() && (ng < 0 || used_groups + ng > S.batch->gcap)) break;
                 if (S.used + est <= S.cfg.hbm_budget_bytes) used_groups += std::max(0, ng);
-            }
-            if (est > S.cfg.hbm_budget_bytes) {
-                qslbm_result res;
-                std::memset(&res, 0, sizeof(res));
-                res.id = it->id;
-                res.status = QSLBM_EBUDGET;
-                res.t_submit = it->t_submit;
-                res.t_admit = res.t_done = now_s(S);
-                S.done.push_back(res);
-                it = S.pending.erase(it);
-                continue;
             }
             if (S.used + est > S.cfg.hbm_budget_bytes) {
                 ++it;
