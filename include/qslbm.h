@@ -302,7 +302,7 @@ int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_
  * step for the remainder).  The magnetic sub-iteration (Sec. V.G, with the IB
  * on b after each sweep, Sec. V.D) takes one of two routes per instance:
  *  - resident groups (FP32): an instance with a straight wall (the same ring
- *    on every plane) and planes of at most 8192 nodes runs all its N_mag
+ *    on every plane) and planes of at most 5120 nodes runs all its N_mag
  *    sweeps in one cooperative launch shared by every such instance; each CTA
  *    holds a group of whole planes in shared memory, and the groups of an
  *    instance exchange their end planes through global memory with bounded
@@ -311,9 +311,9 @@ int qslbm_check_bounded_wait(double limit_s, int32_t counter_set, int32_t* gave_
  *    first while their groups fit co-resident on the device;
  *  - marching: every other instance (and any created with sweep_kernel =
  *    QSLBM_SWEEP_SPLIT) takes one persistent z-marching launch per sweep over
- *    the instances with N_mag > s, then one IB launch; the sweep's tile shape
- *    and persistent grid are chosen by timing candidates on the batch when it
- *    is first built with such a member.
+ *    the instances with N_mag > s, then one IB launch; the sweep's launch
+ *    mode, tile shape and persistent grid are chosen by timing candidates on
+ *    the batch when it is first built with such a member.
  * Each instance follows the same arithmetic as a handle created alone with
  * QSLBM_SWEEP_SPLIT (the same expressions in the same order). */
 typedef struct qslbm_batch qslbm_batch;
