@@ -186,3 +186,30 @@ def test_resident_groups_chunked_steps_equal_single_steps():
         for i in range(len(ps)):
             for a, b in zip(A.member(i).state(), B.member(i).state()):
                 np.testing.assert_array_equal(a, b)
+
+
+def test_resident_groups_variants_match_single_instances():
+    # the sweep variants the group kernel runs through the sweep weights: the
+    # accelerated sweep (Sec. V.H), the time-resolved update (Sec. III.D, one
+    # sweep per step), a single plane (both z neighbours are the plane itself),
+    # and the six-magnet in-plane field split over several groups
+    ps = [
+        W.small_pipe(nx=24, ny=24, nz=40, diameter=16.0, Re=100.0, Ha=20.0, Rm=1e-3, alpha=0.75, n_mag=60, seed=31),
+        W.small_pipe(nx=24, ny=22, nz=10, diameter=16.0, U0=0.05, Re=50.0, Ha=10.0, Rm=4.0, b0_kind="tanh",
+                     ramp_center=5.0, ramp_width=2.0, perturb=0.0, mag_scheme=1, seed=32),
+        W.small_pipe(nx=20, ny=20, nz=1, diameter=14.0, Re=40.0, Ha=10.0, Rm=1e-2, n_mag=30, seed=33),
+        W.small_pipe(nx=40, ny=40, nz=12, diameter=30.0, Ha=12.0, Rm=5e-3, n_mag=40, b0_kind="field",
+                     b0_field=W.six_magnet_field(40, 40, 30.0), seed=34),
+    ]
+    steps = 6
+    with Batch(ps) as B:
+        info = B.info()
+        assert info["resident_instances"] == len(ps)
+        B.step(steps)
+        got = [B.member(i).state() for i in range(len(ps))]
+    for i, p in enumerate(ps):
+        with Solver(dict(p, sweep_kernel="split")) as s:
+            s.step(steps)
+            want = s.state()
+        for a, b in zip(got[i], want):
+            assert rel(a, b) <= 1e-6, i
