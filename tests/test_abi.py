@@ -82,3 +82,35 @@ def test_static_diagnostics_null_arguments_set_the_error_text():
     rc = L.qslbm_observables_static(None, None, None, None, None, 0.0, 0, None, None)
     assert rc == _lib.EINVAL
     assert b"NULL" in L.qslbm_last_error()
+
+
+STRUCTS = ["qslbm_params", "qslbm_units", "qslbm_obs", "qslbm_batch_info_t", "qslbm_server_config",
+           "qslbm_result", "qslbm_server_stats_t"]
+
+
+def test_struct_sizes_and_offsets_match_the_header(tmp_path):
+    # a C program built against the header prints every struct's size and
+    # every field's offset; the binding's ctypes layouts must agree
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "qslbm.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'  printf("{name} . %zu\\n", sizeof({name}));')
+        for field, _ in getattr(_lib, name)._fields_:
+            cfield = field[:-1] if field.endswith("_") else field  # a Python keyword in the binding
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {cfield}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        name, field, value = line.split()
+        cls = getattr(_lib, name)
+        want = C.sizeof(cls) if field == "." else getattr(cls, field).offset
+        assert int(value) == want, (name, field, int(value), want)
