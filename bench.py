@@ -335,7 +335,7 @@ def run_batched(steps: int = 3, count: int = 64):
 
 
 def run_serving(window_s: float = 30.0, time_cap_s: float = 120.0, rate: float = 20.0, tol: float = 1e-6,
-                max_steps: int = 20000, chunk: int = 200, max_running: int = 0, budget: int = 64 << 20,
+                max_steps: int = 20000, chunk: int = 200, max_running: int = 0, budget: int = 70 << 20,
                 fp64_cap_s: float = 150.0):
     """Serving at the stated request mix: Poisson arrivals (mean `rate` per
     second, seed 5) during the first `window_s` seconds of steady-state pipe
@@ -346,7 +346,7 @@ def run_serving(window_s: float = 30.0, time_cap_s: float = 120.0, rate: float =
     batch's resident group kernel, advanced by continuous batching until
     `time_cap_s`.  The stated arrivals bring about 10^3 times more work than
     one GPU can finish (a D = 128 solve alone needs ~10^6 steps of 14 M
-    nodes), so the budget (64 MB) admits the pipes that can reach the residual
+    nodes), so the budget (70 MiB) admits the pipes that can reach the residual
     within minutes (D <= 32) and answers larger ones at once with
     QSLBM_EBUDGET.  Reports solves/s and p50/p99 time-to-steady (submit to
     result) of the converged requests, and every request's outcome by
