@@ -372,6 +372,7 @@ void launch_sweep(qslbm_batch& B, int s, int threads, int grid, cudaStream_t st)
         switch (qslbm::ib_staged_unroll(S, np, B.sms)) {
             case 1: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 1>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
             case 2: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 2>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
+            case 4: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 4>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
             default: launch_pdl(B.pdl, qslbm::k_batch_ib_staged<T, 5>, ig, ib, sm, st, d, pf, kact, s, R, S); break;
         }
     } else if (nm > 0) {
@@ -568,6 +569,8 @@ int build_tables(qslbm_batch& B, int threads) {
             BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
             BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+            BCHK(cudaFuncSetAttribute(qslbm::k_batch_ib_staged<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
             B.ib_staged_smem = smem;
         }

@@ -787,12 +787,14 @@ __host__ __device__ inline size_t ib_staged_smem_bytes(int max_ring, int max_she
 // Shell nodes a thread of the staged corrector loads at once (U), and the CTAs
 // kept resident per SM at that U (bounds the registers).  When the launch's
 // planes fit one wave at four CTAs per SM, U is chosen for the largest shell
-// so that one batch of loads covers it (with U = 5 in FP32, four CTAs per SM
-// cover a plane per CTA of a 512-plane domain); with more planes than that,
-// U = 1 keeps eight CTAs per SM in flight.
+// so that one batch of loads covers it (U = 4 for shells of up to 1024 nodes,
+// as on the 96x96x512 pipe, where four CTAs per SM cover a plane per CTA; 5
+// above that); with more planes than that, U = 1 keeps eight CTAs per SM in
+// flight.
 inline int ib_staged_unroll(int max_shell, long long planes, int sms) {
     if (planes > 4LL * sms) return 1;
-    return max_shell <= kNodeThreads ? 1 : (max_shell <= 2 * kNodeThreads ? 2 : 5);
+    return max_shell <= kNodeThreads ? 1
+                                      : (max_shell <= 2 * kNodeThreads ? 2 : (max_shell <= 4 * kNodeThreads ? 4 : 5));
 }
 template <typename T, int U>
 constexpr int kIbStagedMinBlocks = (sizeof(T) == 4 ? 8 : 4) / (U == 1 ? 1 : 2);

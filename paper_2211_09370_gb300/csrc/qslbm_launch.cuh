@@ -133,6 +133,7 @@ struct Launch {
                     switch (s.ib_staged_u) {
                         case 1: launch_pdl(k_ib_staged<T, 1>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
                         case 2: launch_pdl(k_ib_staged<T, 2>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
+                        case 4: launch_pdl(k_ib_staged<T, 4>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
                         default: launch_pdl(k_ib_staged<T, 5>, ig, ib, sm, st, geo(s), bout, v, R, S); break;
                     }
                 } else if (s.ib.nm > 0) {
@@ -402,7 +403,10 @@ struct Launch {
             if (smem <= (size_t)max_optin) {
                 s.ib_staged_u = ib_staged_unroll(s.ib.max_shell, s.nz, sms);
                 const int U = s.ib_staged_u;
-                e = cudaFuncSetAttribute(U == 1 ? k_ib_staged<T, 1> : (U == 2 ? k_ib_staged<T, 2> : k_ib_staged<T, 5>),
+                e = cudaFuncSetAttribute(U == 1   ? k_ib_staged<T, 1>
+                                         : U == 2 ? k_ib_staged<T, 2>
+                                         : U == 4 ? k_ib_staged<T, 4>
+                                                  : k_ib_staged<T, 5>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 s.ib_staged_smem = smem;
