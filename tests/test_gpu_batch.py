@@ -213,3 +213,32 @@ def test_resident_groups_variants_match_single_instances():
             want = s.state()
         for a, b in zip(got[i], want):
             assert rel(a, b) <= 1e-6, i
+
+
+def test_batch_two_phase_ib_member_matches_oracle_fp64():
+    # a pipe whose ring (1131 markers per plane, D = 360) and shell are too
+    # large for the staged corrector's shared memory in FP64, so the batch
+    # corrects b after each sweep with the two-phase form (one thread per
+    # marker, then one per shell node; two launches per sweep); the same pipe
+    # alone takes the single-instance two-phase form
+    big = W.small_pipe(nx=368, ny=368, nz=2, diameter=360.0, n_mag=4, precision="fp64", seed=21)
+    small = W.small_pipe(nx=20, ny=20, nz=7, diameter=14.0, n_mag=4, precision="fp64", seed=22)
+    steps = 2
+    with Batch([small, big]) as B:
+        info = B.info()
+        # force, flow and parity advance, then per sweep the marching launch
+        # and the two IB launches
+        assert info["launches_per_step"] == 3 + 4 * 3, info["launches_per_step"]
+        B.step(steps)
+        rho, u, b = B.member(1).state()
+    with Solver(big) as s:
+        assert s.units["n_markers"] == 2 * 1131
+        s.step(steps)
+        want = s.state()
+    for a, w in zip((rho, u, b), want):
+        assert rel(a, w) <= 1e-13
+    o = oracle.Oracle(big)
+    o.step(steps)
+    orho, ou, ob = o.state()
+    assert rel(u, ou) <= 1e-12 and rel(b, ob) <= 1e-12, (rel(u, ou), rel(b, ob))
+    assert np.abs(rho - orho).max() <= 1e-12
