@@ -412,9 +412,15 @@ int qslbm_server_run(qslbm_server* s, int32_t* n_running, int32_t* n_pending);
 /* Move up to max finished results into out; *n = how many. */
 int qslbm_server_poll(qslbm_server* s, qslbm_result* out, int32_t max, int32_t* n);
 /* Fields of a finished request submitted with keep_fields (binary64 host
- * arrays as in qslbm_get_state); QSLBM_ENOTFOUND otherwise. */
+ * arrays as in qslbm_get_state); QSLBM_ENOTFOUND otherwise.  The first call
+ * for a request allocates its host-copy staging buffer (56 B per node), which
+ * counts against the HBM budget with the rest of its memory. */
 int qslbm_server_fields(qslbm_server* s, int64_t id, double* rho, double* u, double* b);
+/* Free a kept request's device memory and return it to the budget;
+ * QSLBM_ENOTFOUND for an id that is not kept. */
 int qslbm_server_release(qslbm_server* s, int64_t id);
+/* Counters; device_bytes is the device memory the admitted and kept requests
+ * hold, the figure admission compares with the budget. */
 int qslbm_server_stats(const qslbm_server* s, qslbm_server_stats_t* st);
 int qslbm_server_destroy(qslbm_server* s);
 

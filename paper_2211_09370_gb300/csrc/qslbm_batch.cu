@@ -1296,7 +1296,14 @@ int qslbm_server_poll(qslbm_server* S, qslbm_result* out, int32_t max, int32_t* 
 int qslbm_server_fields(qslbm_server* S, int64_t id, double* rho, double* u, double* b) {
     if (!S) return QSLBM_EINVAL;
     for (auto& kv : S->kept)
-        if (kv.first == id) return qslbm_get_state(kv.second, rho, u, b, nullptr);
+        if (kv.first == id) {
+            // the first host copy allocates the handle's staging buffer; it is
+            // held until the release, so it counts against the budget
+            const long long before = qslbm::handle_state_mut(kv.second).device_bytes;
+            const int rc = qslbm_get_state(kv.second, rho, u, b, nullptr);
+            S->used += qslbm::handle_state_mut(kv.second).device_bytes - before;
+            return rc;
+        }
     return QSLBM_ENOTFOUND;
 }
 
