@@ -48,7 +48,7 @@ extern "C" {
 #define QSLBM_ENOMEM -2    /* device or host allocation failed                 */
 #define QSLBM_ECUDA -3     /* a CUDA call failed (message: qslbm_last_error)   */
 #define QSLBM_EUNSTABLE -4 /* non-finite field value detected                  */
-#define QSLBM_ETIMEOUT -5  /* step cap reached before the stop tolerance       */
+#define QSLBM_ETIMEOUT -5  /* step cap reached before the stop tolerance, or a bounded device wait gave up */
 #define QSLBM_EBUDGET -6   /* request does not fit the device-memory budget    */
 #define QSLBM_ENOTFOUND -7 /* unknown request id                               */
 #define QSLBM_EARCH -8     /* device is not sm_103                             */

@@ -1072,7 +1072,7 @@ const char* qslbm_strerror(int code) {
         case QSLBM_ENOMEM: return "out of memory";
         case QSLBM_ECUDA: return "CUDA error";
         case QSLBM_EUNSTABLE: return "non-finite field value";
-        case QSLBM_ETIMEOUT: return "step cap reached before the stop tolerance";
+        case QSLBM_ETIMEOUT: return "timed out: step cap reached before the stop tolerance, or a bounded device wait gave up";
         case QSLBM_EBUDGET: return "request exceeds the device-memory budget";
         case QSLBM_ENOTFOUND: return "unknown request";
         case QSLBM_EARCH: return "device is not sm_103";

@@ -65,6 +65,9 @@ def test_null_arguments():
     assert L.qslbm_observables(None, None, None, None, None) == _lib.EINVAL
     assert L.qslbm_destroy(None) == _lib.EINVAL
     assert L.qslbm_strerror(_lib.EBUDGET).decode().startswith("request exceeds")
+    # the step cap and a bounded device wait that gave up share one code
+    t = L.qslbm_strerror(_lib.ETIMEOUT).decode()
+    assert "step cap" in t and "wait" in t
 
 
 def test_bounded_wait_check_rejects_bad_limits_before_the_device():
