@@ -134,9 +134,7 @@ def load(path: str | None = None):
     L.qslbm_batch_info.argtypes = [C.c_void_p, C.POINTER(qslbm_batch_info_t)]
     L.qslbm_batch_destroy.argtypes = [C.c_void_p]
     for name in ("qslbm_batch_create", "qslbm_batch_step", "qslbm_batch_handle", "qslbm_batch_info",
-                 "qslbm_batch_destroy", "qslbm_server_create", "qslbm_server_submit", "qslbm_server_run",
-           "qslbm_server_poll", "qslbm_server_fields", "qslbm_server_release", "qslbm_server_stats",
-           "qslbm_server_destroy"):
+                 "qslbm_batch_destroy"):
         getattr(L, name).restype = C.c_int
     L.qslbm_server_create.argtypes = [C.POINTER(qslbm_server_config), C.POINTER(C.c_void_p)]
     L.qslbm_server_submit.argtypes = [C.c_void_p, C.POINTER(qslbm_params), C.c_double, C.c_int64, C.c_int32,
