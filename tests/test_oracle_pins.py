@@ -139,6 +139,37 @@ def test_explicit_ib_equals_implicit_solve_when_A_is_diagonal():
     np.testing.assert_allclose(D @ explicit.T, 0.0, atol=1e-12)
 
 
+@pytest.mark.parametrize("magnetic", [False, True])
+def test_scaled_ib_correction_solves_the_lumped_relation(magnetic):
+    # Sec. V.E (Sec. V.F for the field): the rescaled marker correction is the
+    # solution of delta = lambda A^-1 (U_b - D f*) + (1 - lambda) D D^+ delta
+    # with A^-1 and D D^+ lumped to 1/d and d, wall value U_b = 0.  The
+    # corrections are recovered from the corrected field (f - f* = D^T delta,
+    # D of full row rank) on walls whose supports do not overlap and sit off
+    # the nodes (A diagonal, d != 1), at lambda = 2 (nu_ref = nu/2) and at the
+    # sweep's lambda_m = c.  A corrector that ignored lambda, or flipped the
+    # sign of (lambda - 1), would leave a residual (1 - lambda)(1/d - 1) r.
+    p = W.hartmann_channel_2d(nx=16, ny=12, diameter=8.6)
+    p = dict(p, nu_ref=oracle.Oracle(p).derived()["nu"] / 2)
+    o = oracle.Oracle(p)
+    lam = o.derived()["lambda_m" if magnetic else "lambda"]
+    assert lam > 1.5
+    D = _dense_D(o, p)
+    A = D @ D.T
+    assert np.allclose(A, np.diag(np.diag(A)))
+    d = np.diag(A).copy()
+    assert np.abs(d - 1.0).max() > 0.05
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(3, D.shape[1]))
+    g = o.ib_apply(f.reshape(3, 1, 12, 16), magnetic=magnetic).reshape(3, -1)
+    delta = np.linalg.solve(A, D @ (g - f).T)  # markers x components
+    r = -(D @ f.T)
+    rhs = (lam / d)[:, None] * r + ((1.0 - lam) * d)[:, None] * delta
+    np.testing.assert_allclose(delta, rhs, rtol=1e-9, atol=1e-11 * np.abs(r).max())
+    # the correction is not the unscaled one: lambda changes it
+    assert np.abs(delta - r / d[:, None]).max() > 1e-3 * np.abs(r).max()
+
+
 def test_explicit_ib_close_to_implicit_on_curved_wall():
     # Sec. V.C: the lumped corrector approximates the implicit solve; the
     # interpolated wall velocity after one correction is a small fraction of
