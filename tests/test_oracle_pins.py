@@ -111,6 +111,34 @@ def test_ib_diagonal_matches_dense_assembly(case):
     np.testing.assert_allclose(m["s"], lam / (d_dense * (1 + d_dense * (lam - 1))), rtol=1e-13)
 
 
+@pytest.mark.parametrize("diameter", [14.0, 27.0, 56.0])
+def test_marker_rings_lie_on_the_wall(diameter):
+    # Fig. 3(b): Lagrangian markers one lattice unit apart along the wall.  A
+    # pipe ring holds round(pi D) markers on the circle of radius D/2 about the
+    # axis, equally spaced in angle, one ring on every integer z plane.
+    n = int(diameter) + 8
+    p = W.small_pipe(nx=n, ny=n, nz=3, diameter=diameter)
+    m = oracle.Oracle(p).markers()
+    per = round(math.pi * diameter)
+    assert len(m["X"]) == 3 * per
+    for z in range(3):
+        X, Y, Z = (m[k][z * per:(z + 1) * per] for k in ("X", "Y", "Z"))
+        np.testing.assert_array_equal(Z, float(z))
+        cx, cy = X.mean(), Y.mean()
+        np.testing.assert_allclose(np.hypot(X - cx, Y - cy), diameter / 2, rtol=1e-13)
+        th = np.sort(np.mod(np.arctan2(Y - cy, X - cx), 2 * math.pi))
+        gaps = np.diff(np.concatenate([th, th[:1] + 2 * math.pi]))
+        np.testing.assert_allclose(gaps, 2 * math.pi / per, rtol=1e-9)
+        assert abs(math.pi * diameter / per - 1.0) <= 0.5 / per + 1e-12  # arc spacing within rounding of 1
+    # a channel: one marker per node along x on each wall line, at y = cy -/+ D/2
+    q = W.hartmann_channel_2d()
+    mc = oracle.Oracle(q).markers()
+    assert len(mc["X"]) == 2 * q["nx"]
+    np.testing.assert_array_equal(np.sort(mc["X"][: q["nx"]]), np.arange(q["nx"], dtype=float))
+    ys = np.unique(mc["Y"])
+    assert len(ys) == 2 and ys[1] - ys[0] == pytest.approx(q["diameter"])
+
+
 def test_ib_on_node_wall_has_unit_scaling_for_any_lambda():
     # Flat walls on nodes: A = I, d = 1, and lambda/(d(1+d(lambda-1))) = 1.
     for nu_ref in (0.0, 0.02, 1.0 / 6.0, 0.5):
