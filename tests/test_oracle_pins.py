@@ -323,6 +323,26 @@ def test_uniform_flow_gains_exactly_the_body_force(gamma, flow_q):
     np.testing.assert_allclose(rho, 1.0, atol=1e-14)
 
 
+def test_steady_residual_of_a_uniformly_accelerating_flow():
+    # The steady residual ||u^t - u^{t-k}|| / (k ||u^t||) over the fluid nodes:
+    # a uniform flow in a periodic box gains exactly F0 per step, so after k
+    # steps since the last diagnostics it is F0 / |u^t|, whatever k is.
+    p = W.small_pipe(nx=6, ny=5, nz=4, geometry="none", Ha=0.0, n_mag=1, perturb=0.0)
+    o = oracle.Oracle(p)
+    F0 = o.derived()["F0"]
+    u0 = np.array([0.01, -0.02, 0.005])
+    u = np.broadcast_to(u0[:, None, None, None], (3, 4, 5, 6)).copy()
+    o.set_state(rho=np.ones((4, 5, 6)), u=u, b=np.zeros_like(u), t=0)
+    o.observables()  # the reference velocity is now u(t = 0)
+    t = 0
+    for k in (10, 30):
+        o.step(k)
+        t += k
+        r = o.observables()["steady_residual"]
+        uz = u0[2] + t * F0
+        assert r == pytest.approx(F0 / math.sqrt(u0[0] ** 2 + u0[1] ** 2 + uz ** 2), rel=1e-10)
+
+
 @pytest.mark.parametrize("gamma", [1.0, 2.0])
 def test_pulsating_body_force_phase(gamma):
     # Sec. IV Eq. "variable force": F(t) = F0 (1 + amp sin(2 pi t / T)) with t
