@@ -203,7 +203,9 @@ void qslbm_params_init(qslbm_params* p);
  * b = 0 and u = seeded splitmix64 noise of size perturb * U0 inside the wall.
  * *p is copied.  On success *out owns the handle.
  * Errors: QSLBM_EINVAL (bad parameters, wall outside the box, markers not on
- * integer z planes), QSLBM_ENOMEM, QSLBM_ECUDA, QSLBM_EARCH. */
+ * integer z planes, more than 4096 (FP32) or 2048 (FP64) markers on one plane,
+ * the most whose corrections a per-plane IB kernel holds in shared memory;
+ * qslbm_last_error gives the reason), QSLBM_ENOMEM, QSLBM_ECUDA, QSLBM_EARCH. */
 int qslbm_create(const qslbm_params* p, qslbm_handle** out);
 
 /* Lattice-unit values of the handle.  Errors: QSLBM_EINVAL (NULL argument). */

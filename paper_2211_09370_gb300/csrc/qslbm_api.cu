@@ -262,7 +262,12 @@ int build_markers(State& s) {
     }
     h.max_ring = 0;
     for (int z = 0; z < planes; ++z) h.max_ring = std::max(h.max_ring, h.ring_off[z + 1] - h.ring_off[z]);
-    if ((size_t)3 * h.max_ring * (p.precision == QSLBM_FP64 ? 8 : 4) > 48 * 1024) return QSLBM_EINVAL;
+    if ((size_t)3 * h.max_ring * (p.precision == QSLBM_FP64 ? 8 : 4) > 48 * 1024) {
+        // the per-plane IB kernels keep a plane's marker deltas in shared memory
+        g_last_error = "wall ring of " + std::to_string(h.max_ring) + " markers per plane exceeds the limit of " +
+                       std::to_string(48 * 1024 / (3 * (p.precision == QSLBM_FP64 ? 8 : 4))) + " for this precision";
+        return QSLBM_EINVAL;
+    }
     // d_j and the scalings
     const long long P = (long long)s.nx * s.ny;
     std::vector<double> W;
