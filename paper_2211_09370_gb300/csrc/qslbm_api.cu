@@ -133,57 +133,67 @@ int map_units(const qslbm_params& p, qslbm_units& u) {
     return QSLBM_OK;
 }
 
+// Refusal of a parameter set, with its reason left in qslbm_last_error.
+int refuse(const std::string& why) {
+    g_last_error = "invalid parameters: " + why;
+    return QSLBM_EINVAL;
+}
+
 int validate(const qslbm_params& p) {
-    if (p.dim != 2 && p.dim != 3) return QSLBM_EINVAL;
-    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return QSLBM_EINVAL;
-    if (p.dim == 2 && p.nz != 1) return QSLBM_EINVAL;
-    if (p.geometry < QSLBM_CHANNEL || p.geometry > QSLBM_PERIODIC) return QSLBM_EINVAL;
-    if (!(p.diameter > 0) || !(p.Re > 0) || !(p.Rm > 0) || !(p.Ha >= 0)) return QSLBM_EINVAL;
-    if (!(p.marker_spacing > 0)) return QSLBM_EINVAL;
-    if (p.b0_kind != QSLBM_B0_UNIFORM && p.b0_kind != QSLBM_B0_TANH && p.b0_kind != QSLBM_B0_FIELD) return QSLBM_EINVAL;
-    if (p.b0_kind == QSLBM_B0_FIELD && !p.b0_field) return QSLBM_EINVAL;
-    if (p.b0_kind == QSLBM_B0_TANH && !(p.ramp_width > 0)) return QSLBM_EINVAL;
-    if (p.force_amp != 0.0 && !(p.force_period > 0)) return QSLBM_EINVAL;
-    if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return QSLBM_EINVAL;
-    if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0) return QSLBM_EINVAL;
-    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_FUSED) return QSLBM_EINVAL;
-    if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return QSLBM_EINVAL;
-    if (p.dim == 3 && p.flow_q != 0 && p.flow_q != 19 && p.flow_q != 27) return QSLBM_EINVAL;
-    if (p.dim == 2 && p.flow_q != 0 && p.flow_q != 9) return QSLBM_EINVAL;
-    if (p.flow_scheme != QSLBM_FLOW_SINGLE_STEP && p.flow_scheme != QSLBM_FLOW_MACROSCOPIC) return QSLBM_EINVAL;
+    if (p.dim != 2 && p.dim != 3) return refuse("dim must be 2 or 3");
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return refuse("nx, ny and nz must be at least 1");
+    if (p.dim == 2 && p.nz != 1) return refuse("a 2-D domain has nz = 1");
+    if (p.geometry < QSLBM_CHANNEL || p.geometry > QSLBM_PERIODIC) return refuse("unknown geometry");
+    if (!(p.diameter > 0)) return refuse("diameter must be positive");
+    if (!(p.Re > 0) || !(p.Rm > 0)) return refuse("Re and Rm must be positive");
+    if (!(p.Ha >= 0)) return refuse("Ha must not be negative");
+    if (!(p.marker_spacing > 0)) return refuse("marker_spacing must be positive");
+    if (p.b0_kind != QSLBM_B0_UNIFORM && p.b0_kind != QSLBM_B0_TANH && p.b0_kind != QSLBM_B0_FIELD)
+        return refuse("unknown b0_kind");
+    if (p.b0_kind == QSLBM_B0_FIELD && !p.b0_field) return refuse("b0_kind = field needs b0_field");
+    if (p.b0_kind == QSLBM_B0_TANH && !(p.ramp_width > 0)) return refuse("ramp_width must be positive");
+    if (p.force_amp != 0.0 && !(p.force_period > 0)) return refuse("a pulsating force needs force_period > 0");
+    if (p.precision != QSLBM_FP32 && p.precision != QSLBM_FP64) return refuse("unknown precision");
+    if (p.n_mag < 0 || p.perturb < 0 || p.nu_ref < 0 || p.eta_ref < 0)
+        return refuse("n_mag, perturb, nu_ref and eta_ref must not be negative");
+    if (p.sweep_kernel < QSLBM_SWEEP_AUTO || p.sweep_kernel > QSLBM_SWEEP_FUSED) return refuse("unknown sweep_kernel");
+    if (p.init_kind != QSLBM_INIT_REST && p.init_kind != QSLBM_INIT_POISEUILLE) return refuse("unknown init_kind");
+    if (p.dim == 3 && p.flow_q != 0 && p.flow_q != 19 && p.flow_q != 27) return refuse("3-D flow_q is 19 or 27");
+    if (p.dim == 2 && p.flow_q != 0 && p.flow_q != 9) return refuse("2-D flow_q is 9");
+    if (p.flow_scheme != QSLBM_FLOW_SINGLE_STEP && p.flow_scheme != QSLBM_FLOW_MACROSCOPIC)
+        return refuse("unknown flow_scheme");
     if (p.flow_scheme == QSLBM_FLOW_MACROSCOPIC) {
-        if (!(p.gamma == 0.0 || p.gamma == 1.0)) return QSLBM_EINVAL;  // the scheme sets the time step
+        if (!(p.gamma == 0.0 || p.gamma == 1.0))  // the scheme sets the time step
+            return refuse("the macroscopic flow scheme sets gamma itself");
         qslbm_units u;
         map_units(p, u);
-        if (!(6.0 * u.nu >= 1.0 - 1e-12)) {
-            g_last_error = "macroscopic flow scheme: 6 nu = " + std::to_string(6.0 * u.nu) + " < 1 (tau < 1)";
-            return QSLBM_EINVAL;
-        }
+        if (!(6.0 * u.nu >= 1.0 - 1e-12))
+            return refuse("macroscopic flow scheme: 6 nu = " + std::to_string(6.0 * u.nu) + " < 1 (tau < 1)");
     }
     {
         // accelerated sweep: the checkerboard gain (2 w_0 - 2 + alpha)/alpha
         // stays >= -1 only for alpha >= 1 - w_0 (w_0 = 1/4 on D3Q7, 1/3 on D2Q5)
         const double a = p.alpha == 0.0 ? 1.0 : p.alpha;
         const double w0 = p.dim == 3 ? 0.25 : 1.0 / 3.0;
-        if (!(a >= 1.0 - w0 - 1e-12 && a <= 1.0)) return QSLBM_EINVAL;
-        if (p.mag_scheme != QSLBM_MAG_QS && p.mag_scheme != QSLBM_MAG_TIME) return QSLBM_EINVAL;
-        if (p.mag_scheme == QSLBM_MAG_TIME && a != 1.0) return QSLBM_EINVAL;
-        if (!(p.gamma >= 0.0) || p.gamma > 1e6) return QSLBM_EINVAL;
+        if (!(a >= 1.0 - w0 - 1e-12 && a <= 1.0))
+            return refuse("alpha outside [" + std::to_string(1.0 - w0) + ", 1], the sweep's stable range");
+        if (p.mag_scheme != QSLBM_MAG_QS && p.mag_scheme != QSLBM_MAG_TIME) return refuse("unknown mag_scheme");
+        if (p.mag_scheme == QSLBM_MAG_TIME && a != 1.0)
+            return refuse("the time-resolved magnetic update takes no alpha");
+        if (!(p.gamma >= 0.0) || p.gamma > 1e6) return refuse("gamma outside [0, 1e6]");
     }
     if (p.mag_scheme == QSLBM_MAG_TIME) {
         // checkerboard gain (2 tau_m - 1)(2 w_0 - 1) - 2 (tau_m - 1) >= -1
         qslbm_units u;
         map_units(p, u);
         const double tmax = p.dim == 3 ? 7.0 / 6.0 : 5.0 / 4.0;
-        if (!(u.tau_m > 0.5 && u.tau_m <= tmax + 1e-12)) {
-            g_last_error = "time-resolved magnetic update: tau_m = " + std::to_string(u.tau_m) + " outside (1/2, " +
-                           std::to_string(tmax) + "]";
-            return QSLBM_EINVAL;
-        }
+        if (!(u.tau_m > 0.5 && u.tau_m <= tmax + 1e-12))
+            return refuse("time-resolved magnetic update: tau_m = " + std::to_string(u.tau_m) + " outside (1/2, " +
+                          std::to_string(tmax) + "]");
     }
     // kernels index the three components of a field with 32-bit offsets
     long long n = (long long)p.nx * p.ny * p.nz;
-    if (3 * n > (1LL << 31) - 1) return QSLBM_EINVAL;
+    if (3 * n > (1LL << 31) - 1) return refuse("more than (2^31 - 1)/3 nodes");
     return QSLBM_OK;
 }
 
@@ -233,7 +243,10 @@ int build_markers(State& s) {
         }
     } else if (p.geometry == QSLBM_PIPE) {
         long long nth = std::llround(M_PI * p.diameter / p.marker_spacing);
-        if (nth < 3) return QSLBM_EINVAL;
+        if (nth < 3) {
+            g_last_error = "invalid parameters: a pipe ring needs at least 3 markers (pi D / marker_spacing)";
+            return QSLBM_EINVAL;
+        }
         for (int z = 0; z < planes; ++z) {
             for (long long i = 0; i < nth; ++i) {
                 double th = 2.0 * M_PI * (double)i / (double)nth;
@@ -327,7 +340,10 @@ int build_markers(State& s) {
             h.max_nnz = std::max(h.max_nnz, h.csr_off[h.shell_off[z + 1]] - h.csr_off[h.shell_off[z]]);
     }
     for (double v : h.d)
-        if (!(v > 0)) return QSLBM_EINVAL;
+        if (!(v > 0)) {
+            g_last_error = "invalid parameters: a marker has no lattice node in its support (d_j = 0)";
+            return QSLBM_EINVAL;
+        }
     return QSLBM_OK;
 }
 
@@ -642,7 +658,10 @@ int check_device() {
 }
 
 int create_impl(const qslbm_params* pin, qslbm_handle** out) {
-    if (!pin || !out) return QSLBM_EINVAL;
+    if (!pin || !out) {
+        g_last_error = "qslbm_create: the parameter or output pointer is NULL";
+        return QSLBM_EINVAL;
+    }
     *out = nullptr;
     int rc = validate(*pin);
     if (rc) return rc;

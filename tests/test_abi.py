@@ -38,29 +38,38 @@ def test_struct_layouts_match_header_sizes():
     assert math.isnan(p.center[0]) and p.b0_dir[0] == 1.0 and p.precision == _lib.FP32 and p.alpha == 1.0
 
 
-@pytest.mark.parametrize("bad", [
-    dict(dim=4), dict(nx=0), dict(diameter=-1.0), dict(Re=0.0), dict(Rm=-1.0), dict(Ha=-2.0),
-    dict(marker_spacing=0.0), dict(b0_kind=7), dict(b0_kind="tanh", ramp_width=0.0),
-    dict(force_amp=0.2, force_period=0.0), dict(precision=5), dict(n_mag=-3), dict(perturb=-1.0),
-    dict(alpha=0.7), dict(alpha=1.5), dict(alpha=-1.0),
-    dict(mag_scheme=2), dict(mag_scheme=1),  # the second: tau_m far above 7/6 at Rm = 1e-3
-    dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), dict(gamma=-1.0), dict(b0_kind="field"),
-    dict(flow_q=15), dict(flow_q=9), dict(dim=2, nz=1, flow_q=27),
-    dict(flow_scheme="macroscopic"),  # Re = 100: 6 nu < 1, tau < 1
-    dict(flow_scheme="macroscopic", Re=1.0, Ha=5.0, gamma=2.0),
+@pytest.mark.parametrize("bad,why", [
+    (dict(dim=4), "dim must be"), (dict(nx=0), "at least 1"), (dict(diameter=-1.0), "diameter"),
+    (dict(Re=0.0), "Re and Rm"), (dict(Rm=-1.0), "Re and Rm"), (dict(Ha=-2.0), "Ha must not"),
+    (dict(marker_spacing=0.0), "marker_spacing"), (dict(b0_kind=7), "b0_kind"),
+    (dict(b0_kind="tanh", ramp_width=0.0), "ramp_width"), (dict(force_amp=0.2, force_period=0.0), "force_period"),
+    (dict(precision=5), "precision"), (dict(n_mag=-3), "not be negative"), (dict(perturb=-1.0), "not be negative"),
+    (dict(alpha=0.7), "alpha outside"), (dict(alpha=1.5), "alpha outside"), (dict(alpha=-1.0), "alpha outside"),
+    (dict(mag_scheme=2), "mag_scheme"),
+    (dict(mag_scheme=1), "tau_m"),  # tau_m far above 7/6 at Rm = 1e-3
+    (dict(mag_scheme=1, Rm=3.0, U0=0.05, alpha=0.8), "no alpha"), (dict(gamma=-1.0), "gamma outside"),
+    (dict(b0_kind="field"), "b0_field"),
+    (dict(flow_q=15), "3-D flow_q"), (dict(flow_q=9), "3-D flow_q"), (dict(dim=2, nz=1, flow_q=27), "2-D flow_q"),
+    (dict(flow_scheme="macroscopic"), "6 nu"),  # Re = 100: 6 nu < 1, tau < 1
+    (dict(flow_scheme="macroscopic", Re=1.0, Ha=5.0, gamma=2.0), "sets gamma"),
 ])
-def test_invalid_parameters_rejected_before_device(bad):
+def test_invalid_parameters_rejected_before_device(bad, why):
     p = W.small_pipe(**bad)
     q = _lib.make_params(p)
     h = C.c_void_p()
-    rc = _lib.load().qslbm_create(C.byref(q), C.byref(h))
+    L = _lib.load()
+    rc = L.qslbm_create(C.byref(q), C.byref(h))
     assert rc == _lib.EINVAL
     assert not h.value
+    # the reason is left in qslbm_last_error
+    msg = L.qslbm_last_error().decode()
+    assert msg.startswith("invalid parameters: ") and why in msg, msg
 
 
 def test_null_arguments():
     L = _lib.load()
     assert L.qslbm_create(None, None) == _lib.EINVAL
+    assert b"NULL" in L.qslbm_last_error()
     assert L.qslbm_step(None, 1) == _lib.EINVAL
     assert L.qslbm_observables(None, None, None, None, None) == _lib.EINVAL
     assert L.qslbm_destroy(None) == _lib.EINVAL
