@@ -885,11 +885,18 @@ int set_members(qslbm_batch* B, const std::vector<qslbm_handle*>& hs, const std:
 }
 
 int create_batch(const qslbm_params* params, int32_t count, void* stream, qslbm_batch** out) {
-    if (!params || !out || count <= 0) return QSLBM_EINVAL;
+    if (!params || !out || count <= 0) {
+        qslbm::set_last_error("qslbm_batch_create: NULL argument or a count below one");
+        return QSLBM_EINVAL;
+    }
     *out = nullptr;
     const int prec = params[0].precision;
     for (int i = 0; i < count; ++i)
-        if (params[i].precision != prec || params[i].dim != 3) return QSLBM_EINVAL;
+        if (params[i].precision != prec || params[i].dim != 3) {
+            qslbm::set_last_error("qslbm_batch_create: member " + std::to_string(i) +
+                                  (params[i].dim != 3 ? " is not 3-D" : " has another precision than member 0"));
+            return QSLBM_EINVAL;
+        }
     qslbm_batch* B = new (std::nothrow) qslbm_batch();
     if (!B) return QSLBM_ENOMEM;
     B->precision = prec;
@@ -1232,9 +1239,19 @@ int server_run(qslbm_server& S, int32_t* n_running, int32_t* n_pending) {
 extern "C" {
 
 int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out) {
-    if (!cfg || !out || cfg->chunk_steps <= 0 || cfg->hbm_budget_bytes <= 0) return QSLBM_EINVAL;
-    if (cfg->precision != QSLBM_FP32 && cfg->precision != QSLBM_FP64) return QSLBM_EINVAL;
-    if (cfg->admit != QSLBM_ADMIT_FIFO && cfg->admit != QSLBM_ADMIT_SMALLEST) return QSLBM_EINVAL;
+    const char* why = nullptr;
+    if (!cfg || !out)
+        why = "NULL argument";
+    else if (cfg->chunk_steps <= 0 || cfg->hbm_budget_bytes <= 0)
+        why = "chunk_steps and hbm_budget_bytes must be positive";
+    else if (cfg->precision != QSLBM_FP32 && cfg->precision != QSLBM_FP64)
+        why = "unknown precision";
+    else if (cfg->admit != QSLBM_ADMIT_FIFO && cfg->admit != QSLBM_ADMIT_SMALLEST)
+        why = "unknown admission order";
+    if (why) {
+        qslbm::set_last_error(std::string("qslbm_server_create: ") + why);
+        return QSLBM_EINVAL;
+    }
     *out = nullptr;
     qslbm_server* S = new (std::nothrow) qslbm_server();
     if (!S) return QSLBM_ENOMEM;
@@ -1266,8 +1283,10 @@ int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out) {
 
 int qslbm_server_submit(qslbm_server* S, const qslbm_params* p, double tol, int64_t max_steps, int32_t keep_fields,
                         int64_t* id) {
-    if (!S || !p || !(tol > 0) || max_steps <= 0) return QSLBM_EINVAL;
-    if (p->dim != 3) return QSLBM_EINVAL;
+    if (!S || !p || !(tol > 0) || max_steps <= 0 || p->dim != 3) {
+        qslbm::set_last_error("qslbm_server_submit: NULL argument, tol or max_steps not positive, or a 2-D problem");
+        return QSLBM_EINVAL;
+    }
     std::lock_guard<std::mutex> lock(S->mu);
     Request r{S->next_id++, *p, tol, max_steps, keep_fields, now_s(*S)};
     S->pending.push_back(r);

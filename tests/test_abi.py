@@ -79,6 +79,30 @@ def test_null_arguments():
     assert "step cap" in t and "wait" in t
 
 
+def test_batch_and_server_refusals_before_the_device():
+    # refused on the host, before any device work, with the reason left in
+    # qslbm_last_error
+    L = _lib.load()
+    out = C.c_void_p()
+    assert L.qslbm_batch_create(None, 0, None, C.byref(out)) == _lib.EINVAL
+    assert b"qslbm_batch_create" in L.qslbm_last_error()
+    mixed = (_lib.qslbm_params * 2)(_lib.make_params(W.small_pipe()), _lib.make_params(W.small_pipe(precision="fp64")))
+    assert L.qslbm_batch_create(mixed, 2, None, C.byref(out)) == _lib.EINVAL and not out.value
+    assert b"member 1" in L.qslbm_last_error()
+    flat = (_lib.qslbm_params * 1)(_lib.make_params(W.hartmann_channel_2d(precision="fp32")))
+    assert L.qslbm_batch_create(flat, 1, None, C.byref(out)) == _lib.EINVAL
+    assert b"not 3-D" in L.qslbm_last_error()
+    for cfg, why in (((0, 100, 0, _lib.FP32, None, 0), b"positive"), ((1 << 30, 0, 0, _lib.FP32, None, 0), b"positive"),
+                     ((1 << 30, 100, 0, 9, None, 0), b"precision"), ((1 << 30, 100, 0, _lib.FP32, None, 5), b"admission")):
+        c = _lib.qslbm_server_config(*cfg)
+        assert L.qslbm_server_create(C.byref(c), C.byref(out)) == _lib.EINVAL and not out.value
+        assert why in L.qslbm_last_error()
+    assert L.qslbm_server_create(None, C.byref(out)) == _lib.EINVAL
+    assert b"NULL" in L.qslbm_last_error()
+    assert L.qslbm_server_submit(None, None, 1e-6, 10, 0, None) == _lib.EINVAL
+    assert b"qslbm_server_submit" in L.qslbm_last_error()
+
+
 def test_bounded_wait_check_rejects_bad_limits_before_the_device():
     L = _lib.load()
     g, w = C.c_int32(), C.c_double()
