@@ -856,7 +856,10 @@ int capture_chunk(State& s, int bc, int fc, cudaGraphExec_t* exec) {
 }
 
 int step_impl(State& s, long long nsteps) {
-    if (nsteps < 0) return QSLBM_EINVAL;
+    if (nsteps < 0) {
+        g_last_error = "negative step count";
+        return QSLBM_EINVAL;
+    }
     NvtxRange range("qslbm step");
     const qslbm::Ops& o = ops(s);
     long long done = 0;
@@ -991,6 +994,12 @@ const State& handle_state(const qslbm_handle* h) { return h->s; }
 State& handle_state_mut(qslbm_handle* h) { return h->s; }
 }  // namespace qslbm
 
+// A NULL handle or an out-of-range argument of an ABI call.
+static int bad_argument(const char* what) {
+    g_last_error = what;
+    return QSLBM_EINVAL;
+}
+
 extern "C" {
 
 void qslbm_params_init(qslbm_params* p) {
@@ -1018,19 +1027,19 @@ int qslbm_create(const qslbm_params* p, qslbm_handle** out) {
 }
 
 int qslbm_get_units(const qslbm_handle* h, qslbm_units* out) {
-    if (!h || !out) return QSLBM_EINVAL;
+    if (!h || !out) return bad_argument("qslbm_get_units: NULL argument");
     *out = h->s.units;
     out->device_bytes = h->s.device_bytes;
     return QSLBM_OK;
 }
 
 int qslbm_step(qslbm_handle* h, int64_t nsteps) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_step: NULL handle");
     return step_impl(h->s, nsteps);
 }
 
 int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps) {
-    if (!h || nsweeps < 0) return QSLBM_EINVAL;
+    if (!h || nsweeps < 0) return bad_argument("qslbm_mag_sweeps: NULL handle or negative sweep count");
     NvtxRange range("magnetic sweeps + IB on b");
     ops(h->s).sweeps(h->s, nsweeps, h->s.stream);
     QCHK(cudaGetLastError());
@@ -1043,7 +1052,7 @@ int qslbm_mag_sweeps(qslbm_handle* h, int32_t nsweeps) {
 }
 
 int qslbm_observables(qslbm_handle* h, qslbm_obs* out, double* rho, double* u, double* b) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_observables: NULL handle");
     int rc = observe_impl(h->s, out);
     if (rc && rc != QSLBM_EUNSTABLE) return rc;
     int rc2 = get_fields(h->s, rho, u, b);
@@ -1051,7 +1060,7 @@ int qslbm_observables(qslbm_handle* h, qslbm_obs* out, double* rho, double* u, d
 }
 
 int qslbm_get_state(qslbm_handle* h, double* rho, double* u, double* b, int64_t* t) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_get_state: NULL handle");
     int rc = get_fields(h->s, rho, u, b);
     if (rc) return rc;
     QCHK(cudaStreamSynchronize(h->s.stream));
@@ -1060,13 +1069,13 @@ int qslbm_get_state(qslbm_handle* h, double* rho, double* u, double* b, int64_t*
 }
 
 int qslbm_set_state(qslbm_handle* h, const double* rho, const double* u, const double* b, int64_t t) {
-    if (!h || t < 0) return QSLBM_EINVAL;
+    if (!h || t < 0) return bad_argument("qslbm_set_state: NULL handle or negative time");
     return set_fields(h->s, rho, u, b, t);
 }
 
 int qslbm_step_host(qslbm_handle* h, const double* rho_in, const double* u_in, const double* b_in, int64_t t_in,
                     int64_t nsteps, double* rho_out, double* u_out, double* b_out, qslbm_obs* obs) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_step_host: NULL handle");
     int rc = set_fields(h->s, rho_in, u_in, b_in, t_in);
     if (rc) return rc;
     if ((rc = step_impl(h->s, nsteps))) return rc;
@@ -1074,14 +1083,14 @@ int qslbm_step_host(qslbm_handle* h, const double* rho_in, const double* u_in, c
 }
 
 int qslbm_sync(qslbm_handle* h) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_sync: NULL handle");
     QCHK(cudaStreamSynchronize(h->s.stream));
     QCHK(cudaGetLastError());
     return check_resident(h->s);
 }
 
 int qslbm_destroy(qslbm_handle* h) {
-    if (!h) return QSLBM_EINVAL;
+    if (!h) return bad_argument("qslbm_destroy: NULL handle");
     cudaError_t e = cudaStreamSynchronize(h->s.stream);
     release(h->s);
     delete h;

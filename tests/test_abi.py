@@ -70,9 +70,11 @@ def test_null_arguments():
     L = _lib.load()
     assert L.qslbm_create(None, None) == _lib.EINVAL
     assert b"NULL" in L.qslbm_last_error()
-    assert L.qslbm_step(None, 1) == _lib.EINVAL
-    assert L.qslbm_observables(None, None, None, None, None) == _lib.EINVAL
-    assert L.qslbm_destroy(None) == _lib.EINVAL
+    for fn, args in (("qslbm_step", (None, 1)), ("qslbm_observables", (None, None, None, None, None)),
+                     ("qslbm_get_state", (None, None, None, None, None)), ("qslbm_sync", (None,)),
+                     ("qslbm_mag_sweeps", (None, 1)), ("qslbm_destroy", (None,))):
+        assert getattr(L, fn)(*args) == _lib.EINVAL
+        assert L.qslbm_last_error().decode().startswith(fn + ":")
     assert L.qslbm_strerror(_lib.EBUDGET).decode().startswith("request exceeds")
     # the step cap and a bounded device wait that gave up share one code
     t = L.qslbm_strerror(_lib.ETIMEOUT).decode()
