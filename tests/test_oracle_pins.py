@@ -1094,34 +1094,55 @@ def _gold_velocity(r, th, Ha, terms):
     return (np.cosh(a * r * np.cos(th)) * even - np.sinh(a * r * np.cos(th)) * odd) / Ha
 
 
+def _gold_field(r, th, Ha, terms):
+    """Sec. IV Eq. "Magnetic field Gold solution" over R^2 F / sqrt(eta nu):
+    the streamwise induced field, the sum over n = -inf..inf folded onto
+    n >= 0 (I_-n = I_n)."""
+    sp = pytest.importorskip("scipy.special")
+    a = Ha / 2.0
+    x = a * r * np.cos(th)
+    acc = np.zeros_like(r)
+    for n in range(terms):
+        acc += ((1.0 if n == 0 else 2.0) * (np.exp(-x) - (-1.0) ** n * np.exp(x)) * sp.ivp(n, a) / sp.iv(n, a)
+                * sp.iv(n, a * r) * np.cos(n * th))
+    return (acc - 2.0 * r * np.cos(th)) / (2.0 * Ha)
+
+
 def test_gold_series_is_the_pipe_hartmann_solution():
-    # The series as printed: zero on the insulating wall; Poiseuille (1 - r^2)/4
-    # as Ha -> 0; and, eliminating b from nu lap u + B0 d_x b + F = 0 and
-    # eta lap b + B0 d_x u = 0, the fourth-order equation lap^2 u = Ha^2 d_x^2 u
-    # (lengths over R), checked by central differences inside the pipe.
+    # The two series as printed are the solution of the steady quasi-static
+    # pipe problem in units of the radius: lap U + Ha d_x B + 1 = 0 (momentum,
+    # unit forcing) and lap B + Ha d_x U = 0 (induction), with U = B = 0 on the
+    # insulating wall r = 1 -- which fixes the solution.  Checked by central
+    # differences at interior points, on the wall, and in the Poiseuille limit
+    # (1 - r^2)/4 as Ha -> 0.
     th = np.linspace(0.0, 2.0 * math.pi, 13)
     for Ha in (4.0, 8.0, 12.0):
         assert np.abs(_gold_velocity(np.ones_like(th), th, Ha, 40)).max() < 1e-11
+        assert np.abs(_gold_field(np.ones_like(th), th, Ha, 40)).max() < 1e-11
     r = np.linspace(0.0, 1.0, 11)
     np.testing.assert_allclose(_gold_velocity(r, 0.3 + 0 * r, 0.02, 8), (1 - r * r) / 4, rtol=1e-4, atol=1e-7)
-    h, Ha = 1e-2, 8.0
+    h = 1e-3
     rng = np.random.default_rng(4)
-    for x0, y0 in rng.uniform(-0.5, 0.5, size=(6, 2)):
-        def U(dx, dy):
-            x, y = x0 + dx * h, y0 + dy * h
-            return _gold_velocity(np.array([math.hypot(x, y)]), np.array([math.atan2(y, x)]), Ha, 40)[0]
-        lap = lambda f: lambda i, j: f(i + 1, j) + f(i - 1, j) + f(i, j + 1) + f(i, j - 1) - 4 * f(i, j)  # noqa: E731
-        bih = lap(lap(U))(0, 0) / h ** 4
-        dxx = (U(1, 0) - 2 * U(0, 0) + U(-1, 0)) / h ** 2
-        assert bih == pytest.approx(Ha * Ha * dxx, rel=2e-3, abs=1e-3 * Ha * Ha * abs(U(0, 0)))
+    for Ha in (4.0, 8.0):
+        for x0, y0 in rng.uniform(-0.6, 0.6, size=(4, 2)):
+            def at(g, i, j):
+                x, y = x0 + i * h, y0 + j * h
+                return g(np.array([math.hypot(x, y)]), np.array([math.atan2(y, x)]), Ha, 40)[0]
+
+            lap = {g: (at(g, 1, 0) + at(g, -1, 0) + at(g, 0, 1) + at(g, 0, -1) - 4 * at(g, 0, 0)) / h ** 2
+                   for g in (_gold_velocity, _gold_field)}
+            dx = {g: (at(g, 1, 0) - at(g, -1, 0)) / (2 * h) for g in (_gold_velocity, _gold_field)}
+            assert abs(lap[_gold_velocity] + Ha * dx[_gold_field] + 1.0) < 1e-4
+            assert abs(lap[_gold_field] + Ha * dx[_gold_velocity]) < 1e-4
 
 
 @pytest.mark.slow
 def test_pipe_matches_gold_at_finite_hartmann(pipe_hartmann_state):
     # Sec. IV: the converged pipe against Gold's solution on the nodes at
-    # r <= R - 2, within the curved wall's IB error (9.9 % here at D = 16;
+    # r <= R - 2, within the curved wall's IB error (u 9.9 % here at D = 16;
     # 4.3 % measured at D = 24 and 5.2 % at Ha = 12).  Without the Lorentz
-    # brake the flow would be Poiseuille, 130 % above it.
+    # brake the flow would be Poiseuille, 130 % above it; a flipped induction
+    # source would flip b (200 % off).
     o, p = pipe_hartmann_state
     d = o.derived()
     _, u, _ = o.state()
@@ -1136,6 +1157,11 @@ def test_pipe_matches_gold_at_finite_hartmann(pipe_hartmann_state):
     got = u[2, 0][inside]
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 0.12
     np.testing.assert_allclose(u[2, 1], u[2, 0], rtol=1e-12, atol=1e-16)  # z invariant
+    # the induced streamwise field (3.2 % here)
+    _, _, b = o.state()
+    want_b = R * R * d["F0"] / math.sqrt(d["eta"] * d["nu"]) * _gold_field(r[inside], th[inside], p["Ha"], 40)
+    got_b = b[2, 0][inside]
+    assert np.linalg.norm(got_b - want_b) / np.linalg.norm(want_b) < 0.08
 
 
 @pytest.mark.slow
