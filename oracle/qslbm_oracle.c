@@ -44,8 +44,7 @@
  *   Sec. V.G    Eqs. "densities MAC", "momentum Mac": the macroscopic flow
  *               scheme for tau >= 1 (flow_scheme = 1, R18)
  *
- * Readings where the paper is silent or garbled (each one is also listed in the
- * design notes of the repository):
+ * Readings where the paper is silent or garbled:
  *   R1 f^eq(x - c_i) in the density update carries the index i.
  *   R2 In the velocity update with the discrete-effect correction every term is
  *      a momentum and the sum is divided by rho(t+1) once.

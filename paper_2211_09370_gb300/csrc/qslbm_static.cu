@@ -4,8 +4,8 @@
 // diagnostics: code that is recording a CUDA graph (cudaMalloc is refused
 // while a stream is being captured), code whose device memory is handed out by
 // another allocator that already owns the pool (a framework's caching
-// allocator), or a loop with latency limits that must stay out of the driver's
-// allocator.  This file gives them the same FP64 diagnostic reduction as
+// allocator), or a loop with latency limits that must stay out of the CUDA
+// driver's allocator.  This file gives them the same FP64 diagnostic reduction as
 // qslbm_observables, over fields they pass in, with the per-block partial sums
 // kept in a fixed array compiled into the library instead of allocated memory.
 #include <cuda_runtime.h>
