@@ -344,19 +344,23 @@ typedef struct qslbm_batch_info_t {
  * qslbm_create. */
 int qslbm_batch_create(const qslbm_params* params, int32_t count, void* stream, qslbm_batch** out);
 
-/* Queue nsteps flow steps of every instance (asynchronous). */
+/* Queue nsteps flow steps of every instance (asynchronous; device errors
+ * surface at qslbm_batch_handle).  Errors: QSLBM_EINVAL (NULL batch, negative
+ * nsteps), QSLBM_ECUDA (a graph launch failed). */
 int qslbm_batch_step(qslbm_batch* b, int64_t nsteps);
 
 /* The handle of instance i (in creation order), after synchronising the
  * batch's stream: use it with qslbm_observables, qslbm_get_state,
  * qslbm_set_state and qslbm_get_units; stepping it on its own would leave the
- * batch out of step.  The batch owns it. */
+ * batch out of step.  The batch owns it.  Errors: QSLBM_EINVAL (NULL
+ * argument, i out of range), QSLBM_ECUDA, QSLBM_ETIMEOUT (a resident group's
+ * neighbour wait gave up; the counters are reset). */
 int qslbm_batch_handle(qslbm_batch* b, int32_t i, qslbm_handle** out);
 
-/* Sizes, tuned launch and timing of the batch. */
+/* Sizes, tuned launch and timing of the batch.  Errors: QSLBM_EINVAL (NULL). */
 int qslbm_batch_info(const qslbm_batch* b, qslbm_batch_info_t* info);
 
-/* Release every instance and the batch. */
+/* Release every instance and the batch.  Errors: QSLBM_EINVAL (NULL). */
 int qslbm_batch_destroy(qslbm_batch* b);
 
 /* ------------------------------------------------------------------ serving
@@ -403,15 +407,22 @@ typedef struct qslbm_server_stats_t {
     int64_t chunks, rebuilds, steps, node_steps, device_bytes;
 } qslbm_server_stats_t;
 
+/* Errors: QSLBM_EINVAL (NULL argument, chunk_steps or hbm_budget_bytes not
+ * positive, unknown precision or admission order), QSLBM_ENOMEM, QSLBM_ECUDA. */
 int qslbm_server_create(const qslbm_server_config* cfg, qslbm_server** out);
 /* Queue a request (dim 3; precision and stream are the server's).  keep_fields
  * keeps the finished fields on the device for qslbm_server_fields until
- * qslbm_server_release.  Thread-safe. */
+ * qslbm_server_release.  Thread-safe.  Its parameters are checked when it is
+ * admitted (a refusal becomes its result's status).  Errors: QSLBM_EINVAL
+ * (NULL argument, tol or max_steps not positive, dim != 3). */
 int qslbm_server_submit(qslbm_server* s, const qslbm_params* p, double tol, int64_t max_steps, int32_t keep_fields,
                         int64_t* id);
-/* One admission + chunk + retirement round (blocks until the chunk is done). */
+/* One admission + chunk + retirement round (blocks until the chunk is done).
+ * Errors: QSLBM_EINVAL (NULL server), QSLBM_ECUDA, QSLBM_ETIMEOUT (a resident
+ * group's neighbour wait gave up), QSLBM_ENOMEM. */
 int qslbm_server_run(qslbm_server* s, int32_t* n_running, int32_t* n_pending);
-/* Move up to max finished results into out; *n = how many. */
+/* Move up to max finished results into out; *n = how many.  Errors:
+ * QSLBM_EINVAL (NULL server or n, max < 0, NULL out with max > 0). */
 int qslbm_server_poll(qslbm_server* s, qslbm_result* out, int32_t max, int32_t* n);
 /* Fields of a finished request submitted with keep_fields (binary64 host
  * arrays as in qslbm_get_state); QSLBM_ENOTFOUND otherwise.  The first call
@@ -424,10 +435,12 @@ int qslbm_server_release(qslbm_server* s, int64_t id);
 /* Counters; device_bytes is the device memory the admitted and kept requests
  * hold, the figure admission compares with the budget. */
 int qslbm_server_stats(const qslbm_server* s, qslbm_server_stats_t* st);
+/* Release every running and kept request and the server (synchronises its
+ * stream first).  Errors: QSLBM_EINVAL (NULL). */
 int qslbm_server_destroy(qslbm_server* s);
 
-/* Static string for a code, and the text of the last CUDA error seen by the
- * calling thread (empty if none). */
+/* Static string for a code, and the reason for the calling thread's last
+ * refusal or failed CUDA call (empty if none). */
 const char* qslbm_strerror(int code);
 const char* qslbm_last_error(void);
 

@@ -251,7 +251,11 @@ struct qslbm_batch {
 
 namespace {
 
-thread_local std::string g_batch_error;
+// An argument refused on the host, with its reason left in qslbm_last_error.
+int refuse(const char* why) {
+    qslbm::set_last_error(why);
+    return QSLBM_EINVAL;
+}
 
 int fail(cudaError_t e, const char* what) {
     qslbm::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -950,7 +954,7 @@ int qslbm_batch_create(const qslbm_params* params, int32_t count, void* stream, 
 }
 
 int qslbm_batch_step(qslbm_batch* B, int64_t nsteps) {
-    if (!B || nsteps < 0) return QSLBM_EINVAL;
+    if (!B || nsteps < 0) return refuse("qslbm_batch_step: NULL batch or negative step count");
     if (B->members.empty()) return QSLBM_OK;
     long long i = 0;
     if (B->graph_chunk)
@@ -961,7 +965,8 @@ int qslbm_batch_step(qslbm_batch* B, int64_t nsteps) {
 }
 
 int qslbm_batch_handle(qslbm_batch* B, int32_t i, qslbm_handle** out) {
-    if (!B || !out || i < 0 || i >= (int)B->members.size()) return QSLBM_EINVAL;
+    if (!B || !out || i < 0 || i >= (int)B->members.size())
+        return refuse("qslbm_batch_handle: NULL argument or member index out of range");
     BCHK(cudaStreamSynchronize(B->stream));
     const int rc = check_groups(*B);
     if (rc) return rc;
@@ -970,7 +975,7 @@ int qslbm_batch_handle(qslbm_batch* B, int32_t i, qslbm_handle** out) {
 }
 
 int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
-    if (!B || !info) return QSLBM_EINVAL;
+    if (!B || !info) return refuse("qslbm_batch_info: NULL argument");
     std::memset(info, 0, sizeof(*info));
     info->count = (int32_t)B->members.size();
     info->max_n_mag = B->max_nmag;
@@ -1000,7 +1005,7 @@ int qslbm_batch_info(const qslbm_batch* B, qslbm_batch_info_t* info) {
 }
 
 int qslbm_batch_destroy(qslbm_batch* B) {
-    if (!B) return QSLBM_EINVAL;
+    if (!B) return refuse("qslbm_batch_destroy: NULL batch");
     destroy_batch(B);
     return QSLBM_OK;
 }
@@ -1295,7 +1300,7 @@ int qslbm_server_submit(qslbm_server* S, const qslbm_params* p, double tol, int6
 }
 
 int qslbm_server_run(qslbm_server* S, int32_t* n_running, int32_t* n_pending) {
-    if (!S) return QSLBM_EINVAL;
+    if (!S) return refuse("qslbm_server_run: NULL server");
     try {
         return server_run(*S, n_running, n_pending);
     } catch (...) {
@@ -1304,7 +1309,7 @@ int qslbm_server_run(qslbm_server* S, int32_t* n_running, int32_t* n_pending) {
 }
 
 int qslbm_server_poll(qslbm_server* S, qslbm_result* out, int32_t max, int32_t* n) {
-    if (!S || !n || max < 0 || (max > 0 && !out)) return QSLBM_EINVAL;
+    if (!S || !n || max < 0 || (max > 0 && !out)) return refuse("qslbm_server_poll: NULL argument or max < 0");
     const int k = std::min<int>(max, (int)S->done.size());
     for (int i = 0; i < k; ++i) out[i] = S->done[i];
     S->done.erase(S->done.begin(), S->done.begin() + k);
@@ -1313,7 +1318,7 @@ int qslbm_server_poll(qslbm_server* S, qslbm_result* out, int32_t max, int32_t* 
 }
 
 int qslbm_server_fields(qslbm_server* S, int64_t id, double* rho, double* u, double* b) {
-    if (!S) return QSLBM_EINVAL;
+    if (!S) return refuse("qslbm_server_fields: NULL server");
     for (auto& kv : S->kept)
         if (kv.first == id) {
             // the first host copy allocates the handle's staging buffer; it is
@@ -1327,7 +1332,7 @@ int qslbm_server_fields(qslbm_server* S, int64_t id, double* rho, double* u, dou
 }
 
 int qslbm_server_release(qslbm_server* S, int64_t id) {
-    if (!S) return QSLBM_EINVAL;
+    if (!S) return refuse("qslbm_server_release: NULL server");
     for (size_t i = 0; i < S->kept.size(); ++i)
         if (S->kept[i].first == id) {
             S->used -= qslbm::handle_state_mut(S->kept[i].second).device_bytes;
@@ -1339,7 +1344,7 @@ int qslbm_server_release(qslbm_server* S, int64_t id) {
 }
 
 int qslbm_server_stats(const qslbm_server* S, qslbm_server_stats_t* st) {
-    if (!S || !st) return QSLBM_EINVAL;
+    if (!S || !st) return refuse("qslbm_server_stats: NULL argument");
     std::memset(st, 0, sizeof(*st));
     st->running = (int32_t)S->running.size();
     st->pending = (int32_t)S->pending.size();
@@ -1354,7 +1359,7 @@ int qslbm_server_stats(const qslbm_server* S, qslbm_server_stats_t* st) {
 }
 
 int qslbm_server_destroy(qslbm_server* S) {
-    if (!S) return QSLBM_EINVAL;
+    if (!S) return refuse("qslbm_server_destroy: NULL server");
     if (S->batch->stream) cudaStreamSynchronize(S->batch->stream);
     for (Running& r : S->running)
         if (r.h) qslbm_destroy(r.h);

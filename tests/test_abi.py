@@ -103,6 +103,14 @@ def test_batch_and_server_refusals_before_the_device():
     assert b"NULL" in L.qslbm_last_error()
     assert L.qslbm_server_submit(None, None, 1e-6, 10, 0, None) == _lib.EINVAL
     assert b"qslbm_server_submit" in L.qslbm_last_error()
+    n = C.c_int32()
+    for fn, args in (("qslbm_batch_step", (None, 1)), ("qslbm_batch_handle", (None, 0, C.byref(out))),
+                     ("qslbm_batch_info", (None, None)), ("qslbm_batch_destroy", (None,)),
+                     ("qslbm_server_run", (None, None, None)), ("qslbm_server_poll", (None, None, 0, C.byref(n))),
+                     ("qslbm_server_fields", (None, 1, None, None, None)), ("qslbm_server_release", (None, 1)),
+                     ("qslbm_server_stats", (None, None)), ("qslbm_server_destroy", (None,))):
+        assert getattr(L, fn)(*args) == _lib.EINVAL
+        assert L.qslbm_last_error().decode().startswith(fn + ":")
 
 
 def test_bounded_wait_check_rejects_bad_limits_before_the_device():
